@@ -1,0 +1,172 @@
+"""ctypes front end of the C oracle (oracle/pagani_oracle.c).
+
+ORACLE / TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke()
+and the CPU-baseline leg of bench.py, never by the product package.  The
+oracle is built from source with gcc (-O2 -ffp-contract=off) into
+oracle/_build/; build() does that and is also called by __graft_entry__.build().
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import rule as _rule
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pagani_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liboracle.so")
+
+STATUS = {0: "converged", 1: "it_max", 2: "memory exhausted", 3: "tolerance unreachable"}
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Rule(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("G", ctypes.c_int),
+                ("gen", ctypes.POINTER(ctypes.c_double)), ("wts", ctypes.POINTER(ctypes.c_double)),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("q", ctypes.c_double)]
+
+
+class _Opt(ctypes.Structure):
+    _fields_ = [("relerr_filter", ctypes.c_int), ("heuristic_filter", ctypes.c_int),
+                ("init_div", ctypes.c_int), ("it_max", ctypes.c_int)]
+
+
+class _Res(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("errorest", ctypes.c_double),
+                ("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("n_regions", ctypes.c_int64), ("n_active_last", ctypes.c_int64)]
+
+
+TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.int32), ("search_ok", np.int32),
+                        ("s", np.int64), ("n_relerr_active", np.int64), ("n_survivors", np.int64),
+                        ("v", np.float64), ("e", np.float64), ("vf", np.float64), ("ef", np.float64),
+                        ("threshold", np.float64), ("direction_changes", np.float64)])
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.oracle_evaluate.restype = ctypes.c_int
+        _lib.oracle_pagani.restype = ctypes.c_int
+        _lib.oracle_default_init_div.restype = ctypes.c_int
+    return _lib
+
+
+_rule_cache: dict = {}
+
+
+def _rule_struct(n: int):
+    if n not in _rule_cache:
+        gen, wts = _rule.rule_tables(n)
+        g = np.ascontiguousarray(gen, dtype=np.float64)
+        w = np.ascontiguousarray(wts, dtype=np.float64)
+        a, b = _rule.fourth_difference_offsets()
+        q = float(_rule.LP / _rule.L2)
+        r = _Rule(n, g.shape[0], g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a, b, q)
+        _rule_cache[n] = (r, g, w)
+    return _rule_cache[n][0]
+
+
+def _dp(x):
+    return x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def default_init_div(n: int) -> int:
+    return _load().oracle_default_init_div(n)
+
+
+def evaluate(family: int, n: int, params, lower, width, diag: bool = False):
+    """Evaluate regions (arrays m x n).  Returns V, E (null-rule error, before
+    the two-level refinement) and K; with diag=True also the diagnostic rows
+    [N_1..N_4, rounding scales of N_1..N_4, rounding scale of V, D_0..D_{n-1},
+    rounding scales of D_j]."""
+    lib = _load()
+    lo = np.ascontiguousarray(lower, dtype=np.float64).reshape(-1, n)
+    wd = np.ascontiguousarray(width, dtype=np.float64).reshape(-1, n)
+    m = lo.shape[0]
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    V = np.zeros(m)
+    E = np.zeros(m)
+    K = np.zeros(m, dtype=np.int32)
+    D = np.zeros((m, 9 + 2 * n)) if diag else None
+    lib.oracle_evaluate(ctypes.byref(_rule_struct(n)), ctypes.c_int(family), _dp(p), ctypes.c_int64(m),
+                        _dp(lo), _dp(wd), _dp(V), _dp(E), K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        _dp(D) if diag else None)
+    return (V, E, K, D) if diag else (V, E, K)
+
+
+@dataclass
+class OracleResult:
+    estimate: float
+    errorest: float
+    status: int
+    iterations: int
+    n_regions: int
+    n_active_last: int
+    trace: np.ndarray
+    final_lower: np.ndarray | None
+    final_width: np.ndarray | None
+    finished_volume: float
+
+
+def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20, max_regions: int = 10 ** 6,
+              relerr_filter: int = 1, heuristic_filter: int = 1, init_div: int = 0, it_max: int = 100,
+              want_regions: bool = False) -> OracleResult:
+    lib = _load()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    opt = _Opt(relerr_filter, heuristic_filter, init_div, it_max)
+    res = _Res()
+    trace = np.zeros(it_max, dtype=TRACE_DTYPE)
+    fl = fw = None
+    cap = 0
+    if want_regions:
+        cap = max_regions
+        fl = np.zeros((cap, n))
+        fw = np.zeros((cap, n))
+    fv = ctypes.c_double(0.0)
+    lib.oracle_pagani(ctypes.byref(_rule_struct(n)), ctypes.c_int(family), _dp(p), ctypes.c_double(epsrel),
+                      ctypes.c_double(epsabs), ctypes.c_int64(max_regions), ctypes.byref(opt), ctypes.byref(res),
+                      trace.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(it_max),
+                      _dp(fl) if want_regions else None, _dp(fw) if want_regions else None,
+                      ctypes.c_int64(cap), ctypes.byref(fv))
+    it = res.iterations
+    tr = trace[:max(it, 0)].copy()
+    if want_regions:
+        m = int(tr["s"][-1]) if len(tr) else 0
+        fl, fw = fl[:m].copy(), fw[:m].copy()
+    return OracleResult(res.estimate, res.errorest, res.status, it, res.n_regions, res.n_active_last, tr,
+                        fl, fw, fv.value)
+
+
+def threshold_classify(A, E, v_tot: float, e_tot: float, e_it: float, tau_rel: float):
+    """Run the oracle's Threshold-Classify on given lists; returns
+    (ok, A_out, probes, t, direction_changes)."""
+    lib = _load()
+    a = np.ascontiguousarray(A, dtype=np.uint8).copy()
+    e = np.ascontiguousarray(E, dtype=np.float64)
+    probes = ctypes.c_int(0)
+    chg = ctypes.c_int(0)
+    t = ctypes.c_double(0.0)
+    ok = lib.oracle_threshold_classify(a.ctypes.data_as(ctypes.c_void_p), _dp(e), ctypes.c_double(v_tot),
+                                       ctypes.c_double(e_tot), ctypes.c_double(e_it), ctypes.c_int64(len(e)),
+                                       ctypes.c_double(tau_rel), ctypes.byref(probes), ctypes.byref(t),
+                                       ctypes.byref(chg))
+    return ok, a, probes.value, t.value, chg.value

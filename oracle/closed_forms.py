@@ -1,0 +1,61 @@
+"""Closed-form integrals over [0,1]^n of the five synthetic integrand families.
+
+ORACLE / TEST INFRASTRUCTURE ONLY (imported by tests/, the smoke check and the
+CPU baseline of bench.py; never by the product package).
+
+The paper argues for Genz families with fixed parameters so that analytic
+values exist (Sec. 4.2 "Accuracy"); it prints the formulas (Sec. 4.1) but no
+values.  These are the integrals written out, one 1-D factor per axis where
+the family is a product:
+
+* product peak  prod_j 1/(c_j^-2 + (x_j - w_j)^2):
+      prod_j c_j [atan(c_j (1 - w_j)) + atan(c_j w_j)]
+* Gaussian      exp(-sum_j a_j^2 (x_j - w_j)^2):
+      prod_j sqrt(pi)/(2 a_j) [erf(a_j (1 - w_j)) + erf(a_j w_j)]
+* oscillatory   cos(2 pi u + sum_j a_j x_j):
+      Re[ exp(2 pi i u) prod_j (exp(i a_j) - 1)/(i a_j) ]
+* corner peak   (1 + sum_j a_j x_j)^-(n+1):
+      1/(n! prod_j a_j) sum_{S subset [n]} (-1)^|S| / (1 + sum_{j in S} a_j)
+  evaluated in exact rational arithmetic (the alternating sum cancels heavily)
+* C0            exp(-sum_j a_j |x_j - w_j|):
+      prod_j (2 - exp(-a_j w_j) - exp(-a_j (1 - w_j))) / a_j
+
+Pinned in tests/test_oracle_closed_forms.py against tensor Gauss-Legendre
+quadrature (split at the kink for C0) in low dimension.
+"""
+from __future__ import annotations
+
+import cmath
+import itertools
+import math
+from fractions import Fraction
+
+PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0 = 0, 1, 2, 3, 4
+
+
+def closed_form(family: int, n: int, params) -> float:
+    p = [float(x) for x in params]
+    if family == PRODUCT_PEAK:
+        c, w = p[:n], p[n:2 * n]
+        return math.prod(cj * (math.atan(cj * (1 - wj)) + math.atan(cj * wj)) for cj, wj in zip(c, w))
+    if family == GAUSSIAN:
+        a, w = p[:n], p[n:2 * n]
+        return math.prod(math.sqrt(math.pi) / (2 * aj) * (math.erf(aj * (1 - wj)) + math.erf(aj * wj))
+                         for aj, wj in zip(a, w))
+    if family == OSCILLATORY:
+        u, a = p[0], p[1:1 + n]
+        z = cmath.exp(2j * math.pi * u)
+        for aj in a:
+            z *= (cmath.exp(1j * aj) - 1) / (1j * aj)
+        return z.real
+    if family == CORNER_PEAK:
+        a = [Fraction(x) for x in p[:n]]
+        tot = Fraction(0)
+        for k in range(n + 1):
+            for S in itertools.combinations(range(n), k):
+                tot += Fraction((-1) ** k) / (1 + sum((a[j] for j in S), Fraction(0)))
+        return float(tot / (math.factorial(n) * math.prod(a)))
+    if family == C0:
+        a, w = p[:n], p[n:2 * n]
+        return math.prod((2 - math.exp(-aj * wj) - math.exp(-aj * (1 - wj))) / aj for aj, wj in zip(a, w))
+    raise ValueError(f"unknown family {family}")

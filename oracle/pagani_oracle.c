@@ -1,0 +1,567 @@
+/*
+ * Plain CPU oracle of the PAGANI adaptive integration loop.
+ *
+ * ORACLE / TEST INFRASTRUCTURE ONLY.  This file shares no code with the CUDA
+ * path and is never linked into the product library.  Only tests/, the smoke
+ * check and the CPU-baseline leg of bench.py load it (through oracle/capi.py).
+ *
+ * It follows the paper's "PAGANI Algorithm" (Sec. 3.1, Algorithm 2) and
+ * "Threshold Classification" (Sec. 3.5.3, Algorithm 3) step by step in the
+ * paper's order and notation: Uniform-Split, then per iteration Evaluate,
+ * Two-Level-Error, Rel-Err-Classify, Sum(V), Sum(E), the termination test,
+ * Threshold-Classify, the finished accumulations v_f and e_f, Filter, the
+ * parent update and Split.  Everything is double precision, single threaded,
+ * summed in region-index order, and compiled with -ffp-contract=off so the
+ * results are the same on x86-64 and aarch64.
+ *
+ * Readings of passages the paper leaves open (all listed in the design doc):
+ *  - Evaluate (Sec. 3.2): the rule, its null rules and the error formula come
+ *    in as tables from oracle/rule.py; the error from the four null values
+ *    N_1..N_4 is: r = max(N_1/N_2, N_2/N_3) (x/0 = inf for x > 0, 0 for x = 0);
+ *    err = 10 max(N_k) if r >= 1, 10 r N_1 if 1/2 <= r < 1, 40 r^3 N_1 else.
+ *  - Split axis (Sec. 2.2, Sec. 3.2): fourth divided difference per axis,
+ *    D_j = |(f(c+a h_j e_j) + f(c-a h_j e_j) - 2 f(c))
+ *           - q (f(c+b h_j e_j) + f(c-b h_j e_j) - 2 f(c))|, q = a^2/b^2,
+ *    K = smallest j with D_j >= (1 - 1e-10) max D; widest axis if max D = 0.
+ *  - Two-level error (Sec. 2.1, Sec. 3.2): for siblings L, R of parent P,
+ *    delta = |V_L + V_R - V_P| / 4, S = E_L + E_R; if S > 0 each child's error
+ *    becomes E (1 + 2 delta / S) + delta, else E + delta.
+ *  - Uniform-Split (Sec. 3.1): d = largest power of two >= 2 with d^n <= 4096.
+ *  - Children of survivor p are stored at 2p (lower half) and 2p+1 (upper
+ *    half), so the parent of region i is i/2 and its sibling i^1.
+ *  - Threshold-Classify trigger (Sec. 3.5.2): (a) from the second iteration
+ *    on, |v_tot - v_tot_prev| <= tau_rel |v_tot|; (b) 2 (number of rel-err
+ *    actives) > max_regions.
+ *  - Threshold search (Sec. 3.5.3): candidate finished set = rel-err finished
+ *    plus {E_i < t}; too few finished -> t += (max - t)/2; too much error ->
+ *    t -= (t - min)/2; every change of direction adds 0.10 to P_max (cap
+ *    0.95); give up after 10 direction changes or 64 probes; e_b uses |v_tot|.
+ *  - Memory exhaustion (Sec. 3.5.2): if 2 (survivors) > max_regions after
+ *    the threshold step, return the latest estimates with status 2.
+ *  - Unreachable tolerance (Sec. 3.5.3): when no region stays active, or the
+ *    finished error e_f alone exceeds max(tau_rel |v + v_f|, tau_abs), stop
+ *    with status 3 and the latest estimates.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+enum {
+  FAM_PRODUCT_PEAK = 0,
+  FAM_GAUSSIAN = 1,
+  FAM_OSCILLATORY = 2,
+  FAM_CORNER_PEAK = 3,
+  FAM_C0 = 4,
+  FAM_MONOMIAL = 100 /* test-only: prod_j x_j^(p_j), integer p_j */
+};
+
+typedef struct {
+  int n;              /* dimension */
+  int G;              /* number of generators */
+  const double *gen;  /* G x n generator magnitudes on [-1,1]^n, row-major */
+  const double *wts;  /* G x 5: basic rule, then null rules u_1..u_4 */
+  double a, b, q;     /* fourth-difference radii sqrt(lp), sqrt(l2); q = a^2/b^2 */
+} oracle_rule;
+
+typedef struct {
+  int relerr_filter;     /* Sec. 3.5.1: 0 turns rel-err classification off */
+  int heuristic_filter;  /* Sec. 3.5.2: 0 turns Threshold-Classify off */
+  int init_div;          /* 0 = default Uniform-Split divisions */
+  int it_max;
+} oracle_options;
+
+typedef struct {
+  double estimate, errorest;
+  int status;            /* 0 converged, 1 it_max, 2 memory exhausted,
+                            3 tolerance unreachable, <0 error */
+  int iterations;
+  int64_t n_regions;     /* sum over iterations of regions evaluated */
+  int64_t n_active_last; /* regions evaluated in the last iteration */
+} oracle_result;
+
+typedef struct {
+  int32_t it, trigger, probes, search_ok;
+  int64_t s, n_relerr_active, n_survivors;
+  double v, e, vf, ef, threshold, direction_changes;
+} oracle_trace;
+
+/* ------------------------------------------------------------ integrands -- */
+static double integrand(int fam, int n, const double *p, const double *x) {
+  double s = 0.0, r = 1.0;
+  int j;
+  switch (fam) {
+  case FAM_PRODUCT_PEAK: /* prod_j 1/(c_j^-2 + (x_j - w_j)^2); p = c[n], w[n] */
+    for (j = 0; j < n; ++j) {
+      double t = x[j] - p[n + j];
+      r *= 1.0 / (pow(p[j], -2.0) + t * t);
+    }
+    return r;
+  case FAM_GAUSSIAN: /* exp(-sum_j a_j^2 (x_j - w_j)^2); p = a[n], w[n] */
+    for (j = 0; j < n; ++j) {
+      double t = x[j] - p[n + j];
+      s += p[j] * p[j] * t * t;
+    }
+    return exp(-s);
+  case FAM_OSCILLATORY: /* cos(2 pi u + sum_j a_j x_j); p = u, a[n] */
+    s = 2.0 * OR_PI * p[0];
+    for (j = 0; j < n; ++j) s += p[1 + j] * x[j];
+    return cos(s);
+  case FAM_CORNER_PEAK: /* (1 + sum_j a_j x_j)^-(n+1); p = a[n] */
+    s = 1.0;
+    for (j = 0; j < n; ++j) s += p[j] * x[j];
+    return pow(s, -(double)(n + 1));
+  case FAM_C0: /* exp(-sum_j a_j |x_j - w_j|); p = a[n], w[n] */
+    for (j = 0; j < n; ++j) s += p[j] * fabs(x[j] - p[n + j]);
+    return exp(-s);
+  case FAM_MONOMIAL:
+    for (j = 0; j < n; ++j) {
+      int e, k = (int)p[j];
+      for (e = 0; e < k; ++e) r *= x[j];
+    }
+    return r;
+  }
+  return NAN;
+}
+
+/* ------------------------------------------------------ orbit enumeration -- */
+/* next lexicographic permutation of v[0..n) (ascending order); 0 at the end */
+static int next_perm(double *v, int n) {
+  int i = n - 2, k;
+  while (i >= 0 && !(v[i] < v[i + 1])) --i;
+  if (i < 0) return 0;
+  k = n - 1;
+  while (!(v[i] < v[k])) --k;
+  { double t = v[i]; v[i] = v[k]; v[k] = t; }
+  for (int lo = i + 1, hi = n - 1; lo < hi; ++lo, --hi) {
+    double t = v[lo]; v[lo] = v[hi]; v[hi] = t;
+  }
+  return 1;
+}
+
+static int cmp_double(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+/* Sum of f over the orbit of one generator (all distinct coordinate
+ * permutations, all sign changes of the non-zero coordinates) on the box with
+ * centre c and half-widths h.  Also returns the sum of |f| and the count. */
+static double orbit_sum(int fam, int n, const double *p, const double *genrow,
+                        const double *c, const double *h, double *abs_sum,
+                        int64_t *count) {
+  double v[16], x[16], s = 0.0, sa = 0.0;
+  int64_t cnt = 0;
+  memcpy(v, genrow, sizeof(double) * n);
+  qsort(v, n, sizeof(double), cmp_double);
+  do {
+    int nzi[16], nz = 0;
+    for (int j = 0; j < n; ++j)
+      if (v[j] != 0.0) nzi[nz++] = j;
+    for (int mask = 0; mask < (1 << nz); ++mask) {
+      for (int j = 0; j < n; ++j) x[j] = c[j];
+      for (int t = 0; t < nz; ++t) {
+        int j = nzi[t];
+        double g = (mask >> t & 1) ? -v[j] : v[j];
+        x[j] = c[j] + h[j] * g;
+      }
+      double f = integrand(fam, n, p, x);
+      s += f;
+      sa += fabs(f);
+      ++cnt;
+    }
+  } while (next_perm(v, n));
+  *abs_sum = sa;
+  *count = cnt;
+  return s;
+}
+
+/* --------------------------------------------------------------- Evaluate -- */
+static double ratio_or(double x, double y) {
+  if (y > 0.0) return x / y;
+  return x > 0.0 ? INFINITY : 0.0;
+}
+
+/* The region error from the four null-rule values (reading given above). */
+static double null_rule_error(const double N[4]) {
+  double r = fmax(ratio_or(N[0], N[1]), ratio_or(N[1], N[2]));
+  if (r >= 1.0) return 10.0 * fmax(fmax(N[0], N[1]), fmax(N[2], N[3]));
+  if (r >= 0.5) return 10.0 * r * N[0];
+  return 40.0 * r * r * r * N[0];
+}
+
+/* Evaluate one region [lower, lower + width]: integral V, null-rule error E,
+ * split axis K.  diag (if not NULL) receives N_1..N_4, the four sums
+ * vol * sum_g |u_kg| * sum_orbit |f| (rounding scale of N_k), the rounding
+ * scale of V, then D_0..D_{n-1} and the rounding scales of the D_j. */
+static void evaluate_region(const oracle_rule *R, int fam, const double *p,
+                            const double *lower, const double *width, double *V,
+                            double *E, int *K, double *diag) {
+  int n = R->n;
+  double c[16], h[16], vol = 1.0;
+  double Sg[32], Ag[32];
+  for (int j = 0; j < n; ++j) {
+    h[j] = 0.5 * width[j];
+    c[j] = lower[j] + h[j];
+    vol *= width[j];
+  }
+  for (int g = 0; g < R->G; ++g) {
+    int64_t cnt;
+    Sg[g] = orbit_sum(fam, n, p, R->gen + (size_t)g * n, c, h, &Ag[g], &cnt);
+  }
+  double basic = 0.0, basic_abs = 0.0, N[4], Nabs[4];
+  for (int g = 0; g < R->G; ++g) {
+    basic += R->wts[g * 5] * Sg[g];
+    basic_abs += fabs(R->wts[g * 5]) * Ag[g];
+  }
+  for (int k = 0; k < 4; ++k) {
+    double s = 0.0, sa = 0.0;
+    for (int g = 0; g < R->G; ++g) {
+      s += R->wts[g * 5 + 1 + k] * Sg[g];
+      sa += fabs(R->wts[g * 5 + 1 + k]) * Ag[g];
+    }
+    N[k] = vol * fabs(s);
+    Nabs[k] = vol * sa;
+  }
+  *V = vol * basic;
+  *E = null_rule_error(N);
+
+  /* split axis from fourth divided differences */
+  double x[16], D[16], Dabs[16], f0, Dmax = 0.0;
+  for (int j = 0; j < n; ++j) x[j] = c[j];
+  f0 = integrand(fam, n, p, x);
+  for (int j = 0; j < n; ++j) {
+    double fa_p, fa_m, fb_p, fb_m;
+    x[j] = c[j] + h[j] * R->a; fa_p = integrand(fam, n, p, x);
+    x[j] = c[j] - h[j] * R->a; fa_m = integrand(fam, n, p, x);
+    x[j] = c[j] + h[j] * R->b; fb_p = integrand(fam, n, p, x);
+    x[j] = c[j] - h[j] * R->b; fb_m = integrand(fam, n, p, x);
+    x[j] = c[j];
+    D[j] = fabs((fa_p + fa_m - 2.0 * f0) - R->q * (fb_p + fb_m - 2.0 * f0));
+    Dabs[j] = fabs(fa_p) + fabs(fa_m) + 2.0 * fabs(f0) +
+              R->q * (fabs(fb_p) + fabs(fb_m) + 2.0 * fabs(f0));
+    if (D[j] > Dmax) Dmax = D[j];
+  }
+  int k = 0;
+  if (Dmax > 0.0) {
+    while (!(D[k] >= (1.0 - 1e-10) * Dmax)) ++k;
+  } else {
+    for (int j = 1; j < n; ++j)
+      if (width[j] > width[k]) k = j;
+  }
+  *K = k;
+  if (diag) {
+    for (int t = 0; t < 4; ++t) diag[t] = N[t];
+    for (int t = 0; t < 4; ++t) diag[4 + t] = Nabs[t];
+    diag[8] = vol * basic_abs;
+    for (int j = 0; j < n; ++j) diag[9 + j] = D[j];
+    for (int j = 0; j < n; ++j) diag[9 + n + j] = Dabs[j];
+  }
+}
+
+/* Exported: evaluate m regions (row-major lower/width, m x n). */
+int oracle_evaluate(const oracle_rule *R, int fam, const double *params,
+                    int64_t m, const double *lower, const double *width,
+                    double *V, double *E, int32_t *K, double *diag) {
+  for (int64_t i = 0; i < m; ++i) {
+    int k;
+    evaluate_region(R, fam, params, lower + i * R->n, width + i * R->n, &V[i],
+                    &E[i], &k, diag ? diag + i * (9 + 2 * R->n) : NULL);
+    K[i] = k;
+  }
+  return 0;
+}
+
+/* ----------------------------------------------------- Neumaier summation -- */
+typedef struct { double s, c; } nsum;
+static void nadd(nsum *a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+  else a->c += (x - t) + a->s;
+  a->s = t;
+}
+static double nval(const nsum *a) { return a->s + a->c; }
+
+/* ---------------------------------------------------- Two-Level-Error ---- */
+static void two_level_error(int64_t s, const double *V, double *E,
+                            const double *Vp) {
+  for (int64_t p = 0; p < s / 2; ++p) {
+    int64_t L = 2 * p, Rr = 2 * p + 1;
+    double delta = fabs(V[L] + V[Rr] - Vp[p]) / 4.0;
+    double S = E[L] + E[Rr];
+    if (S > 0.0) {
+      double cc = 1.0 + 2.0 * delta / S;
+      E[L] = E[L] * cc + delta;
+      E[Rr] = E[Rr] * cc + delta;
+    } else {
+      E[L] += delta;
+      E[Rr] += delta;
+    }
+  }
+}
+
+/* --------------------------------------------------- Rel-Err-Classify ---- */
+static void rel_err_classify(int64_t s, const double *V, const double *E,
+                             double tau_rel, int enabled, uint8_t *A) {
+  for (int64_t i = 0; i < s; ++i)
+    A[i] = enabled ? !(E[i] <= tau_rel * fabs(V[i])) : 1;
+}
+
+/* ------------------------------------------------- Threshold-Classify ---- */
+/* Returns 1 and updates A when a threshold meets the memory and accuracy
+ * requirements; otherwise leaves A unchanged (unsuccessful filtering). */
+static int threshold_classify(uint8_t *A, const double *E, double v_tot,
+                              double e_tot, double e_it, int64_t s_it,
+                              double tau_rel, int *probes_out, double *t_out,
+                              int *dirchg_out) {
+  double Pmax = 0.25;
+  double mn = INFINITY, mx = -INFINITY;
+  for (int64_t i = 0; i < s_it; ++i) {
+    if (E[i] < mn) mn = E[i];
+    if (E[i] > mx) mx = E[i];
+  }
+  double e_b = e_tot - fabs(v_tot) * tau_rel;
+  double t = e_it / (double)s_it;
+  int probes = 0, last_dir = 0, changes = 0, ok = 0;
+  *probes_out = 0;
+  *t_out = t;
+  *dirchg_out = 0;
+  if (!(e_b > 0.0)) return 0;
+  uint8_t *Acand = (uint8_t *)malloc((size_t)s_it);
+  for (;;) {
+    /* Apply-Threshold: finished = rel-err finished or E_i < t */
+    nsum sumAE = {0, 0};
+    int64_t sumA = 0;
+    for (int64_t i = 0; i < s_it; ++i) {
+      Acand[i] = A[i] && !(E[i] < t);
+      sumA += Acand[i];
+      if (Acand[i]) nadd(&sumAE, E[i]);
+    }
+    ++probes;
+    int64_t s_abar = s_it - sumA;
+    int dir;
+    if (s_abar > 0.5 * (double)s_it) {           /* memory requirement */
+      double e_abar = e_it - nval(&sumAE);
+      if (e_abar <= Pmax * e_b) { ok = 1; break; } /* accuracy requirement */
+      dir = -1;                                   /* too much error: lower t */
+    } else {
+      dir = +1;                                   /* too few finished: raise t */
+    }
+    if (last_dir != 0 && dir != last_dir) {
+      ++changes;
+      Pmax = fmin(Pmax + 0.10, 0.95);
+    }
+    last_dir = dir;
+    if (changes >= 10 || probes >= 64) break;
+    if (dir > 0) t = t + (mx - t) / 2.0;
+    else t = t - (t - mn) / 2.0;
+  }
+  if (ok) memcpy(A, Acand, (size_t)s_it);
+  free(Acand);
+  *probes_out = probes;
+  *t_out = t;
+  *dirchg_out = changes;
+  return ok;
+}
+
+/* ------------------------------------------------------- Uniform-Split ---- */
+int oracle_default_init_div(int n) {
+  int d = 2;
+  while (1) {
+    int64_t pw = 1;
+    for (int j = 0; j < n; ++j) pw *= 2 * d;
+    if (pw > 4096) break;
+    d *= 2;
+  }
+  return d;
+}
+
+/* Region i of the d^n grid: axis n-1 varies fastest. */
+static void uniform_split(int n, int d, double *lower, double *width) {
+  int64_t s = 1;
+  for (int j = 0; j < n; ++j) s *= d;
+  for (int64_t i = 0; i < s; ++i) {
+    int64_t r = i;
+    for (int j = n - 1; j >= 0; --j) {
+      lower[i * n + j] = (double)(r % d) / (double)d;
+      width[i * n + j] = 1.0 / (double)d;
+      r /= d;
+    }
+  }
+}
+
+/* ------------------------------------------------------ PAGANI main loop -- */
+int oracle_pagani(const oracle_rule *R, int fam, const double *params,
+                  double tau_rel, double tau_abs, int64_t max_regions,
+                  const oracle_options *opt, oracle_result *res,
+                  oracle_trace *trace, int trace_cap,
+                  double *final_lower, double *final_width, int64_t final_cap,
+                  double *fin_vol_out) {
+  int n = R->n;
+  int d = opt->init_div > 0 ? opt->init_div : oracle_default_init_div(n);
+  int64_t s = 1;
+  for (int j = 0; j < n; ++j) s *= d;
+  memset(res, 0, sizeof(*res));
+  if (s > max_regions) { res->status = -7; return -7; }
+
+  int64_t cap = s > max_regions ? s : max_regions;
+  double *H_lo = (double *)malloc(sizeof(double) * (size_t)cap * n);
+  double *H_w = (double *)malloc(sizeof(double) * (size_t)cap * n);
+  double *V = (double *)calloc((size_t)cap, sizeof(double));
+  double *E = (double *)calloc((size_t)cap, sizeof(double));
+  int32_t *K = (int32_t *)calloc((size_t)cap, sizeof(int32_t));
+  uint8_t *A = (uint8_t *)malloc((size_t)cap);
+  double *Vp = (double *)calloc((size_t)cap, sizeof(double));
+  double *Ep = (double *)calloc((size_t)cap, sizeof(double));
+  double v = 0, e = 0, vf = 0, ef = 0, v_tot_prev = 0;
+  nsum finvol = {0, 0};
+  int status = 1, it;
+
+  uniform_split(n, d, H_lo, H_w);               /* H <- Uniform-Split(R_0, d) */
+  memset(A, 1, (size_t)s);                      /* A[1:s] <- 1 */
+
+  for (it = 1; it <= opt->it_max; ++it) {
+    oracle_trace tr;
+    memset(&tr, 0, sizeof(tr));
+    tr.it = it;
+    tr.s = s;
+    res->n_regions += s;
+    res->n_active_last = s;
+    /* V, E, K <- Evaluate(H) */
+    for (int64_t i = 0; i < s; ++i) {
+      int k;
+      evaluate_region(R, fam, params, H_lo + i * n, H_w + i * n, &V[i], &E[i],
+                      &k, NULL);
+      K[i] = k;
+    }
+    for (int64_t i = 0; i < s; ++i)
+      if (!isfinite(V[i]) || !isfinite(E[i])) { status = -6; goto done; }
+    /* E <- Two-Level-Error(V, E, V_p, E_p) */
+    if (it > 1) two_level_error(s, V, E, Vp);
+    /* A <- Rel-Err-Classify(V, E, A) */
+    rel_err_classify(s, V, E, tau_rel, opt->relerr_filter, A);
+    /* v <- Sum(V); e <- Sum(E) */
+    nsum sv = {0, 0}, se = {0, 0};
+    for (int64_t i = 0; i < s; ++i) { nadd(&sv, V[i]); nadd(&se, E[i]); }
+    v = nval(&sv);
+    e = nval(&se);
+    int64_t n_rel = 0;
+    for (int64_t i = 0; i < s; ++i) n_rel += A[i];
+    tr.v = v; tr.e = e; tr.vf = vf; tr.ef = ef;
+    tr.n_relerr_active = n_rel;
+    /* termination test */
+    if ((e + ef) / fabs(v + vf) <= tau_rel || e + ef <= tau_abs) {
+      status = 0;
+      tr.n_survivors = 0;
+      if (trace && it - 1 < trace_cap) trace[it - 1] = tr;
+      break;
+    }
+    if (it == opt->it_max) {
+      status = 1;
+      if (trace && it - 1 < trace_cap) trace[it - 1] = tr;
+      break;
+    }
+    /* A <- Threshold-Classify(A, E, v + v_f, e + e_f, e, s) when triggered */
+    double v_tot = v + vf;
+    int trig = 0;
+    if (opt->heuristic_filter) {
+      if (it >= 2 && fabs(v_tot - v_tot_prev) <= tau_rel * fabs(v_tot)) trig |= 1;
+      if (2 * n_rel > max_regions) trig |= 2;
+    }
+    tr.trigger = trig;
+    if (trig) {
+      int probes, chg;
+      double t;
+      tr.search_ok = threshold_classify(A, E, v_tot, e + ef, e, s, tau_rel,
+                                        &probes, &t, &chg);
+      tr.probes = probes;
+      tr.threshold = t;
+      tr.direction_changes = chg;
+    }
+    v_tot_prev = v_tot;
+    int64_t n_surv = 0;
+    for (int64_t i = 0; i < s; ++i) n_surv += A[i];
+    tr.n_survivors = n_surv;
+    if (2 * n_surv > max_regions) {             /* memory exhausted */
+      status = 2;
+      if (trace && it - 1 < trace_cap) trace[it - 1] = tr;
+      break;
+    }
+    /* v_f <- v - Sum(V.A) + v_f ; e_f <- e - Sum(E.A) + e_f */
+    nsum sva = {0, 0}, sea = {0, 0};
+    for (int64_t i = 0; i < s; ++i)
+      if (A[i]) { nadd(&sva, V[i]); nadd(&sea, E[i]); }
+    double vf_new = v - nval(&sva) + vf;
+    double ef_new = e - nval(&sea) + ef;
+    tr.vf = vf_new; tr.ef = ef_new;
+    if (trace && it - 1 < trace_cap) trace[it - 1] = tr;
+    /* the tolerance is out of reach once no region stays active or the
+     * finished regions alone carry more error than it allows (Sec. 3.5.3
+     * notes this case is detectable); the latest estimates are v + v_f and
+     * e + e_f over the current leaves */
+    if (n_surv == 0 || ef_new > fmax(tau_rel * fabs(v + vf), tau_abs)) {
+      status = 3;
+      break;
+    }
+    vf = vf_new;
+    ef = ef_new;
+    for (int64_t i = 0; i < s; ++i)
+      if (!A[i]) {
+        double vol = 1.0;
+        for (int j = 0; j < n; ++j) vol *= H_w[i * n + j];
+        nadd(&finvol, vol);
+      }
+    /* H, V, E <- Filter(H, V, E, A); V_p <- V, E_p <- E */
+    int64_t q = 0;
+    for (int64_t i = 0; i < s; ++i) {
+      if (!A[i]) continue;
+      memmove(H_lo + q * n, H_lo + i * n, sizeof(double) * n);
+      memmove(H_w + q * n, H_w + i * n, sizeof(double) * n);
+      Vp[q] = V[i];
+      Ep[q] = E[i];
+      K[q] = K[i];
+      ++q;
+    }
+    /* H <- Split(H, K): children of p at 2p (lower) and 2p+1 (upper) */
+    for (int64_t pp = q - 1; pp >= 0; --pp) {
+      int k = K[pp];
+      for (int j = 0; j < n; ++j) {
+        double lo = H_lo[pp * n + j], w = H_w[pp * n + j];
+        H_lo[(2 * pp) * n + j] = lo;
+        H_w[(2 * pp) * n + j] = w;
+        H_lo[(2 * pp + 1) * n + j] = lo;
+        H_w[(2 * pp + 1) * n + j] = w;
+      }
+      H_w[(2 * pp) * n + k] *= 0.5;
+      H_w[(2 * pp + 1) * n + k] *= 0.5;
+      H_lo[(2 * pp + 1) * n + k] += H_w[(2 * pp + 1) * n + k];
+    }
+    s = 2 * q;                                  /* s <- 2s */
+    memset(A, 1, (size_t)s);
+  }
+  if (it > opt->it_max) it = opt->it_max;
+done:
+  res->status = status;
+  res->iterations = it;
+  res->estimate = v + vf;
+  res->errorest = e + ef;
+  if (final_lower && final_width) {
+    int64_t m = s < final_cap ? s : final_cap;
+    memcpy(final_lower, H_lo, sizeof(double) * (size_t)m * n);
+    memcpy(final_width, H_w, sizeof(double) * (size_t)m * n);
+  }
+  if (fin_vol_out) *fin_vol_out = nval(&finvol);
+  free(H_lo); free(H_w); free(V); free(E); free(K); free(A); free(Vp); free(Ep);
+  return status;
+}
+
+/* Exported for unit tests of Threshold-Classify on synthetic error lists. */
+int oracle_threshold_classify(uint8_t *A, const double *E, double v_tot,
+                              double e_tot, double e_it, int64_t s_it,
+                              double tau_rel, int *probes, double *t,
+                              int *direction_changes) {
+  return threshold_classify(A, E, v_tot, e_tot, e_it, s_it, tau_rel, probes, t,
+                            direction_changes);
+}

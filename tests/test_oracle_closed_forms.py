@@ -1,0 +1,86 @@
+"""Pins of oracle/closed_forms.py against brute-force composite tensor
+Gauss-Legendre quadrature in 2-D and 3-D (panels split at w for the C0 kink),
+and of the corner-peak formula against its 1-D antiderivative."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import closed_forms as cf
+from paper_2104_06494_gb300.workloads import draw_params, PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def f_numpy(family, n, p, X):
+    """Integrand on an array of points X (m x n), written from the formulas."""
+    p = np.asarray(p, dtype=np.float64)
+    if family == PRODUCT_PEAK:
+        c, w = p[:n], p[n:]
+        return np.prod(1.0 / (c ** -2.0 + (X - w) ** 2), axis=1)
+    if family == GAUSSIAN:
+        a, w = p[:n], p[n:]
+        return np.exp(-np.sum(a ** 2 * (X - w) ** 2, axis=1))
+    if family == OSCILLATORY:
+        return np.cos(2 * np.pi * p[0] + X @ p[1:])
+    if family == CORNER_PEAK:
+        return (1.0 + X @ p) ** (-(n + 1))
+    if family == C0:
+        a, w = p[:n], p[n:]
+        return np.exp(-np.sum(a * np.abs(X - w), axis=1))
+    raise ValueError
+
+
+def gl_nodes(breaks, m):
+    x, wt = np.polynomial.legendre.leggauss(m)
+    xs, ws = [], []
+    for lo, hi in zip(breaks[:-1], breaks[1:]):
+        xs.append(lo + (hi - lo) * (x + 1) / 2)
+        ws.append(wt * (hi - lo) / 2)
+    return np.concatenate(xs), np.concatenate(ws)
+
+
+def tensor_gl(family, n, p, panels=16, m=12):
+    per_axis = []
+    for j in range(n):
+        br = list(np.linspace(0, 1, panels + 1))
+        if family in (C0, GAUSSIAN, PRODUCT_PEAK):
+            w = p[n + j]
+            br = sorted(set(br + [w]))
+        per_axis.append(gl_nodes(np.array(br), m))
+    grids = np.meshgrid(*[a[0] for a in per_axis], indexing="ij")
+    wgrid = np.ones_like(grids[0])
+    for j, g in enumerate(np.meshgrid(*[a[1] for a in per_axis], indexing="ij")):
+        wgrid = wgrid * g
+    X = np.stack([g.ravel() for g in grids], axis=1)
+    return float(np.sum(wgrid.ravel() * f_numpy(family, n, p, X)))
+
+
+@pytest.mark.parametrize("family", [PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0])
+@pytest.mark.parametrize("n", [2, 3])
+def test_closed_form_vs_gauss_legendre(family, n):
+    p = draw_params(family, n, 9000 + 10 * family + n)
+    panels, m = (16, 12) if n == 2 else (8, 10)
+    ref = tensor_gl(family, n, p, panels, m)
+    assert abs(cf.closed_form(family, n, p) - ref) <= 1e-10 * abs(ref)
+
+
+@pytest.mark.parametrize("a", [0.5, 1.0, 2.0, 7.0])
+def test_corner_peak_1d(a):
+    # int_0^1 (1 + a x)^-2 dx = 1/(1 + a)
+    assert abs(cf.closed_form(CORNER_PEAK, 1, [a]) - 1 / (1 + a)) < 1e-15
+
+
+def test_golden_paper_integrands_are_reproduced():
+    d = json.load(open(os.path.join(GOLDEN, "paper_integrands.json")))
+    for c in d["cases"]:
+        assert cf.closed_form(c["family"], c["dim"], c["params"]) == float(c["integral"])
+
+
+def test_gaussian_closed_form_special_case():
+    # with w = 1/2 each factor is sqrt(pi)/a * erf(a/2)
+    a = 25.0
+    v = cf.closed_form(GAUSSIAN, 1, [a, 0.5])
+    assert abs(v - math.sqrt(math.pi) / a * math.erf(a / 2)) < 1e-16

@@ -1,0 +1,179 @@
+"""Pins of the oracle's PAGANI loop (oracle/pagani_oracle.c): results within
+the error estimate of the closed form, brute-force tensor Gauss-Legendre on
+tiny cases, a hand-computed fourth difference, the Lemma of Sec. 3.5.1, exact
+bookkeeping invariants, the threshold search's requirements (Algorithm 3) and
+the failure statuses."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import capi, closed_forms as cf, rule
+from paper_2104_06494_gb300.workloads import (draw_params, random_dyadic_regions, PRODUCT_PEAK, GAUSSIAN,
+                                              OSCILLATORY, CORNER_PEAK, C0, SplitMix64)
+
+FAMS = [PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0]
+
+
+@pytest.mark.parametrize("family", FAMS)
+@pytest.mark.parametrize("n,tau", [(2, 1e-3), (2, 1e-6), (2, 1e-9), (3, 1e-4), (3, 1e-7), (4, 1e-5)])
+def test_estimate_within_errorest_of_closed_form(family, n, tau):
+    p = draw_params(family, n, 100 + 7 * family + n)
+    ex = cf.closed_form(family, n, p)
+    r = capi.integrate(family, n, p, tau, max_regions=2_000_000, relerr_filter=0 if family == OSCILLATORY else 1)
+    assert r.status in (0, 3), r.status
+    assert abs(r.estimate - ex) <= r.errorest + 1e-15 * abs(ex), (r.estimate, ex, r.errorest)
+    if r.status == 0:
+        assert r.errorest <= tau * abs(r.estimate) * (1 + 1e-12) or r.errorest <= 1e-20
+
+
+@pytest.mark.parametrize("family", [GAUSSIAN, PRODUCT_PEAK])
+def test_tiny_cases_vs_tensor_gauss_legendre(family):
+    from tests.test_oracle_closed_forms import tensor_gl
+    for n in (2, 3):
+        p = draw_params(family, n, 4242 + n)
+        ref = tensor_gl(family, n, p, 32 if n == 2 else 12, 16 if n == 2 else 12)
+        r = capi.integrate(family, n, p, 1e-8, max_regions=2_000_000)
+        assert abs(r.estimate - ref) <= max(r.errorest, 1e-13 * abs(ref))
+
+
+def test_hand_computed_fourth_difference_x1_pow4():
+    """f = x_1^4 on [0,1]^2: along axis 0 the second differences at radii a,
+    b are 12 c^2 r^2 h^2 + 2 r^4 h^4, so D_0 = 2 a^2 h^4 |a^2 - b^2| with
+    a^2 = 1/16, b^2 = l2, h = 1/2; along axis 1 f is constant, D_1 = 0."""
+    V, E, K, D = capi.evaluate(100, 2, [4, 0], [[0.0, 0.0]], [[1.0, 1.0]], diag=True)
+    a2, b2, h = 1 / 16, float(rule.L2), 0.5
+    assert abs(D[0, 9] - 2 * a2 * h ** 4 * abs(a2 - b2)) < 1e-16
+    assert D[0, 10] == 0.0
+    assert K[0] == 0
+    assert abs(V[0] - 0.2) < 1e-16
+
+
+def test_split_axis_widest_when_flat():
+    # f = x_0 x_1: D_j = 0 on every axis (degree < 4 along each), so the widest axis wins
+    V, E, K = capi.evaluate(100, 3, [1, 1, 0], [[0.0, 0.0, 0.0]], [[0.25, 0.5, 0.5]])
+    assert K[0] == 1
+
+
+def test_error_zero_for_linear():
+    V, E, K = capi.evaluate(100, 4, [1, 0, 0, 0], [[0.1, 0.2, 0.3, 0.4]], [[0.5, 0.25, 0.125, 0.5]])
+    # all four null rules annihilate degree 1: only rounding noise (~10 N(d) eps) remains
+    assert E[0] <= 10 * 153 * 2.2e-16 * abs(V[0])
+
+
+@pytest.mark.parametrize("family", [PRODUCT_PEAK, GAUSSIAN, CORNER_PEAK, C0])
+def test_lemma_on_relerr_finished_regions(family):
+    """Sec. 3.5.1 Lemma: if every region satisfies e_i <= tau |v_i| and the
+    v_i share a sign, the sums satisfy e <= tau |v|."""
+    n, tau = 3, 1e-4
+    p = draw_params(family, n, 31 + family)
+    lo, wd = random_dyadic_regions(n, 4000, 7 + family, max_level=6)
+    V, E, K = capi.evaluate(family, n, p, lo, wd)
+    fin = E <= tau * np.abs(V)
+    assert fin.sum() > 10
+    assert np.sum(E[fin]) <= tau * abs(np.sum(V[fin]))
+
+
+@pytest.mark.parametrize("family,n,tau", [(GAUSSIAN, 3, 1e-6), (C0, 3, 1e-4), (CORNER_PEAK, 4, 1e-6),
+                                          (PRODUCT_PEAK, 2, 1e-9)])
+def test_bookkeeping_invariants(family, n, tau):
+    p = draw_params(family, n, 55 + family)
+    r = capi.integrate(family, n, p, tau, max_regions=2_000_000, want_regions=True)
+    tr = r.trace
+    # s_{it+1} = 2 (survivors of it)
+    for a, b in zip(tr[:-1], tr[1:]):
+        assert b["s"] == 2 * a["n_survivors"]
+    assert r.n_regions == int(tr["s"].sum())
+    # active volume + finished volume = 1 (dyadic boxes)
+    act = float(np.sum(np.prod(r.final_width, axis=1)))
+    assert abs(act + r.finished_volume - 1.0) <= 1e-14
+    # the final estimate is v + v_f and the error e + e_f over the last leaves
+    # (v_f, e_f before the last iteration's finished accumulation)
+    last = tr[-1]
+    vf_prev = tr[-2]["vf"] if len(tr) > 1 else 0.0
+    ef_prev = tr[-2]["ef"] if len(tr) > 1 else 0.0
+    assert r.estimate == last["v"] + vf_prev and r.errorest == last["e"] + ef_prev
+
+
+def test_threshold_search_meets_requirements_when_it_accepts():
+    rng = SplitMix64(99)
+    for trial in range(40):
+        s = 200 + trial * 37
+        E = np.array([10 ** rng.uniform(-12, -6) for _ in range(s)])
+        V = np.array([rng.uniform(1e-6, 2e-6) for _ in range(s)])
+        tau = 1e-3
+        A = (E > tau * V).astype(np.uint8)
+        e_it = float(np.sum(E))
+        v_tot = float(np.sum(V))
+        e_tot = e_it * (1 + rng.uniform(0, 0.5))
+        e_b = e_tot - abs(v_tot) * tau
+        ok, Aout, probes, t, chg = capi.threshold_classify(A, E, v_tot, e_tot, e_it, tau)
+        if ok:
+            fin = Aout == 0
+            assert fin.sum() > 0.5 * s                       # memory requirement
+            assert np.sum(E[fin]) <= 0.95 * e_b * (1 + 1e-12)  # accuracy requirement (P_max <= 0.95)
+            assert np.all(Aout <= A)                          # rel-err finished stay finished
+            assert np.all(Aout[E < t] == 0) and np.all(Aout[(E >= t) & (A == 1)] == 1)
+            assert E.min() <= t <= E.max()
+        else:
+            assert np.array_equal(Aout, A)
+            assert probes == 64 or chg >= 10 or e_b <= 0
+
+
+def test_threshold_search_lowers_mean_threshold_when_budget_exceeded():
+    """Sec. 3.5.3 example: the mean error threshold would finish 80 % of the
+    regions but spend 488 % of the error budget, so the search moves the
+    threshold down and accepts one below the mean that meets both
+    requirements."""
+    E = np.concatenate([np.logspace(-3, 0, 800), np.full(200, 10.0)])
+    s = len(E)
+    e_it = float(E.sum())
+    mean = e_it / s
+    fin_at_mean = float(E[E < mean].sum())
+    assert np.count_nonzero(E < mean) == 800
+    e_b = fin_at_mean / 4.88
+    v_tot, tau = 1e3, 1e-6
+    e_tot = e_b + v_tot * tau
+    A = np.ones(s, dtype=np.uint8)
+    ok, Aout, probes, t, chg = capi.threshold_classify(A, E, v_tot, e_tot, e_it, tau)
+    assert ok == 1 and probes > 1 and t < mean
+    fin = Aout == 0
+    assert fin.sum() > s / 2 and E[fin].sum() <= 0.95 * e_b
+
+
+def test_threshold_search_no_budget_returns_unchanged():
+    E = np.linspace(1, 2, 10)
+    A = np.ones(10, dtype=np.uint8)
+    ok, Aout, probes, t, chg = capi.threshold_classify(A, E, 1.0, 1e-9, float(E.sum()), 1e-3)
+    assert ok == 0 and probes == 0 and np.array_equal(A, Aout)
+
+
+def test_status_memory_exhausted():
+    p = draw_params(GAUSSIAN, 3, 3)
+    r = capi.integrate(GAUSSIAN, 3, p, 1e-12, max_regions=6000, heuristic_filter=0)
+    assert r.status == 2
+    assert r.n_active_last <= 6000
+
+
+def test_status_it_max():
+    p = draw_params(GAUSSIAN, 3, 3)
+    r = capi.integrate(GAUSSIAN, 3, p, 1e-12, max_regions=10 ** 6, it_max=1)
+    assert r.status == 1 and r.iterations == 1 and r.n_regions == 4096
+
+
+def test_status_initial_split_too_large():
+    p = draw_params(GAUSSIAN, 3, 3)
+    r = capi.integrate(GAUSSIAN, 3, p, 1e-3, max_regions=100)
+    assert r.status == -7
+
+
+def test_status_nonfinite_integrand():
+    # corner peak with 1 + a.x crossing zero inside the cube
+    r = capi.integrate(CORNER_PEAK, 2, [-2.0, 0.5], 1e-3, max_regions=10 ** 5)
+    assert r.status == -6
+
+
+def test_default_initial_divisions():
+    assert [capi.default_init_div(n) for n in range(2, 9)] == [64, 16, 8, 4, 4, 2, 2]
