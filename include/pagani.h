@@ -1,0 +1,154 @@
+/*
+ * pagani.h - C ABI of the GB300 (sm_103a) PAGANI adaptive integrator.
+ *
+ * PAGANI (Sakiotis et al., "PAGANI: A Parallel Adaptive GPU Algorithm for
+ * Numerical Integration", SC'21) integrates f over the unit hypercube [0,1]^n
+ * by evaluating a degree-9 fully symmetric cubature rule and its null-rule
+ * error estimate on every active sub-region at once, classifying regions as
+ * active or finished, filtering the finished ones out with a prefix scan and
+ * bisecting the survivors along an axis chosen by fourth divided
+ * differences (Sec. 3, Algorithm 2; threshold search Sec. 3.5.3, Algorithm 3).
+ *
+ * Every step of that loop runs in this library's CUDA kernels on one GPU; the
+ * loop itself stays on the device (a CUDA graph with conditional nodes).
+ * All arithmetic is IEEE double precision.
+ *
+ * Conventions for every entry point:
+ *  - Return value: a status code (>= 0 success or a non-converged but valid
+ *    result, < 0 error; see PAGANI_STATUS_*).  No C++ exception crosses the
+ *    ABI.  On error pagani_last_error() describes the failure.
+ *  - Host pointers are read (or written) during the call only; the caller
+ *    keeps ownership.  Device pointers must be CUDA device memory of the
+ *    current device, sized as stated, and stay valid until the call returns.
+ *  - cuda_stream: a cudaStream_t (NULL = a non-blocking stream the library
+ *    owns).  The calls below synchronise that stream before they return.
+ *  - Calls are serialised on an internal lock; the workspace is owned by the
+ *    library and reused across calls.
+ */
+#ifndef PAGANI_GB300_H
+#define PAGANI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Integrand families (the synthetic Genz families of Sec. 4.1).  params layout
+ * (float64, n = dim):
+ *   PRODUCT_PEAK  f = prod_j 1/(c_j^-2 + (x_j - w_j)^2)   params = c[n], w[n]
+ *   GAUSSIAN      f = exp(-sum_j a_j^2 (x_j - w_j)^2)     params = a[n], w[n]
+ *   OSCILLATORY   f = cos(2 pi u + sum_j a_j x_j)         params = u, a[n]
+ *   CORNER_PEAK   f = (1 + sum_j a_j x_j)^-(n+1)          params = a[n]
+ *   C0            f = exp(-sum_j a_j |x_j - w_j|)         params = a[n], w[n]   */
+#define PAGANI_PRODUCT_PEAK 0
+#define PAGANI_GAUSSIAN 1
+#define PAGANI_OSCILLATORY 2
+#define PAGANI_CORNER_PEAK 3
+#define PAGANI_C0 4
+
+#define PAGANI_MIN_DIM 2
+#define PAGANI_MAX_DIM 8
+
+/* Status codes.  0..3 come with valid estimates (Algorithm 2 returns the
+ * latest v + v_f, e + e_f in each case). */
+#define PAGANI_STATUS_CONVERGED 0    /* (e+e_f)/|v+v_f| <= epsrel or e+e_f <= epsabs */
+#define PAGANI_STATUS_IT_MAX 1       /* it_max iterations without convergence      */
+#define PAGANI_STATUS_MEMORY 2       /* splitting the actives would exceed max_regions (Sec. 3.5.2) */
+#define PAGANI_STATUS_UNREACHABLE 3  /* finished error alone exceeds the tolerance, or no active region left */
+#define PAGANI_ERR_DIM (-1)          /* dim outside [PAGANI_MIN_DIM, PAGANI_MAX_DIM] */
+#define PAGANI_ERR_INTEGRAND (-2)    /* unknown integrand_id or invalid params */
+#define PAGANI_ERR_TOLERANCE (-3)    /* epsrel <= 0 / NaN, or epsabs < 0 / NaN */
+#define PAGANI_ERR_CUDA (-4)         /* CUDA error or device allocation failure */
+#define PAGANI_ERR_WATCHDOG (-5)     /* a device-side consistency check failed */
+#define PAGANI_ERR_NONFINITE (-6)    /* the integrand produced NaN or Inf */
+#define PAGANI_ERR_CAPACITY (-7)     /* max_regions below the initial uniform split */
+#define PAGANI_ERR_ARGUMENT (-8)     /* other invalid argument (null pointer, size) */
+
+typedef struct {
+  double estimate;        /* v + v_f                                          */
+  double errorest;        /* e + e_f                                          */
+  int32_t status;         /* PAGANI_STATUS_* / PAGANI_ERR_*                   */
+  int32_t iterations;     /* Evaluate passes performed                       */
+  int64_t n_regions;      /* regions evaluated, summed over iterations       */
+  int64_t n_active_last;  /* regions evaluated in the last iteration         */
+  double finished_volume; /* volume of the regions classified finished       */
+} pagani_result;
+
+typedef struct {
+  int32_t relerr_filter;    /* 1 (default): Rel-Err-Classify on; 0 for sign-changing f (Sec. 3.5.1) */
+  int32_t heuristic_filter; /* 1 (default): Threshold-Classify on (Sec. 3.5.2-3.5.3)               */
+  int32_t init_div;         /* divisions per axis of the Uniform-Split; 0 = largest power of two
+                               d >= 2 with d^dim <= 4096 (Sec. 3.1)                                 */
+  int32_t it_max;           /* iteration limit (default 100)                                       */
+  int32_t use_graph;        /* 1 (default): device-resident loop in one CUDA graph; 0: host-driven */
+} pagani_options;
+
+/* One record per iteration (Algorithm 2 scalars after that iteration). */
+typedef struct {
+  int32_t it, trigger, probes, search_ok;
+  int64_t s, n_relerr_active, n_survivors;
+  double v, e, vf, ef, threshold, direction_changes;
+} pagani_trace_record;
+
+/* Fills *opt with the defaults listed above. */
+void pagani_default_options(pagani_options* opt);
+
+/* Integrate family `integrand_id` with parameters `params` (host array,
+ * layout above) over [0,1]^dim to relative tolerance epsrel or absolute
+ * tolerance epsabs (Algorithm 2, Sec. 3.1).  max_regions caps the regions
+ * held in one iteration (memory requirement of Sec. 3.5.2).  Writes *out and
+ * returns out->status.  Uses default options and the library's stream. */
+int pagani_integrate(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
+                     int64_t max_regions, pagani_result* out);
+
+/* As pagani_integrate with explicit options (NULL = defaults), a CUDA stream,
+ * and an optional per-iteration trace: trace (host array of trace_cap
+ * records, may be NULL) receives min(iterations, trace_cap) records. */
+int pagani_integrate_ex(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
+                        int64_t max_regions, const pagani_options* opt, void* cuda_stream, pagani_result* out,
+                        pagani_trace_record* trace, int trace_cap);
+
+/* Allocates (or grows) the library workspace for up to max_regions regions
+ * of dimension dim so that later calls do not allocate (the paper times
+ * integration without workspace set-up, Sec. 4).  Returns 0 or < 0. */
+int pagani_workspace_reserve(int64_t max_regions, int dim);
+
+/* Frees the workspace and every cached CUDA graph.  Returns 0. */
+int pagani_workspace_release(void);
+
+/* Evaluate (Sec. 3.2) on a caller-given list of m boxes: lower and width are
+ * DEVICE arrays in SoA layout [dim][m] (box i spans lower[j*m+i] ..
+ * lower[j*m+i] + width[j*m+i] on axis j).  Writes, per box, the rule
+ * estimate V[i], the null-rule error E[i] (before the two-level refinement)
+ * and the split axis K[i] (fourth differences).  diag (device, may be NULL)
+ * receives, SoA [(8 + dim)][m], the null-rule values N_1..N_4, their noise
+ * floors (values at or below count as zero in the error formula) and the
+ * fourth differences D_0..D_{dim-1}.  params is a host array.  Returns 0 or
+ * < 0. */
+int pagani_evaluate(int dim, int integrand_id, const double* params, int64_t m, const double* lower,
+                    const double* width, double* V, double* E, int32_t* K, double* diag, void* cuda_stream);
+
+/* The rule tables this library generated for dimension dim (host outputs):
+ * radius[5] = generator radii sqrt(l1), sqrt(l2), sqrt(l3), sqrt(lp), sqrt(l0);
+ * weights[9*5] = per generator orbit (centre, l1, l2, l3, lp, l1l1, l1l2,
+ * l1l1l1, l0^n) the basic rule and null rules 1..4 on the unit-volume cube;
+ * counts[9] = orbit sizes.  Host computation only (no GPU needed).  Returns
+ * the number of rule points N(dim), or < 0 on error. */
+int pagani_rule_tables(int dim, double* radius, double* weights, int64_t* counts);
+
+/* Measures this GPU's FP64 FMA throughput with an independent-chain
+ * microbenchmark (used as the roofline denominator of Evaluate).  Writes
+ * TFLOP/s (2 flops per FMA) to *tflops.  Returns 0 or < 0. */
+int pagani_fp64_peak(double* tflops, void* cuda_stream);
+
+/* Human-readable description of the last error on this thread. */
+const char* pagani_last_error(void);
+
+/* Library build identification. */
+const char* pagani_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAGANI_GB300_H */

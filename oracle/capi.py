@@ -37,7 +37,8 @@ def build(force: bool = False) -> str:
 class _Rule(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("G", ctypes.c_int),
                 ("gen", ctypes.POINTER(ctypes.c_double)), ("wts", ctypes.POINTER(ctypes.c_double)),
-                ("a", ctypes.c_double), ("b", ctypes.c_double), ("q", ctypes.c_double)]
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("q", ctypes.c_double),
+                ("count", ctypes.POINTER(ctypes.c_int64))]
 
 
 class _Opt(ctypes.Structure):
@@ -79,9 +80,12 @@ def _rule_struct(n: int):
         w = np.ascontiguousarray(wts, dtype=np.float64)
         a, b = _rule.fourth_difference_offsets()
         q = float(_rule.LP / _rule.L2)
+        _, counts, _, _, _ = _rule.exact_rule(n)
+        c = np.ascontiguousarray(counts, dtype=np.int64)
         r = _Rule(n, g.shape[0], g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                  w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a, b, q)
-        _rule_cache[n] = (r, g, w)
+                  w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a, b, q,
+                  c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        _rule_cache[n] = (r, g, w, c)
     return _rule_cache[n][0]
 
 
@@ -97,7 +101,7 @@ def evaluate(family: int, n: int, params, lower, width, diag: bool = False):
     """Evaluate regions (arrays m x n).  Returns V, E (null-rule error, before
     the two-level refinement) and K; with diag=True also the diagnostic rows
     [N_1..N_4, rounding scales of N_1..N_4, rounding scale of V, D_0..D_{n-1},
-    rounding scales of D_j]."""
+    rounding scales of D_j, noise floors of N_1..N_4]."""
     lib = _load()
     lo = np.ascontiguousarray(lower, dtype=np.float64).reshape(-1, n)
     wd = np.ascontiguousarray(width, dtype=np.float64).reshape(-1, n)
@@ -106,7 +110,7 @@ def evaluate(family: int, n: int, params, lower, width, diag: bool = False):
     V = np.zeros(m)
     E = np.zeros(m)
     K = np.zeros(m, dtype=np.int32)
-    D = np.zeros((m, 9 + 2 * n)) if diag else None
+    D = np.zeros((m, 13 + 2 * n)) if diag else None
     lib.oracle_evaluate(ctypes.byref(_rule_struct(n)), ctypes.c_int(family), _dp(p), ctypes.c_int64(m),
                         _dp(lo), _dp(wd), _dp(V), _dp(E), K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                         _dp(D) if diag else None)

@@ -19,6 +19,10 @@
  *    in as tables from oracle/rule.py; the error from the four null values
  *    N_1..N_4 is: r = max(N_1/N_2, N_2/N_3) (x/0 = inf for x > 0, 0 for x = 0);
  *    err = 10 max(N_k) if r >= 1, 10 r N_1 if 1/2 <= r < 1, 40 r^3 N_1 else.
+ *    A null value N_k no larger than 64 N(n) u vol sum_g |u_kg| M_g (u the
+ *    unit roundoff, M_g the magnitude of orbit sum S_g: |S_g| for the
+ *    positive families, the orbit size for the oscillatory one, |f| <= 1) is
+ *    at the rounding level of its sum and counts as zero.
  *  - Split axis (Sec. 2.2, Sec. 3.2): fourth divided difference per axis,
  *    D_j = |(f(c+a h_j e_j) + f(c-a h_j e_j) - 2 f(c))
  *           - q (f(c+b h_j e_j) + f(c-b h_j e_j) - 2 f(c))|, q = a^2/b^2,
@@ -64,6 +68,7 @@ typedef struct {
   const double *gen;  /* G x n generator magnitudes on [-1,1]^n, row-major */
   const double *wts;  /* G x 5: basic rule, then null rules u_1..u_4 */
   double a, b, q;     /* fourth-difference radii sqrt(lp), sqrt(l2); q = a^2/b^2 */
+  const int64_t *count; /* G orbit sizes */
 } oracle_rule;
 
 typedef struct {
@@ -211,22 +216,33 @@ static void evaluate_region(const oracle_rule *R, int fam, const double *p,
     int64_t cnt;
     Sg[g] = orbit_sum(fam, n, p, R->gen + (size_t)g * n, c, h, &Ag[g], &cnt);
   }
-  double basic = 0.0, basic_abs = 0.0, N[4], Nabs[4];
+  double basic = 0.0, basic_abs = 0.0, N[4], Nabs[4], Nfloor[4], Nused[4];
+  int64_t npts = 0;
   for (int g = 0; g < R->G; ++g) {
     basic += R->wts[g * 5] * Sg[g];
     basic_abs += fabs(R->wts[g * 5]) * Ag[g];
   }
+  for (int g = 0; g < R->G; ++g) npts += R->count ? R->count[g] : 0;
   for (int k = 0; k < 4; ++k) {
-    double s = 0.0, sa = 0.0;
+    double s = 0.0, sa = 0.0, sc = 0.0;
     for (int g = 0; g < R->G; ++g) {
       s += R->wts[g * 5 + 1 + k] * Sg[g];
       sa += fabs(R->wts[g * 5 + 1 + k]) * Ag[g];
+      /* magnitude of the orbit sum: |S_g| = sum |f| for the positive
+       * families; |f| <= 1 bounds it by the orbit size for the oscillatory
+       * one, whose values carry absolute rounding errors */
+      double mag = fam == FAM_OSCILLATORY ? (double)R->count[g] : fabs(Sg[g]);
+      sc += fabs(R->wts[g * 5 + 1 + k]) * mag;
     }
     N[k] = vol * fabs(s);
     Nabs[k] = vol * sa;
+    /* a null value at the rounding level of its own sum carries no
+     * information and counts as zero */
+    Nfloor[k] = 64.0 * (double)npts * 0x1p-53 * (vol * sc);
+    Nused[k] = N[k] <= Nfloor[k] ? 0.0 : N[k];
   }
   *V = vol * basic;
-  *E = null_rule_error(N);
+  *E = null_rule_error(Nused);
 
   /* split axis from fourth divided differences */
   double x[16], D[16], Dabs[16], f0, Dmax = 0.0;
@@ -258,6 +274,7 @@ static void evaluate_region(const oracle_rule *R, int fam, const double *p,
     diag[8] = vol * basic_abs;
     for (int j = 0; j < n; ++j) diag[9 + j] = D[j];
     for (int j = 0; j < n; ++j) diag[9 + n + j] = Dabs[j];
+    for (int t = 0; t < 4; ++t) diag[9 + 2 * n + t] = Nfloor[t];
   }
 }
 
@@ -268,7 +285,7 @@ int oracle_evaluate(const oracle_rule *R, int fam, const double *params,
   for (int64_t i = 0; i < m; ++i) {
     int k;
     evaluate_region(R, fam, params, lower + i * R->n, width + i * R->n, &V[i],
-                    &E[i], &k, diag ? diag + i * (9 + 2 * R->n) : NULL);
+                    &E[i], &k, diag ? diag + i * (13 + 2 * R->n) : NULL);
     K[i] = k;
   }
   return 0;

@@ -1,0 +1,193 @@
+// Device helpers shared by the evaluate kernels and the region-management
+// kernels: compensated sums, block reductions, and the per-iteration decisions
+// of the PAGANI loop (Algorithm 2: termination test, Threshold-Classify
+// trigger; Algorithm 3: one step of the threshold search).
+#pragma once
+#include <cstdint>
+
+#include "pagani_internal.h"
+
+namespace pg {
+
+// Neumaier compensated summation.
+__host__ __device__ __forceinline__ void nadd(NSum& a, double x) {
+  double t = a.s + x;
+  double big = fabs(a.s) >= fabs(x) ? a.s : x;
+  double small = fabs(a.s) >= fabs(x) ? x : a.s;
+  a.c += (big - t) + small;
+  a.s = t;
+}
+__host__ __device__ __forceinline__ NSum ncomb(NSum a, const NSum& b) {
+  nadd(a, b.s);
+  a.c += b.c;
+  return a;
+}
+__host__ __device__ __forceinline__ double nval(const NSum& a) { return a.s + a.c; }
+
+__device__ __forceinline__ NSum shfl_down_nsum(NSum a, int off) {
+  NSum b;
+  b.s = __shfl_down_sync(0xffffffffu, a.s, off);
+  b.c = __shfl_down_sync(0xffffffffu, a.c, off);
+  return b;
+}
+
+// Width 2^-l as an exact double built from its exponent bits (integer ops only).
+__device__ __forceinline__ double pow2_neg(int l) {
+  return __longlong_as_double((long long)(1023 - l) << 52);
+}
+
+// Region error from the four null-rule values (the reading of Sec. 3.2 used
+// throughout): r = max(N1/N2, N2/N3) with x/0 = inf (x > 0) or 0 (x = 0);
+// 10 max(N) if r >= 1, 10 r N1 if 1/2 <= r < 1, 40 r^3 N1 otherwise.  The
+// caller passes N_k = 0 for values at the rounding level of their own sums.
+__device__ __forceinline__ double ratio_or(double x, double y) {
+  return y > 0.0 ? x / y : (x > 0.0 ? __longlong_as_double(0x7ff0000000000000LL) : 0.0);
+}
+__device__ __forceinline__ double null_error(double n1, double n2, double n3, double n4) {
+  double r = fmax(ratio_or(n1, n2), ratio_or(n2, n3));
+  if (r >= 1.0) return 10.0 * fmax(fmax(n1, n2), fmax(n3, n4));
+  if (r >= 0.5) return 10.0 * r * n1;
+  return 40.0 * r * r * r * n1;
+}
+
+// Two-level error refinement of a sibling pair (Sec. 3.2, reading in the design doc).
+__device__ __forceinline__ void two_level(double VL, double VR, double Vpar, double& EL, double& ER) {
+  double delta = fabs(VL + VR - Vpar) / 4.0;
+  double S = EL + ER;
+  if (S > 0.0) {
+    double c = 1.0 + 2.0 * delta / S;
+    EL = EL * c + delta;
+    ER = ER * c + delta;
+  } else {
+    EL += delta;
+    ER += delta;
+  }
+}
+
+// Rel-Err-Classify (Sec. 3.5.1): active unless E <= tau_rel |V|.
+__device__ __forceinline__ bool relerr_active(double V, double E, double tau_rel, int enabled) {
+  return enabled ? !(E <= tau_rel * fabs(V)) : true;
+}
+
+// Final classification of a region after the optional threshold search.
+__device__ __forceinline__ bool final_active(double V, double E, const Ctrl& c) {
+  bool a = relerr_active(V, E, c.tau_rel, c.relerr_filter);
+  if (c.search_ok) a = a && !(E < c.t);
+  return a;
+}
+
+// Last-block election: every block calls this after publishing its partial;
+// exactly one (the last to arrive) gets true and may read all partials.
+__device__ __forceinline__ bool last_block_arrived(unsigned int* ticket) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(ticket, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    if (threadIdx.x == 0) *ticket = 0u;  // reset for the next launch
+  }
+  return is_last;
+}
+
+__device__ __forceinline__ void set_cond(int use_graph, cudaGraphConditionalHandle h, unsigned int v) {
+  if (use_graph) cudaGraphSetConditional(h, v);
+}
+
+// Decisions after Evaluate, Two-Level-Error, Rel-Err-Classify and the sums
+// (Algorithm 2, from the termination test to the Threshold-Classify trigger).
+// Runs on one thread.  Returns 1 if a threshold search starts.
+__device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long long n_rel, double emin,
+                                              double emax, int nonfinite, TraceRec* trace, int trace_cap) {
+  c.v = v;
+  c.e = e;
+  c.n_rel = n_rel;
+  c.emin = emin;
+  c.emax = emax;
+  c.n_regions_total += c.s;
+  c.search = 0;
+  c.search_ok = 0;
+  c.trigger = 0;
+  c.probes = 0;
+  c.dir_changes = 0;
+  c.t = 0.0;
+  if (nonfinite || !isfinite(v) || !isfinite(e)) {
+    c.status = -6;
+    c.done = 1;
+    c.estimate = v + c.vf;
+    c.errorest = e + c.ef;
+    return 0;
+  }
+  TraceRec tr = {};
+  tr.it = c.it;
+  tr.s = c.s;
+  tr.v = v;
+  tr.e = e;
+  tr.vf = c.vf;
+  tr.ef = c.ef;
+  tr.n_relerr_active = n_rel;
+  bool conv = (e + c.ef) / fabs(v + c.vf) <= c.tau_rel || e + c.ef <= c.tau_abs;
+  if (conv || c.it >= c.it_max) {
+    c.status = conv ? 0 : 1;
+    c.done = 1;
+    c.estimate = v + c.vf;
+    c.errorest = e + c.ef;
+    if (c.trace_on && c.it - 1 < trace_cap) trace[c.it - 1] = tr;
+    return 0;
+  }
+  double v_tot = v + c.vf;
+  int trig = 0;
+  if (c.heuristic_filter) {
+    if (c.it >= 2 && fabs(v_tot - c.v_tot_prev) <= c.tau_rel * fabs(v_tot)) trig |= 1;
+    if (2 * n_rel > c.max_regions) trig |= 2;
+  }
+  c.v_tot_prev = v_tot;
+  c.trigger = trig;
+  tr.trigger = trig;
+  if (c.trace_on && c.it - 1 < trace_cap) trace[c.it - 1] = tr;
+  c.search_cont = 0;
+  if (!trig) return 0;
+  // Algorithm 3 set-up: P_max = .25, e_b = e_tot - |v_tot| tau_rel, t = e_it / s_it
+  c.Pmax = 0.25;
+  c.e_b = (e + c.ef) - fabs(v_tot) * c.tau_rel;
+  c.t = e / (double)c.s;
+  c.last_dir = 0;
+  if (!(c.e_b > 0.0)) return 0;
+  c.search = 1;
+  c.search_cont = 1;
+  return 1;
+}
+
+// One step of Algorithm 3 after a probe with threshold c.t counted
+// n_active candidate actives whose errors sum to sum_ae.  Returns 1 if
+// another probe is needed.
+__device__ inline int threshold_step(Ctrl& c, long long n_active, double sum_ae) {
+  c.probes += 1;
+  long long s_abar = c.s - n_active;
+  int dir;
+  if ((double)s_abar > 0.5 * (double)c.s) {       // memory requirement
+    double e_abar = c.e - sum_ae;
+    if (e_abar <= c.Pmax * c.e_b) {               // accuracy requirement
+      c.search_ok = 1;
+      return 0;
+    }
+    dir = -1;
+  } else {
+    dir = +1;
+  }
+  if (c.last_dir != 0 && dir != c.last_dir) {
+    c.dir_changes += 1;
+    c.Pmax = fmin(c.Pmax + 0.10, 0.95);
+  }
+  c.last_dir = dir;
+  if (c.dir_changes >= 10 || c.probes >= 64) return 0;  // unsuccessful filtering
+  if (dir > 0) c.t = c.t + (c.emax - c.t) / 2.0;
+  else c.t = c.t - (c.t - c.emin) / 2.0;
+  return 1;
+}
+
+}  // namespace pg

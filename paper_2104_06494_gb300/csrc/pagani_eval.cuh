@@ -1,0 +1,562 @@
+// Evaluate (Algorithm 2, Sec. 3.2): the degree-9 rule sum, the four null-rule
+// values, the fourth-difference split axis, and, in the loop kernel, the
+// two-level error, Rel-Err-Classify and the block partial sums of V and E.
+//
+// GB300 mapping.  FP64 issue rate is the bound (about 2 FMA/clk/SM), so the
+// kernel spends FP64 instructions only where the arithmetic needs them:
+//  * one thread evaluates one sibling pair (regions 2p and 2p+1).  The two
+//    boxes differ along one axis, so the per-axis factor table (11 coordinate
+//    codes x n axes, in shared memory) is built once and patched on one axis;
+//  * each rule point's value is the product (or sum, for the corner peak) of
+//    its per-axis factors, formed from shared prefix/suffix partial products
+//    so a point costs one or two FP64 multiplies instead of n;
+//  * the nine generator sums are accumulated per thread and weighted once
+//    per region (rule and null rules);
+//  * index arithmetic, table addressing and the rest run on the integer pipes.
+#pragma once
+#include <cstdint>
+
+#include "pagani_device.cuh"
+
+namespace pg {
+
+// ------------------------------------------------------------------ families
+// A family supplies: the element type T of its per-axis factors, the monoid
+// (mul), the value of f at a point from its last two factors (last), the
+// starting element (base), and the per-axis factor at coordinate x.
+
+struct RealProduct {
+  typedef double T;
+  static constexpr bool kUnitBounded = false;  // positive values: |S_g| = sum |f|
+  __device__ static __forceinline__ T mul(T a, T b) { return a * b; }
+  __device__ static __forceinline__ double last(T a, T b) { return a * b; }
+  __device__ static __forceinline__ double val(T a) { return a; }
+};
+
+struct ProductPeak : RealProduct {  // prod_j 1/(c_j^-2 + (x_j - w_j)^2)
+  static constexpr int kFamily = kFamProductPeak;
+  struct Ax { double cm2, w; };
+  __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
+    Ax a;
+    a.cm2 = 1.0 / (p.p0[j] * p.p0[j]);
+    a.w = p.p1[j];
+    return a;
+  }
+  __device__ static __forceinline__ T base(const IntegrandParams&) { return 1.0; }
+  __device__ static __forceinline__ T factor(const Ax& a, double x) {
+    double t = x - a.w;
+    return 1.0 / fma(t, t, a.cm2);
+  }
+};
+
+struct Gaussian : RealProduct {  // exp(-sum_j a_j^2 (x_j - w_j)^2)
+  static constexpr int kFamily = kFamGaussian;
+  struct Ax { double a, w; };
+  __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
+    Ax a;
+    a.a = p.p0[j];
+    a.w = p.p1[j];
+    return a;
+  }
+  __device__ static __forceinline__ T base(const IntegrandParams&) { return 1.0; }
+  __device__ static __forceinline__ T factor(const Ax& a, double x) {
+    double u = a.a * (x - a.w);
+    return exp(-(u * u));
+  }
+};
+
+struct C0Fam : RealProduct {  // exp(-sum_j a_j |x_j - w_j|)
+  static constexpr int kFamily = kFamC0;
+  struct Ax { double a, w; };
+  __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
+    Ax a;
+    a.a = p.p0[j];
+    a.w = p.p1[j];
+    return a;
+  }
+  __device__ static __forceinline__ T base(const IntegrandParams&) { return 1.0; }
+  __device__ static __forceinline__ T factor(const Ax& a, double x) { return exp(-(a.a * fabs(x - a.w))); }
+};
+
+struct Oscillatory {  // cos(2 pi u + sum_j a_j x_j) = Re[e^{2 pi i u} prod_j e^{i a_j x_j}]
+  static constexpr int kFamily = kFamOscillatory;
+  static constexpr bool kUnitBounded = true;  // signed values with |f| <= 1
+  typedef double2 T;
+  struct Ax { double a; };
+  __device__ static __forceinline__ T mul(T a, T b) {
+    T r;
+    r.x = fma(a.x, b.x, -(a.y * b.y));
+    r.y = fma(a.x, b.y, a.y * b.x);
+    return r;
+  }
+  __device__ static __forceinline__ double last(T a, T b) { return fma(a.x, b.x, -(a.y * b.y)); }
+  __device__ static __forceinline__ double val(T a) { return a.x; }
+  __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
+    Ax a;
+    a.a = p.p0[j];
+    return a;
+  }
+  __device__ static __forceinline__ T base(const IntegrandParams& p) {
+    T z;
+    sincospi(2.0 * p.u, &z.y, &z.x);
+    return z;
+  }
+  __device__ static __forceinline__ T factor(const Ax& a, double x) {
+    T z;
+    sincos(a.a * x, &z.y, &z.x);
+    return z;
+  }
+};
+
+template <int N>
+struct CornerPeak {  // (1 + sum_j a_j x_j)^-(N+1): per-axis terms add up
+  static constexpr int kFamily = kFamCornerPeak;
+  static constexpr bool kUnitBounded = false;
+  typedef double T;
+  struct Ax { double a; };
+  __device__ static __forceinline__ T mul(T a, T b) { return a + b; }
+  __device__ static __forceinline__ double outer(double s) {
+    double r = 1.0 / s;
+    double y = 1.0;
+    double pw = r;
+    // r^(N+1) by binary powering (exponent known at compile time)
+#pragma unroll
+    for (int e = N + 1; e > 0; e >>= 1) {
+      if (e & 1) y *= pw;
+      if (e > 1) pw *= pw;
+    }
+    return y;
+  }
+  __device__ static __forceinline__ double last(T a, T b) { return outer(a + b); }
+  __device__ static __forceinline__ double val(T a) { return outer(a); }
+  __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
+    Ax a;
+    a.a = p.p0[j];
+    return a;
+  }
+  __device__ static __forceinline__ T base(const IntegrandParams&) { return 1.0; }
+  __device__ static __forceinline__ T factor(const Ax& a, double x) { return a.a * x; }
+};
+
+// Offset g of a coordinate code on [-1, 1] (radius order: l1, l2, l3, lp, l0).
+__device__ __forceinline__ double code_offset(const EvalRule& R, int code) {
+  if (code == kC0) return 0.0;
+  double r = R.radius[(code - 1) >> 1];
+  return (code & 1) ? r : -r;
+}
+
+// Build the 11 factor entries of one axis (centre c, half-width h).
+template <class F, int N, int THREADS>
+__device__ __forceinline__ void build_axis(typename F::T* tab, const EvalRule& R, const typename F::Ax& ax,
+                                           double c, double h, int j) {
+#pragma unroll
+  for (int code = 0; code < kCodes; ++code) {
+    double x = fma(h, code_offset(R, code), c);
+    tab[(code * N + j) * THREADS] = F::factor(ax, x);
+  }
+}
+
+// The nine generator sums S[g] = sum over the orbit of g of f, and the
+// fourth differences D[j], for one region whose factor table is `tab`.
+template <class F, int N, int THREADS>
+__device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab, typename F::T base, double q,
+                                          double (&S)[kNumGen], double (&D)[N]) {
+  typedef typename F::T T;
+#define PG_TB(code, j) tab[((code) * N + (j)) * THREADS]
+  // prefix products pre[j] = base * prod_{m<j} T0_m, suffix suf[j] = prod_{m>=j} T0_m
+  T pre[N + 1];
+  T suf[N + 1];
+  pre[0] = base;
+#pragma unroll
+  for (int j = 0; j < N; ++j) pre[j + 1] = F::mul(pre[j], PG_TB(kC0, j));
+  suf[N - 1] = PG_TB(kC0, N - 1);
+#pragma unroll
+  for (int j = N - 2; j >= 1; --j) suf[j] = F::mul(PG_TB(kC0, j), suf[j + 1]);
+
+  const double f0 = F::val(pre[N]);
+  S[kGenCentre] = f0;
+#pragma unroll
+  for (int g = 1; g < kNumGen; ++g) S[g] = 0.0;
+
+  // one-axis generators and the fourth differences
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    T Q = (j == N - 1) ? pre[N - 1] : F::mul(pre[j], suf[j + 1]);
+    double p1 = F::last(Q, PG_TB(kR1P, j)), m1 = F::last(Q, PG_TB(kR1M, j));
+    double p2 = F::last(Q, PG_TB(kR2P, j)), m2 = F::last(Q, PG_TB(kR2M, j));
+    double p3 = F::last(Q, PG_TB(kR3P, j)), m3 = F::last(Q, PG_TB(kR3M, j));
+    double pp = F::last(Q, PG_TB(kRpP, j)), mp = F::last(Q, PG_TB(kRpM, j));
+    S[kGenL1] += p1 + m1;
+    S[kGenL2] += p2 + m2;
+    S[kGenL3] += p3 + m3;
+    S[kGenLp] += pp + mp;
+    D[j] = fabs((pp + mp - 2.0 * f0) - q * (p2 + m2 - 2.0 * f0));
+  }
+
+  // axis pairs j < k: Q_jk = pre[j] * prod_{j<m<k} T0_m * suf[k+1]
+#pragma unroll
+  for (int j = 0; j < N - 1; ++j) {
+    T PM = pre[j];
+#pragma unroll
+    for (int k = j + 1; k < N; ++k) {
+      if (k > j + 1) PM = F::mul(PM, PG_TB(kC0, k - 1));
+      T Q = (k == N - 1) ? PM : F::mul(PM, suf[k + 1]);
+      T a1p = F::mul(Q, PG_TB(kR1P, j)), a1m = F::mul(Q, PG_TB(kR1M, j));
+      T a2p = F::mul(Q, PG_TB(kR2P, j)), a2m = F::mul(Q, PG_TB(kR2M, j));
+      const T b1p = PG_TB(kR1P, k), b1m = PG_TB(kR1M, k);
+      const T b2p = PG_TB(kR2P, k), b2m = PG_TB(kR2M, k);
+      S[kGenL1L1] += F::last(a1p, b1p) + F::last(a1p, b1m) + F::last(a1m, b1p) + F::last(a1m, b1m);
+      S[kGenL1L2] += F::last(a1p, b2p) + F::last(a1p, b2m) + F::last(a1m, b2p) + F::last(a1m, b2m) +
+                     F::last(a2p, b1p) + F::last(a2p, b1m) + F::last(a2m, b1p) + F::last(a2m, b1m);
+    }
+  }
+
+  // axis triples j < k < l at l1: Q = pre[j] * mid(j,k) * mid(k,l) * suf[l+1]
+  if (N >= 3) {
+#pragma unroll
+    for (int j = 0; j < N - 2; ++j) {
+      T PM1 = pre[j];
+#pragma unroll
+      for (int k = j + 1; k < N - 1; ++k) {
+        if (k > j + 1) PM1 = F::mul(PM1, PG_TB(kC0, k - 1));
+        T aj[2] = {F::mul(PM1, PG_TB(kR1P, j)), F::mul(PM1, PG_TB(kR1M, j))};
+        T ajk[4] = {F::mul(aj[0], PG_TB(kR1P, k)), F::mul(aj[0], PG_TB(kR1M, k)),
+                    F::mul(aj[1], PG_TB(kR1P, k)), F::mul(aj[1], PG_TB(kR1M, k))};
+        T MID = pre[0];  // identity placeholder until the first middle factor
+        bool mid_id = true;
+#pragma unroll
+        for (int l = k + 1; l < N; ++l) {
+          if (l > k + 1) {
+            MID = mid_id ? PG_TB(kC0, l - 1) : F::mul(MID, PG_TB(kC0, l - 1));
+            mid_id = false;
+          }
+          T C;
+          bool c_id;
+          if (l == N - 1) {
+            C = MID;
+            c_id = mid_id;
+          } else {
+            C = mid_id ? suf[l + 1] : F::mul(MID, suf[l + 1]);
+            c_id = false;
+          }
+          const T tp = PG_TB(kR1P, l), tm = PG_TB(kR1M, l);
+#pragma unroll
+          for (int s4 = 0; s4 < 4; ++s4) {
+            T B = c_id ? ajk[s4] : F::mul(ajk[s4], C);
+            S[kGenL1L1L1] += F::last(B, tp) + F::last(B, tm);
+          }
+        }
+      }
+    }
+  }
+
+  // every axis at l0 (2^N sign vertices): split the axes into halves
+  {
+    constexpr int H1 = N / 2;
+    constexpr int H2 = N - H1;
+    T Bv[1 << H2];
+    Bv[0] = PG_TB(kR0P, H1);
+    Bv[1] = PG_TB(kR0M, H1);
+#pragma unroll
+    for (int t = 1; t < H2; ++t) {
+      const T fp = PG_TB(kR0P, H1 + t), fm = PG_TB(kR0M, H1 + t);
+#pragma unroll
+      for (int s2 = (1 << t) - 1; s2 >= 0; --s2) {
+        Bv[2 * s2 + 1] = F::mul(Bv[s2], fm);
+        Bv[2 * s2] = F::mul(Bv[s2], fp);
+      }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int s1 = 0; s1 < (1 << H1); ++s1) {
+      T Av = base;
+#pragma unroll
+      for (int t = 0; t < H1; ++t) Av = F::mul(Av, ((s1 >> t) & 1) ? PG_TB(kR0M, t) : PG_TB(kR0P, t));
+#pragma unroll
+      for (int s2 = 0; s2 < (1 << H2); ++s2) acc += F::last(Av, Bv[s2]);
+    }
+    S[kGenL0All] = acc;
+  }
+#undef PG_TB
+}
+
+// Rule, null rules, error and split axis of one region from its sums.
+// UNIT: the integrand is signed with |f| <= 1, so the magnitude of an orbit
+// sum is bounded by the orbit size; otherwise f > 0 and it is |S_g|.
+template <int N, bool UNIT>
+__device__ __forceinline__ void region_epilogue(const EvalRule& R, const double (&S)[kNumGen], const double (&D)[N],
+                                                double vol, const double (&width)[N], double& V, double& E, int& K,
+                                                double* nk_out) {
+  double b = 0.0, u[4] = {0.0, 0.0, 0.0, 0.0}, sc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int g = 0; g < kNumGen; ++g) {
+    b = fma(R.w[g][0], S[g], b);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      u[k] = fma(R.w[g][1 + k], S[g], u[k]);
+      sc[k] = fma(fabs(R.w[g][1 + k]), UNIT ? R.cnt[g] : fabs(S[g]), sc[k]);
+    }
+  }
+  V = vol * b;
+  // null values at the rounding level of their own sums count as zero
+  double nk[4], nu[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    nk[k] = vol * fabs(u[k]);
+    const double floor_k = R.noise * (vol * sc[k]);
+    nu[k] = nk[k] <= floor_k ? 0.0 : nk[k];
+    if (nk_out) {
+      nk_out[k] = nk[k];
+      nk_out[4 + k] = floor_k;
+    }
+  }
+  E = null_error(nu[0], nu[1], nu[2], nu[3]);
+  double dmax = 0.0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) dmax = fmax(dmax, D[j]);
+  int k = 0;
+  if (dmax > 0.0) {
+    const double thr = (1.0 - 1e-10) * dmax;
+    k = N - 1;
+#pragma unroll
+    for (int j = N - 1; j >= 0; --j)
+      if (D[j] >= thr) k = j;
+  } else {
+#pragma unroll
+    for (int j = 1; j < N; ++j)
+      if (width[j] > width[k]) k = j;
+  }
+  K = k;
+}
+
+// ------------------------------------------------------------- loop kernel
+// One thread per sibling pair (2p, 2p+1) of the current pool buffer.
+template <class F, int N, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, const LoopArgs A) {
+  typedef typename F::T T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
+
+  Ctrl& c = *A.ctrl;
+  const int64_t s = c.s;
+  const int it = c.it;
+  const int buf = (it - 1) & 1;
+  const int64_t cap = A.pool.cap;
+  const double* __restrict__ lower = A.pool.lower + (size_t)buf * N * cap;
+  const uint8_t* __restrict__ level = A.pool.level + (size_t)buf * N * cap;
+  const double tau_rel = c.tau_rel;
+  const int relerr = c.relerr_filter;
+  const IntegrandParams prm = *A.prm;
+  const T base = F::base(prm);
+
+  NSum sv = {0.0, 0.0}, se = {0.0, 0.0};
+  double emin = __longlong_as_double(0x7ff0000000000000LL), emax = -emin;
+  long long nrel = 0;
+  int nonfinite = 0;
+
+  const int64_t npairs = s >> 1;
+  for (int64_t p = (int64_t)blockIdx.x * THREADS + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * THREADS) {
+    const int64_t iL = 2 * p;
+    double loL[N], loR[N], wL[N], wR[N];
+    int lvL = 0, lvR = 0, diff_axis = -1;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const double2 lo2 = *reinterpret_cast<const double2*>(lower + (size_t)j * cap + iL);
+      const uchar2 lv2 = *reinterpret_cast<const uchar2*>(level + (size_t)j * cap + iL);
+      loL[j] = lo2.x;
+      loR[j] = lo2.y;
+      wL[j] = pow2_neg(lv2.x);
+      wR[j] = pow2_neg(lv2.y);
+      lvL += lv2.x;
+      lvR += lv2.y;
+      if (lo2.x != lo2.y || lv2.x != lv2.y) diff_axis = j;
+    }
+    // factor table of the left region
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const double h = 0.5 * wL[j];
+      build_axis<F, N, THREADS>(tab, R, F::axis(prm, j), loL[j] + h, h, j);
+    }
+    double S[kNumGen], D[N];
+    double VL, EL, VR, ER;
+    int KL, KR;
+    rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
+    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL), wL, VL, EL, KL, nullptr);
+    // patch the one axis where the right sibling differs
+    if (diff_axis >= 0) {
+      double lo = 0.0, w = 1.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+        if (j == diff_axis) { lo = loR[j]; w = wR[j]; }
+      const double h = 0.5 * w;
+      const typename F::Ax ax = F::axis(prm, diff_axis);
+#pragma unroll
+      for (int code = 0; code < kCodes; ++code)
+        tab[(code * N + diff_axis) * THREADS] = F::factor(ax, fma(h, code_offset(R, code), lo + h));
+    }
+    rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
+    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR), wR, VR, ER, KR, nullptr);
+
+    if (it > 1) two_level(VL, VR, A.pool.Vp[p], EL, ER);
+
+    *reinterpret_cast<double2*>(A.pool.V + iL) = make_double2(VL, VR);
+    *reinterpret_cast<double2*>(A.pool.E + iL) = make_double2(EL, ER);
+    *reinterpret_cast<uchar2*>(A.pool.K + iL) = make_uchar2((unsigned char)KL, (unsigned char)KR);
+
+    nadd(sv, VL);
+    nadd(sv, VR);
+    nadd(se, EL);
+    nadd(se, ER);
+    emin = fmin(emin, fmin(EL, ER));
+    emax = fmax(emax, fmax(EL, ER));
+    nrel += relerr_active(VL, EL, tau_rel, relerr) + relerr_active(VR, ER, tau_rel, relerr);
+    if (!isfinite(VL) || !isfinite(VR) || !isfinite(EL) || !isfinite(ER)) nonfinite = 1;
+  }
+
+  // block reduction of the partials (fixed tree order: deterministic)
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sv = ncomb(sv, shfl_down_nsum(sv, off));
+    se = ncomb(se, shfl_down_nsum(se, off));
+    emin = fmin(emin, __shfl_down_sync(0xffffffffu, emin, off));
+    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, off));
+    nrel += __shfl_down_sync(0xffffffffu, nrel, off);
+    nonfinite |= __shfl_down_sync(0xffffffffu, nonfinite, off);
+  }
+  __shared__ EvalPartial wp[THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    wp[warp].v = sv;
+    wp[warp].e = se;
+    wp[warp].emin = emin;
+    wp[warp].emax = emax;
+    wp[warp].n_rel = nrel;
+    wp[warp].nonfinite = nonfinite;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    EvalPartial bp = wp[0];
+    for (int w = 1; w < THREADS / 32; ++w) {
+      bp.v = ncomb(bp.v, wp[w].v);
+      bp.e = ncomb(bp.e, wp[w].e);
+      bp.emin = fmin(bp.emin, wp[w].emin);
+      bp.emax = fmax(bp.emax, wp[w].emax);
+      bp.n_rel += wp[w].n_rel;
+      bp.nonfinite |= wp[w].nonfinite;
+    }
+    A.eval_part[blockIdx.x] = bp;
+  }
+  if (!last_block_arrived(&c.ticket_eval)) return;
+  if (threadIdx.x == 0) {
+    EvalPartial tot = A.eval_part[0];
+    for (unsigned b = 1; b < gridDim.x; ++b) {
+      const EvalPartial& bp = A.eval_part[b];
+      tot.v = ncomb(tot.v, bp.v);
+      tot.e = ncomb(tot.e, bp.e);
+      tot.emin = fmin(tot.emin, bp.emin);
+      tot.emax = fmax(tot.emax, bp.emax);
+      tot.n_rel += bp.n_rel;
+      tot.nonfinite |= bp.nonfinite;
+    }
+    int search = finalize_iteration_head(c, nval(tot.v), nval(tot.e), tot.n_rel, tot.emin, tot.emax,
+                                         tot.nonfinite, A.trace, A.trace_cap);
+    set_cond(A.use_graph, A.h_probe, (unsigned)search);
+    __threadfence();
+  }
+}
+
+// --------------------------------------------------------- standalone kernel
+// Evaluates a caller-given list of boxes (lower, width SoA, n x m) with the
+// null-rule error (no two-level refinement); pairs (2i, 2i+1) share a thread.
+template <class F, int N, int THREADS, bool DIAG>
+__global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule R, const StandaloneArgs A) {
+  typedef typename F::T T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
+  const IntegrandParams prm = *A.prm;
+  const T base = F::base(prm);
+  const int64_t m = A.m;
+  const int64_t npairs = (m + 1) >> 1;
+  for (int64_t p = (int64_t)blockIdx.x * THREADS + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * THREADS) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int64_t i = 2 * p + side;
+      if (i >= m) break;
+      double lo[N], w[N], vol = 1.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        lo[j] = A.lower[(size_t)j * m + i];
+        w[j] = A.width[(size_t)j * m + i];
+        vol *= w[j];
+      }
+      // the right box reuses the left box's entries on every axis it shares
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        bool same = false;
+        if (side == 1) same = (lo[j] == A.lower[(size_t)j * m + i - 1]) && (w[j] == A.width[(size_t)j * m + i - 1]);
+        if (!same) {
+          const double h = 0.5 * w[j];
+          build_axis<F, N, THREADS>(tab, R, F::axis(prm, j), lo[j] + h, h, j);
+        }
+      }
+      double S[kNumGen], D[N], V, E, nk[8];
+      int K;
+      rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
+      region_epilogue<N, F::kUnitBounded>(R, S, D, vol, w, V, E, K, nk);
+      A.V[i] = V;
+      A.E[i] = E;
+      A.K[i] = K;
+      if (DIAG) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) A.diag[(size_t)t * m + i] = nk[t];
+#pragma unroll
+        for (int j = 0; j < N; ++j) A.diag[(size_t)(8 + j) * m + i] = D[j];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <class F, int N, int THREADS>
+cudaError_t launch_loop(const EvalRule& R, const LoopArgs& A, int grid, int block, size_t smem, cudaStream_t st) {
+  k_evaluate_loop<F, N, THREADS><<<grid, block, smem, st>>>(R, A);
+  return cudaGetLastError();
+}
+template <class F, int N, int THREADS, bool DIAG>
+cudaError_t launch_standalone(const EvalRule& R, const StandaloneArgs& A, int grid, int block, size_t smem,
+                              cudaStream_t st) {
+  k_evaluate_standalone<F, N, THREADS, DIAG><<<grid, block, smem, st>>>(R, A);
+  return cudaGetLastError();
+}
+
+template <template <int> class FamOf, int THREADS>
+FamilyKernels make_family_kernels() {
+  FamilyKernels k = {};
+  k.threads = THREADS;
+#define PG_SET(NN)                                                                              \
+  k.loop[NN] = &launch_loop<FamOf<NN>, NN, THREADS>;                                            \
+  k.standalone[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, false>;                         \
+  k.standalone_diag[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, true>;                     \
+  k.loop_fn[NN] = (const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS>;                        \
+  k.table_bytes_per_thread[NN] = (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN);           \
+  cudaFuncSetAttribute((const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS>,                   \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
+  cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, false>,      \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
+  cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, true>,       \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));
+  PG_SET(2) PG_SET(3) PG_SET(4) PG_SET(5) PG_SET(6) PG_SET(7) PG_SET(8)
+#undef PG_SET
+  return k;
+}
+
+template <class F>
+struct Fixed {
+  template <int N>
+  using type = F;
+};
+
+}  // namespace pg

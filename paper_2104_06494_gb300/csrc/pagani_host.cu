@@ -1,0 +1,906 @@
+// Host side of the GB300 PAGANI engine: the region-management kernels of
+// Algorithm 2 (Uniform-Split, the Threshold-Classify probes, the finished
+// accumulation with the survivor count and its scan, and Filter + parent
+// update + Split fused into one compaction kernel), the workspace, the
+// device-resident loop as one CUDA graph with conditional WHILE nodes, and
+// the C ABI declared in include/pagani.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pagani.h"
+#include "pagani_device.cuh"
+#include "pagani_internal.h"
+
+namespace pg {
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+// ------------------------------------------------------ block-level helpers
+template <int THREADS>
+__device__ __forceinline__ long long block_sum_ll(long long x, long long* sh) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  long long t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < THREADS / 32; ++w) t += sh[w];
+  return t;  // valid on thread 0
+}
+
+template <int THREADS>
+__device__ __forceinline__ NSum block_nsum(NSum a, NSum* sh) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a = ncomb(a, shfl_down_nsum(a, off));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = a;
+  __syncthreads();
+  NSum t = {0.0, 0.0};
+  if (threadIdx.x == 0) {
+    t = sh[0];
+    for (int w = 1; w < THREADS / 32; ++w) t = ncomb(t, sh[w]);
+  }
+  return t;  // valid on thread 0
+}
+
+// Exclusive scan of one flag per thread across the block, in thread order.
+// Returns this thread's rank among the set flags; *total = number set.
+template <int THREADS>
+__device__ __forceinline__ int block_rank(bool flag, int* sh, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned ballot = __ballot_sync(0xffffffffu, flag);
+  const int within = __popc(ballot & ((1u << lane) - 1u));
+  __syncthreads();
+  if (lane == 0) sh[warp] = __popc(ballot);
+  __syncthreads();
+  int before = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < THREADS / 32; ++w) {
+    const int v = sh[w];
+    before += (w < warp) ? v : 0;
+    tot += v;
+  }
+  *total = tot;
+  return before + within;
+}
+
+// ------------------------------------------------------------ Uniform-Split
+// Region i of the d^n grid; axis n-1 varies fastest (Sec. 3.1).
+__global__ void k_uniform_split(Pool P, int d, int log2d, int64_t s0) {
+  const int n = P.n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s0; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = i;
+    for (int j = n - 1; j >= 0; --j) {
+      const int digit = (int)(r % d);
+      r /= d;
+      P.lower[(size_t)j * P.cap + i] = (double)digit / (double)d;
+      P.level[(size_t)j * P.cap + i] = (uint8_t)log2d;
+    }
+  }
+}
+
+// ------------------------------------------------- Threshold-Classify probe
+// Counts the candidate actives under threshold t (rel-err active and
+// E >= t) and sums their errors; the last block takes one step of Algorithm 3.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
+  Ctrl& c = *A.ctrl;
+  const int64_t s = c.s;
+  const double t = c.t, tau = c.tau_rel;
+  const int relerr = c.relerr_filter;
+  const double* __restrict__ V = A.pool.V;
+  const double* __restrict__ E = A.pool.E;
+  NSum sa = {0.0, 0.0};
+  long long na = 0;
+  for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < s; i += (int64_t)gridDim.x * THREADS) {
+    const double e = E[i];
+    if (relerr_active(V[i], e, tau, relerr) && !(e < t)) {
+      ++na;
+      nadd(sa, e);
+    }
+  }
+  __shared__ NSum shn[THREADS / 32];
+  __shared__ long long shl[THREADS / 32];
+  NSum bs = block_nsum<THREADS>(sa, shn);
+  long long bn = block_sum_ll<THREADS>(na, shl);
+  if (threadIdx.x == 0) {
+    A.probe_part[blockIdx.x].ea = bs;
+    A.probe_part[blockIdx.x].n_active = bn;
+  }
+  if (!last_block_arrived(&c.ticket_probe)) return;
+  if (threadIdx.x == 0) {
+    NSum tot = A.probe_part[0].ea;
+    long long n = A.probe_part[0].n_active;
+    for (unsigned b = 1; b < gridDim.x; ++b) {
+      tot = ncomb(tot, A.probe_part[b].ea);
+      n += A.probe_part[b].n_active;
+    }
+    const int cont = threshold_step(c, n, nval(tot));
+    c.search_cont = cont;
+    set_cond(A.use_graph, A.h_probe, (unsigned)cont);
+    __threadfence();
+  }
+}
+
+// ------------------------------------------- finished sums + survivor count
+// Per tile of kTile regions: the number of survivors under the final
+// classification.  Per block: sum V.A, sum E.A and the finished volume.  The
+// last block scans the tile counts and takes the decisions that follow
+// Threshold-Classify in Algorithm 2 (v_f, e_f, the memory check).
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
+  Ctrl& c = *A.ctrl;
+  if (c.done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(A.use_graph, A.h_main, 0u);
+    return;
+  }
+  constexpr int TILE = THREADS * ITEMS;
+  const int64_t s = c.s;
+  const int n = A.pool.n;
+  const int64_t cap = A.pool.cap;
+  const uint8_t* __restrict__ level = A.pool.level + (size_t)((c.it - 1) & 1) * n * cap;
+  const double* __restrict__ V = A.pool.V;
+  const double* __restrict__ E = A.pool.E;
+  const int64_t ntiles = (s + TILE - 1) / TILE;
+  __shared__ long long shl[THREADS / 32];
+  __shared__ NSum shn[THREADS / 32];
+  NSum va = {0.0, 0.0}, ea = {0.0, 0.0}, fv = {0.0, 0.0};
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    long long cnt = 0;
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
+      if (i < s) {
+        const double v = V[i], e = E[i];
+        if (final_active(v, e, c)) {
+          ++cnt;
+          nadd(va, v);
+          nadd(ea, e);
+        } else {
+          int L = 0;
+          for (int j = 0; j < n; ++j) L += level[(size_t)j * cap + i];
+          nadd(fv, pow2_neg(L));
+        }
+      }
+    }
+    const long long tc = block_sum_ll<THREADS>(cnt, shl);
+    if (threadIdx.x == 0) A.pool.tile_count[tile] = tc;
+  }
+  NSum bva = block_nsum<THREADS>(va, shn);
+  NSum bea = block_nsum<THREADS>(ea, shn);
+  NSum bfv = block_nsum<THREADS>(fv, shn);
+  if (threadIdx.x == 0) {
+    A.count_part[blockIdx.x].va = bva;
+    A.count_part[blockIdx.x].ea = bea;
+    A.count_part[blockIdx.x].finvol = bfv;
+  }
+  if (!last_block_arrived(&c.ticket_count)) return;
+
+  // exclusive scan of the tile counts (each thread a contiguous chunk)
+  __shared__ long long chunk_sum[THREADS];
+  const int64_t per = (ntiles + THREADS - 1) / THREADS;
+  const int64_t t0 = threadIdx.x * per, t1 = t0 + per < ntiles ? t0 + per : ntiles;
+  long long acc = 0;
+  for (int64_t t = t0; t < t1; ++t) acc += A.pool.tile_count[t];
+  chunk_sum[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long run = 0;
+    for (int w = 0; w < THREADS; ++w) {
+      const long long x = chunk_sum[w];
+      chunk_sum[w] = run;
+      run += x;
+    }
+  }
+  __syncthreads();
+  long long run = chunk_sum[threadIdx.x];
+  for (int64_t t = t0; t < t1; ++t) {
+    const long long x = A.pool.tile_count[t];
+    A.pool.tile_offset[t] = run;
+    run += x;
+  }
+  __syncthreads();
+  if (threadIdx.x != THREADS - 1) return;
+  const long long n_surv = run;  // end of the last chunk = total survivors
+  NSum tva = A.count_part[0].va, tea = A.count_part[0].ea, tfv = A.count_part[0].finvol;
+  for (unsigned b = 1; b < gridDim.x; ++b) {
+    tva = ncomb(tva, A.count_part[b].va);
+    tea = ncomb(tea, A.count_part[b].ea);
+    tfv = ncomb(tfv, A.count_part[b].finvol);
+  }
+  c.n_surv = n_surv;
+  const bool tr_ok = c.trace_on && c.it - 1 < A.trace_cap;
+  TraceRec* tr = tr_ok ? &A.trace[c.it - 1] : nullptr;
+  if (tr) {
+    tr->trigger = c.trigger;
+    tr->n_survivors = n_surv;
+    if (c.trigger) {
+      tr->probes = c.probes;
+      tr->search_ok = c.search_ok;
+      tr->threshold = c.t;
+      tr->direction_changes = (double)c.dir_changes;
+    }
+  }
+  if (2 * n_surv > c.max_regions) {  // memory exhausted (Sec. 3.5.2)
+    c.status = 2;
+    c.done = 1;
+    c.estimate = c.v + c.vf;
+    c.errorest = c.e + c.ef;
+  } else {
+    const double vf_new = c.v - nval(tva) + c.vf;
+    const double ef_new = c.e - nval(tea) + c.ef;
+    if (tr) {
+      tr->vf = vf_new;
+      tr->ef = ef_new;
+    }
+    if (n_surv == 0 || ef_new > fmax(c.tau_rel * fabs(c.v + c.vf), c.tau_abs)) {
+      c.status = 3;  // tolerance out of reach
+      c.done = 1;
+      c.estimate = c.v + c.vf;
+      c.errorest = c.e + c.ef;
+    } else {
+      c.vf = vf_new;
+      c.ef = ef_new;
+      c.fin_volume_acc = ncomb(c.fin_volume_acc, tfv);
+    }
+  }
+  // independent bound on the device loop: never more than it_max + 1 passes
+  c.loop_guard += 1;
+  if (!c.done && c.loop_guard > c.it_max) {
+    c.watchdog = 2;
+    c.done = 1;
+  }
+  set_cond(A.use_graph, A.h_main, c.done ? 0u : 1u);
+  __threadfence();
+}
+
+// ----------------------------------------- Filter + parent update + Split
+// Survivor i with rank r (in region order) writes V_p[r] = V_i and its two
+// halves along K_i to slots 2r (lower half) and 2r+1 (upper half) of the
+// other pool buffer.
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
+  Ctrl& c = *A.ctrl;
+  if (c.done) return;
+  constexpr int TILE = THREADS * ITEMS;
+  const int64_t s = c.s;
+  const int n = A.pool.n;
+  const int64_t cap = A.pool.cap;
+  const int src = (c.it - 1) & 1, dst = src ^ 1;
+  const double* __restrict__ lo_s = A.pool.lower + (size_t)src * n * cap;
+  const uint8_t* __restrict__ lv_s = A.pool.level + (size_t)src * n * cap;
+  double* __restrict__ lo_d = A.pool.lower + (size_t)dst * n * cap;
+  uint8_t* __restrict__ lv_d = A.pool.level + (size_t)dst * n * cap;
+  const int64_t ntiles = (s + TILE - 1) / TILE;
+  __shared__ int shr[THREADS / 32];
+  int bad = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    long long base = A.pool.tile_offset[tile];
+    for (int r = 0; r < ITEMS; ++r) {
+      const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
+      bool act = false;
+      double v = 0.0;
+      if (i < s) {
+        v = A.pool.V[i];
+        act = final_active(v, A.pool.E[i], c);
+      }
+      int total;
+      const int rank = block_rank<THREADS>(act, shr, &total);
+      if (act) {
+        const int64_t q = base + rank;
+        const int k = A.pool.K[i];
+        A.pool.Vp[q] = v;
+        for (int j = 0; j < n; ++j) {
+          const double lo = lo_s[(size_t)j * cap + i];
+          const int lv = lv_s[(size_t)j * cap + i];
+          double2 out = make_double2(lo, lo);
+          uchar2 ol = make_uchar2((unsigned char)lv, (unsigned char)lv);
+          if (j == k) {
+            if (lv >= 62) bad = 1;
+            out.y = lo + pow2_neg(lv + 1);
+            ol = make_uchar2((unsigned char)(lv + 1), (unsigned char)(lv + 1));
+          }
+          *reinterpret_cast<double2*>(lo_d + (size_t)j * cap + 2 * q) = out;
+          *reinterpret_cast<uchar2*>(lv_d + (size_t)j * cap + 2 * q) = ol;
+        }
+      }
+      base += total;
+    }
+  }
+  if (bad) atomicExch(&c.watchdog, 1);
+  if (!last_block_arrived(&c.ticket_split)) return;
+  if (threadIdx.x == 0) {
+    c.s = 2 * c.n_surv;
+    c.it += 1;
+    __threadfence();
+  }
+}
+
+// ------------------------------------------------------- FP64 peak probe
+__global__ void k_fp64_fma(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// --------------------------------------------------------------- workspace
+struct GraphEntry {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct Workspace {
+  int dev = -1;
+  int sms = 0;
+  int64_t cap = 0;
+  int n = 0;
+  Pool pool = {};
+  Ctrl* ctrl = nullptr;
+  IntegrandParams* prm = nullptr;
+  EvalPartial* eval_part = nullptr;
+  ProbePartial* probe_part = nullptr;
+  CountPartial* count_part = nullptr;
+  TraceRec* trace = nullptr;
+  int trace_cap = 0;
+  int max_grid = 0;
+  cudaStream_t own_stream = nullptr;
+  std::vector<void*> allocs;
+  std::map<int, GraphEntry> graphs;  // key = family * 16 + dim
+};
+
+static std::mutex g_mu;
+static Workspace g_ws;
+static std::map<int, RuleTable> g_rules;
+
+constexpr int kMgmtThreads = 256;
+constexpr int kMgmtItems = 8;
+constexpr int kTraceCap = 1024;
+
+static const FamilyKernels& family_kernels(int fam) {
+  switch (fam) {
+    case kFamProductPeak: return kernels_product_peak();
+    case kFamGaussian: return kernels_gaussian();
+    case kFamOscillatory: return kernels_oscillatory();
+    case kFamCornerPeak: return kernels_corner_peak();
+    default: return kernels_c0();
+  }
+}
+
+static void release_graphs(Workspace& w) {
+  for (auto& kv : w.graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  w.graphs.clear();
+}
+
+static void release_ws(Workspace& w) {
+  release_graphs(w);
+  for (void* p : w.allocs) cudaFree(p);
+  w.allocs.clear();
+  w.cap = 0;
+  w.n = 0;
+  w.pool = Pool{};
+  w.ctrl = nullptr;
+}
+
+template <class T>
+static cudaError_t ws_alloc(Workspace& w, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 256);
+  if (e != cudaSuccess) return e;
+  w.allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return cudaSuccess;
+}
+
+static int ensure_workspace(int64_t want_cap, int n) {
+  Workspace& w = g_ws;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (w.dev == dev && w.cap >= want_cap && w.n >= n) return 0;
+  release_ws(w);
+  w.dev = dev;
+  cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = ((want_cap + 4095) / 4096) * 4096;
+  const int nn = n;
+  w.max_grid = w.sms * 16;
+  const int64_t ntiles = cap / kTile + 2;
+#define PG_ALLOC(ptr, cnt)                                                                        \
+  do {                                                                                            \
+    e = ws_alloc(w, &(ptr), (size_t)(cnt));                                                       \
+    if (e != cudaSuccess) {                                                                       \
+      release_ws(w);                                                                              \
+      return fail(PAGANI_ERR_CUDA, std::string("workspace allocation: ") + cudaGetErrorString(e)); \
+    }                                                                                             \
+  } while (0)
+  PG_ALLOC(w.pool.lower, (size_t)2 * nn * cap);
+  PG_ALLOC(w.pool.level, (size_t)2 * nn * cap);
+  PG_ALLOC(w.pool.V, cap);
+  PG_ALLOC(w.pool.E, cap);
+  PG_ALLOC(w.pool.K, cap);
+  PG_ALLOC(w.pool.Vp, cap / 2 + 1);
+  PG_ALLOC(w.pool.tile_count, ntiles);
+  PG_ALLOC(w.pool.tile_offset, ntiles);
+  PG_ALLOC(w.ctrl, 1);
+  PG_ALLOC(w.prm, 1);
+  PG_ALLOC(w.eval_part, w.max_grid);
+  PG_ALLOC(w.probe_part, w.max_grid);
+  PG_ALLOC(w.count_part, w.max_grid);
+  PG_ALLOC(w.trace, kTraceCap);
+#undef PG_ALLOC
+  w.pool.cap = cap;
+  w.pool.n = nn;
+  w.cap = cap;
+  w.n = nn;
+  w.trace_cap = kTraceCap;
+  e = cudaMemset(w.ctrl, 0, sizeof(Ctrl));
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  if (!w.own_stream) cudaStreamCreateWithFlags(&w.own_stream, cudaStreamNonBlocking);
+  return 0;
+}
+
+static const RuleTable* get_rule(int n) {
+  auto it = g_rules.find(n);
+  if (it != g_rules.end()) return &it->second;
+  RuleTable t;
+  double res = 0.0;
+  if (!build_rule(n, &t, &res) || !(res < 1e-14)) return nullptr;
+  return &(g_rules[n] = t);
+}
+
+static EvalRule to_eval_rule(const RuleTable& t) {
+  EvalRule r;
+  for (int i = 0; i < 5; ++i) r.radius[i] = t.radius[i];
+  r.q = t.q;
+  r.noise = 64.0 * (double)t.num_points * 0x1p-53;
+  for (int g = 0; g < kNumGen; ++g) r.cnt[g] = (double)t.count[g];
+  for (int g = 0; g < kNumGen; ++g)
+    for (int k = 0; k < 5; ++k) r.w[g][k] = t.w[g][k];
+  return r;
+}
+
+static int check_params(int fam, int n, const double* p) {
+  const int np = fam == kFamOscillatory ? n + 1 : (fam == kFamCornerPeak ? n : 2 * n);
+  for (int i = 0; i < np; ++i)
+    if (!std::isfinite(p[i])) return fail(PAGANI_ERR_INTEGRAND, "non-finite integrand parameter");
+  if (fam == kFamProductPeak)
+    for (int j = 0; j < n; ++j)
+      if (p[j] == 0.0) return fail(PAGANI_ERR_INTEGRAND, "product peak needs c_j != 0");
+  return 0;
+}
+
+static IntegrandParams to_params(int fam, int n, const double* p) {
+  IntegrandParams q;
+  std::memset(&q, 0, sizeof(q));
+  if (fam == kFamOscillatory) {
+    q.u = p[0];
+    for (int j = 0; j < n; ++j) q.p0[j] = p[1 + j];
+  } else if (fam == kFamCornerPeak) {
+    for (int j = 0; j < n; ++j) q.p0[j] = p[j];
+  } else {
+    for (int j = 0; j < n; ++j) {
+      q.p0[j] = p[j];
+      q.p1[j] = p[n + j];
+    }
+  }
+  return q;
+}
+
+static int default_init_div(int n) {
+  int d = 2;
+  for (;;) {
+    int64_t pw = 1;
+    for (int j = 0; j < n; ++j) pw *= 2 * d;
+    if (pw > 4096) break;
+    d *= 2;
+  }
+  return d;
+}
+
+struct Launch {
+  int eval_grid, eval_block;
+  size_t eval_smem;
+  int mgmt_grid;
+};
+
+static int launch_config(const FamilyKernels& fk, int n, Launch* L) {
+  Workspace& w = g_ws;
+  L->eval_block = fk.threads;
+  L->eval_smem = (size_t)fk.table_bytes_per_thread[n] * fk.threads;
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fk.loop_fn[n], fk.threads, L->eval_smem);
+  if (e != cudaSuccess || occ < 1)
+    return fail(PAGANI_ERR_CUDA, std::string("evaluate kernel does not fit: ") + cudaGetErrorString(e));
+  L->eval_grid = w.sms * occ;
+  if (L->eval_grid > w.max_grid) L->eval_grid = w.max_grid;
+  L->mgmt_grid = w.sms * 8;
+  if (L->mgmt_grid > w.max_grid) L->mgmt_grid = w.max_grid;
+  return 0;
+}
+
+static LoopArgs loop_args(int use_graph, cudaGraphConditionalHandle hm, cudaGraphConditionalHandle hp) {
+  Workspace& w = g_ws;
+  LoopArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.pool = w.pool;
+  a.ctrl = w.ctrl;
+  a.prm = w.prm;
+  a.eval_part = w.eval_part;
+  a.probe_part = w.probe_part;
+  a.count_part = w.count_part;
+  a.trace = w.trace;
+  a.trace_cap = w.trace_cap;
+  a.use_graph = use_graph;
+  a.h_main = hm;
+  a.h_probe = hp;
+  return a;
+}
+
+static cudaError_t add_kernel(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* dep, size_t ndep,
+                              const void* fn, int grid, int block, size_t smem, void** args) {
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
+}
+
+static cudaError_t add_while(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* dep, size_t ndep,
+                             cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  std::memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaError_t e = cudaGraphAddNode(node, g, dep, nullptr, ndep, &np);
+  if (e == cudaSuccess) *body = np.conditional.phGraph_out[0];
+  return e;
+}
+
+// The whole iteration loop of Algorithm 2 as one graph:
+//   WHILE(main) { evaluate -> WHILE(probe) { probe } -> count -> split }
+static int build_graph(int fam, int n, const EvalRule& rule, const Launch& L, GraphEntry* out) {
+  const FamilyKernels& fk = family_kernels(fam);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("cudaGraphCreate: ") + cudaGetErrorString(e));
+  cudaGraphConditionalHandle hm, hp;
+  cudaGraphNode_t wmain, nev, wprobe, nprobe, ncount, nsplit;
+  cudaGraph_t body = nullptr, pbody = nullptr;
+  LoopArgs args;
+  EvalRule r = rule;
+  void* eargs[2];
+  void* margs[1];
+#define PG_CK(x)                                                                     \
+  do {                                                                               \
+    e = (x);                                                                         \
+    if (e != cudaSuccess) {                                                          \
+      cudaGraphDestroy(g);                                                           \
+      return fail(PAGANI_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e));    \
+    }                                                                                \
+  } while (0)
+  PG_CK(cudaGraphConditionalHandleCreate(&hm, g, 1, cudaGraphCondAssignDefault));
+  PG_CK(add_while(&wmain, g, nullptr, 0, hm, &body));
+  PG_CK(cudaGraphConditionalHandleCreate(&hp, body, 0, 0));
+  args = loop_args(1, hm, hp);
+  eargs[0] = &r;
+  eargs[1] = &args;
+  margs[0] = &args;
+  PG_CK(add_kernel(&nev, body, nullptr, 0, fk.loop_fn[n], L.eval_grid, L.eval_block, L.eval_smem, eargs));
+  PG_CK(add_while(&wprobe, body, &nev, 1, hp, &pbody));
+  PG_CK(add_kernel(&nprobe, pbody, nullptr, 0, (const void*)&k_probe<kMgmtThreads>, L.mgmt_grid, kMgmtThreads, 0,
+                   margs));
+  PG_CK(add_kernel(&ncount, body, &wprobe, 1, (const void*)&k_count<kMgmtThreads, kMgmtItems>, L.mgmt_grid,
+                   kMgmtThreads, 0, margs));
+  PG_CK(add_kernel(&nsplit, body, &ncount, 1, (const void*)&k_split<kMgmtThreads, kMgmtItems>, L.mgmt_grid,
+                   kMgmtThreads, 0, margs));
+  cudaGraphExec_t ex = nullptr;
+  PG_CK(cudaGraphInstantiate(&ex, g, 0));
+#undef PG_CK
+  out->graph = g;
+  out->exec = ex;
+  return 0;
+}
+
+static int integrate_locked(int n, int fam, const double* params, double epsrel, double epsabs,
+                            int64_t max_regions, const pagani_options& o, cudaStream_t st, pagani_result* out,
+                            pagani_trace_record* trace, int trace_cap) {
+  std::memset(out, 0, sizeof(*out));
+  if (n < PAGANI_MIN_DIM || n > PAGANI_MAX_DIM) return out->status = fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
+  if (fam < 0 || fam >= kNumFamilies) return out->status = fail(PAGANI_ERR_INTEGRAND, "unknown integrand_id");
+  if (!params) return out->status = fail(PAGANI_ERR_ARGUMENT, "params is NULL");
+  if (!(epsrel > 0.0) || !(epsabs >= 0.0) || !std::isfinite(epsrel) || !std::isfinite(epsabs))
+    return out->status = fail(PAGANI_ERR_TOLERANCE, "need epsrel > 0 and epsabs >= 0, finite");
+  if (o.it_max < 1 || o.it_max > kTraceCap) return out->status = fail(PAGANI_ERR_ARGUMENT, "it_max out of range");
+  int rc = check_params(fam, n, params);
+  if (rc) return out->status = rc;
+  const int d0 = o.init_div > 0 ? o.init_div : default_init_div(n);
+  int log2d = 0;
+  while ((1 << log2d) < d0) ++log2d;
+  if ((1 << log2d) != d0 || log2d > 20) return out->status = fail(PAGANI_ERR_ARGUMENT, "init_div must be a power of two");
+  int64_t s0 = 1;
+  for (int j = 0; j < n; ++j) {
+    s0 *= d0;
+    if (s0 > ((int64_t)1 << 40)) return out->status = fail(PAGANI_ERR_ARGUMENT, "initial split too large");
+  }
+  if (s0 > max_regions) return out->status = fail(PAGANI_ERR_CAPACITY, "max_regions below the initial split");
+  const RuleTable* rt = get_rule(n);
+  if (!rt) return out->status = fail(PAGANI_ERR_CUDA, "rule construction failed");
+  rc = ensure_workspace(max_regions > s0 ? max_regions : s0, n);
+  if (rc) return out->status = rc;
+  Workspace& w = g_ws;
+  if (!st) st = w.own_stream;
+  const FamilyKernels& fk = family_kernels(fam);
+  Launch L;
+  rc = launch_config(fk, n, &L);
+  if (rc) return out->status = rc;
+  const EvalRule rule = to_eval_rule(*rt);
+
+  // pool arrays are laid out for w.n axes; the kernels index with pool.n
+  Pool pool = w.pool;
+  (void)pool;
+  Ctrl h;
+  std::memset(&h, 0, sizeof(h));
+  h.tau_rel = epsrel;
+  h.tau_abs = epsabs;
+  h.max_regions = max_regions;
+  h.it_max = o.it_max;
+  h.relerr_filter = o.relerr_filter ? 1 : 0;
+  h.heuristic_filter = o.heuristic_filter ? 1 : 0;
+  h.trace_on = trace != nullptr ? 1 : 0;
+  h.s = s0;
+  h.it = 1;
+  h.status = -100;
+  IntegrandParams prm = to_params(fam, n, params);
+  cudaError_t e;
+#define PG_CK(x)                                                                          \
+  do {                                                                                    \
+    e = (x);                                                                              \
+    if (e != cudaSuccess) return out->status = fail(PAGANI_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e)); \
+  } while (0)
+  // the pool must be indexed with the call's dimension
+  w.pool.n = n;
+  PG_CK(cudaMemcpyAsync(w.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  PG_CK(cudaMemcpyAsync(w.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
+  {
+    Pool p = w.pool;
+    k_uniform_split<<<(int)((s0 + 255) / 256), 256, 0, st>>>(p, d0, log2d, s0);
+    PG_CK(cudaGetLastError());
+  }
+  if (o.use_graph) {
+    const int key = fam * 16 + n + (w.n << 8);
+    auto it = w.graphs.find(key);
+    if (it == w.graphs.end()) {
+      GraphEntry ge;
+      rc = build_graph(fam, n, rule, L, &ge);
+      if (rc) return out->status = rc;
+      it = w.graphs.emplace(key, ge).first;
+    }
+    PG_CK(cudaGraphLaunch(it->second.exec, st));
+    PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    PG_CK(cudaStreamSynchronize(st));
+  } else {
+    const LoopArgs args = loop_args(0, 0, 0);
+    for (int guard = 0; guard < o.it_max + 2; ++guard) {
+      PG_CK(fk.loop[n](rule, args, L.eval_grid, L.eval_block, L.eval_smem, st));
+      PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      PG_CK(cudaStreamSynchronize(st));
+      if (h.search) {
+        for (int probe = 0; probe < 128; ++probe) {
+          k_probe<kMgmtThreads><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
+          PG_CK(cudaGetLastError());
+          PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+          PG_CK(cudaStreamSynchronize(st));
+          if (!h.search_cont) break;
+        }
+      }
+      k_count<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
+      PG_CK(cudaGetLastError());
+      k_split<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
+      PG_CK(cudaGetLastError());
+      PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      PG_CK(cudaStreamSynchronize(st));
+      if (h.done) break;
+    }
+  }
+  if (trace && trace_cap > 0) {
+    const int nrec = std::min(std::min(h.it, trace_cap), w.trace_cap);
+    if (nrec > 0) {
+      std::vector<TraceRec> tmp(nrec);
+      PG_CK(cudaMemcpyAsync(tmp.data(), w.trace, sizeof(TraceRec) * nrec, cudaMemcpyDeviceToHost, st));
+      PG_CK(cudaStreamSynchronize(st));
+      static_assert(sizeof(TraceRec) == sizeof(pagani_trace_record), "trace layout");
+      std::memcpy(trace, tmp.data(), sizeof(TraceRec) * nrec);
+    }
+  }
+#undef PG_CK
+  out->estimate = h.estimate;
+  out->errorest = h.errorest;
+  out->iterations = h.it;
+  out->n_regions = h.n_regions_total;
+  out->n_active_last = h.s;
+  out->finished_volume = nval(h.fin_volume_acc);
+  if (h.watchdog == 1) return out->status = fail(PAGANI_ERR_WATCHDOG, "region depth limit reached on one axis");
+  if (h.watchdog) return out->status = fail(PAGANI_ERR_WATCHDOG, "device loop exceeded its iteration bound");
+  if (!h.done) return out->status = fail(PAGANI_ERR_WATCHDOG, "device loop ended without a result");
+  out->status = h.status;
+  if (h.status == -6) g_err = "the integrand produced NaN or Inf";
+  return out->status;
+}
+
+}  // namespace pg
+
+// =================================================================== C ABI
+using namespace pg;
+
+extern "C" {
+
+void pagani_default_options(pagani_options* o) {
+  if (!o) return;
+  o->relerr_filter = 1;
+  o->heuristic_filter = 1;
+  o->init_div = 0;
+  o->it_max = 100;
+  o->use_graph = 1;
+}
+
+int pagani_integrate_ex(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
+                        int64_t max_regions, const pagani_options* opt, void* cuda_stream, pagani_result* out,
+                        pagani_trace_record* trace, int trace_cap) {
+  if (!out) return fail(PAGANI_ERR_ARGUMENT, "out is NULL");
+  pagani_options o;
+  pagani_default_options(&o);
+  if (opt) o = *opt;
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    return integrate_locked(dim, integrand_id, params, epsrel, epsabs, max_regions, o,
+                            (cudaStream_t)cuda_stream, out, trace, trace_cap);
+  } catch (...) {
+    return out->status = fail(PAGANI_ERR_CUDA, "internal error");
+  }
+}
+
+int pagani_integrate(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
+                     int64_t max_regions, pagani_result* out) {
+  return pagani_integrate_ex(dim, integrand_id, params, epsrel, epsabs, max_regions, nullptr, nullptr, out,
+                             nullptr, 0);
+}
+
+int pagani_workspace_reserve(int64_t max_regions, int dim) {
+  if (dim < PAGANI_MIN_DIM || dim > PAGANI_MAX_DIM) return fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
+  if (max_regions < 1) return fail(PAGANI_ERR_ARGUMENT, "max_regions must be positive");
+  std::lock_guard<std::mutex> lk(g_mu);
+  return ensure_workspace(max_regions, dim);
+}
+
+int pagani_workspace_release(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  release_ws(g_ws);
+  return 0;
+}
+
+int pagani_evaluate(int dim, int integrand_id, const double* params, int64_t m, const double* lower,
+                    const double* width, double* V, double* E, int32_t* K, double* diag, void* cuda_stream) {
+  if (dim < PAGANI_MIN_DIM || dim > PAGANI_MAX_DIM) return fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
+  if (integrand_id < 0 || integrand_id >= kNumFamilies) return fail(PAGANI_ERR_INTEGRAND, "unknown integrand_id");
+  if (!params || m < 0) return fail(PAGANI_ERR_ARGUMENT, "bad params or m");
+  if (m == 0) return 0;
+  if (!lower || !width || !V || !E || !K) return fail(PAGANI_ERR_ARGUMENT, "null device pointer");
+  int rc = check_params(integrand_id, dim, params);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  const RuleTable* rt = get_rule(dim);
+  if (!rt) return fail(PAGANI_ERR_CUDA, "rule construction failed");
+  rc = ensure_workspace(4096, dim);
+  if (rc) return rc;
+  Workspace& w = g_ws;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : w.own_stream;
+  const FamilyKernels& fk = family_kernels(integrand_id);
+  IntegrandParams prm = to_params(integrand_id, dim, params);
+  cudaError_t e = cudaMemcpyAsync(w.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  StandaloneArgs a;
+  a.lower = lower;
+  a.width = width;
+  a.V = V;
+  a.E = E;
+  a.K = K;
+  a.diag = diag;
+  a.m = m;
+  a.prm = w.prm;
+  const size_t smem = (size_t)fk.table_bytes_per_thread[dim] * fk.threads;
+  const int64_t pairs = (m + 1) / 2;
+  int64_t grid = (pairs + fk.threads - 1) / fk.threads;
+  if (grid > (int64_t)w.sms * 64) grid = (int64_t)w.sms * 64;
+  const EvalRule rule = to_eval_rule(*rt);
+  e = diag ? fk.standalone_diag[dim](rule, a, (int)grid, fk.threads, smem, st)
+           : fk.standalone[dim](rule, a, (int)grid, fk.threads, smem, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
+  return 0;
+}
+
+int pagani_rule_tables(int dim, double* radius, double* weights, int64_t* counts) {
+  if (dim < PAGANI_MIN_DIM || dim > PAGANI_MAX_DIM) return fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
+  RuleTable t;
+  double res = 0.0;
+  if (!build_rule(dim, &t, &res)) return fail(PAGANI_ERR_CUDA, "rule construction failed");
+  if (radius)
+    for (int i = 0; i < 5; ++i) radius[i] = t.radius[i];
+  if (weights)
+    for (int g = 0; g < kNumGen; ++g)
+      for (int k = 0; k < 5; ++k) weights[g * 5 + k] = t.w[g][k];
+  if (counts)
+    for (int g = 0; g < kNumGen; ++g) counts[g] = t.count[g];
+  return t.num_points;
+}
+
+int pagani_fp64_peak(double* tflops, void* cuda_stream) {
+  if (!tflops) return fail(PAGANI_ERR_ARGUMENT, "tflops is NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int grid = sms * 4, block = 256, iters = 4096;
+  double* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, sizeof(double) * grid * block);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  k_fp64_fma<<<grid, block, 0, st>>>(buf, 64, 1.0000001, 1e-9);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(a, st);
+    k_fp64_fma<<<grid, block, 0, st>>>(buf, iters, 1.0000001, 1e-9);
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) best = ms;
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  *tflops = 2.0 * 8.0 * iters * (double)grid * block / (best * 1e-3) / 1e12;
+  return 0;
+}
+
+const char* pagani_last_error(void) { return g_err.c_str(); }
+
+const char* pagani_version(void) { return "pagani-gb300 0.1 (sm_103a, FP64)"; }
+
+}  // extern "C"

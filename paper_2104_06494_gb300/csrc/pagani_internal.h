@@ -1,0 +1,206 @@
+// Internal declarations of the GB300 PAGANI engine (not part of the C ABI).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace pg {
+
+constexpr int kMaxDim = 8;
+constexpr int kNumGen = 9;
+constexpr int kCodes = 11;  // coordinate codes per axis (see below)
+
+// Generator orbits of the degree-9 rule, in table order.
+enum Gen {
+  kGenCentre = 0,   // centre
+  kGenL1 = 1,       // one axis at sqrt(l1)
+  kGenL2 = 2,       // one axis at sqrt(l2)
+  kGenL3 = 3,       // one axis at sqrt(l3)
+  kGenLp = 4,       // one axis at sqrt(lp) (zero basic weight)
+  kGenL1L1 = 5,     // two axes at sqrt(l1)
+  kGenL1L2 = 6,     // two axes at sqrt(l1), sqrt(l2), both orders
+  kGenL1L1L1 = 7,   // three axes at sqrt(l1)
+  kGenL0All = 8     // every axis at sqrt(l0)
+};
+
+// Per-axis coordinate codes: the 11 distinct offsets c_j + h_j g a rule point
+// can take along one axis.
+enum Code {
+  kC0 = 0,
+  kR1P = 1, kR1M = 2,
+  kR2P = 3, kR2M = 4,
+  kR3P = 5, kR3M = 6,
+  kRpP = 7, kRpM = 8,
+  kR0P = 9, kR0M = 10
+};
+
+struct RuleTable {
+  int n;
+  int num_points;
+  double radius[5];        // sqrt of l1, l2, l3, lp, l0 (on [-1, 1])
+  double q;                // lp / l2 (fourth-difference weight)
+  double w[kNumGen][5];    // basic rule, null rules 1..4 (unit-volume cube)
+  int64_t count[kNumGen];  // orbit sizes
+};
+
+bool build_rule(int n, RuleTable* out, double* max_residual);
+int num_points(int n);
+int64_t orbit_count(int n, int g);
+
+enum Family {
+  kFamProductPeak = 0,
+  kFamGaussian = 1,
+  kFamOscillatory = 2,
+  kFamCornerPeak = 3,
+  kFamC0 = 4,
+  kNumFamilies = 5
+};
+
+// Integrand parameters as the kernels read them (device buffer, one per call).
+struct IntegrandParams {
+  double p0[kMaxDim];   // c (product peak), a (Gaussian, corner peak, C0, oscillatory)
+  double p1[kMaxDim];   // w (product peak, Gaussian, C0)
+  double u;             // oscillatory phase parameter
+};
+
+// Neumaier pair used for compensated sums.
+struct NSum { double s, c; };
+
+// Device-resident state of one integration; every kernel of the loop reads
+// and updates it, the host reads it once at the end.
+struct Ctrl {
+  // fixed for the call
+  double tau_rel, tau_abs;
+  int64_t max_regions;
+  int32_t it_max, relerr_filter, heuristic_filter, trace_on;
+  // iteration state
+  int64_t s;                 // regions this iteration
+  int32_t it;                // current iteration, 1-based
+  int32_t done;              // 1 once the result is final
+  int32_t status;            // see pagani.h
+  int32_t nonfinite;         // a region produced NaN/Inf
+  double v, e, vf, ef;       // Algorithm 2 scalars
+  double v_tot_prev;
+  int64_t n_rel;             // rel-err actives this iteration
+  double emin, emax;
+  int32_t trigger;
+  // threshold search (Algorithm 3)
+  int32_t search;            // search requested this iteration
+  int32_t search_ok, probes, last_dir, dir_changes, search_cont;
+  double t, Pmax, e_b;
+  // survivors and totals
+  int64_t n_surv;
+  int64_t n_regions_total;
+  double fin_volume;
+  NSum fin_volume_acc;
+  // result
+  double estimate, errorest;
+  // last-block tickets
+  unsigned int ticket_eval, ticket_probe, ticket_count, ticket_split;
+  int32_t watchdog;          // set if a kernel saw an impossible state
+  int32_t loop_guard;        // iterations counted by the count kernel
+};
+
+// One per-iteration record (mirrors pagani_trace_record in pagani.h).
+struct TraceRec {
+  int32_t it, trigger, probes, search_ok;
+  int64_t s, n_relerr_active, n_survivors;
+  double v, e, vf, ef, threshold, direction_changes;
+};
+
+// Per-block partial results written by the evaluate kernel.
+struct EvalPartial {
+  NSum v, e;
+  double emin, emax;
+  long long n_rel;
+  int nonfinite;
+  int pad;
+};
+
+struct CountPartial {
+  NSum va, ea, finvol;
+};
+
+struct ProbePartial {
+  NSum ea;
+  long long n_active;
+  long long pad;
+};
+
+// Rule data passed by value to the evaluate kernels.
+struct EvalRule {
+  double radius[5];
+  double q;
+  double noise;  // 64 N(n) u: null values below noise * vol * sum_g |u_kg| M_g count as zero
+  double w[kNumGen][5];
+  double cnt[kNumGen];  // orbit sizes
+};
+
+// Region pool: SoA, two buffers (ping-pong).  lower[b][j][cap] doubles,
+// level[b][j][cap] bytes with width = 2^-level.
+struct Pool {
+  double* lower;        // 2 * n * cap
+  uint8_t* level;       // 2 * n * cap
+  double* V;            // cap
+  double* E;            // cap
+  uint8_t* K;           // cap
+  double* Vp;           // cap / 2 + 1
+  long long* tile_count;   // n_tiles + 1
+  long long* tile_offset;  // n_tiles + 1
+  int64_t cap;
+  int n;
+};
+
+// Arguments of the loop kernels (by value).
+struct LoopArgs {
+  Pool pool;
+  Ctrl* ctrl;
+  const IntegrandParams* prm;
+  EvalPartial* eval_part;
+  ProbePartial* probe_part;
+  CountPartial* count_part;
+  TraceRec* trace;
+  int trace_cap;
+  int use_graph;
+  cudaGraphConditionalHandle h_main, h_probe;
+};
+
+// Arguments of the standalone evaluate entry point.
+struct StandaloneArgs {
+  const double* lower;   // n x m SoA
+  const double* width;   // n x m SoA
+  double* V;
+  double* E;
+  int32_t* K;
+  double* diag;          // (8 + n) x m SoA or null
+  int64_t m;
+  const IntegrandParams* prm;
+};
+
+// Launchers implemented per family (eval_<family>.cu).
+typedef cudaError_t (*LoopEvalLauncher)(const EvalRule&, const LoopArgs&, int grid, int block, size_t smem,
+                                        cudaStream_t);
+typedef cudaError_t (*StandaloneLauncher)(const EvalRule&, const StandaloneArgs&, int grid, int block,
+                                          size_t smem, cudaStream_t);
+
+struct FamilyKernels {
+  LoopEvalLauncher loop[kMaxDim + 1];
+  StandaloneLauncher standalone[kMaxDim + 1];
+  StandaloneLauncher standalone_diag[kMaxDim + 1];
+  const void* loop_fn[kMaxDim + 1];        // kernel symbols (for occupancy queries / graph nodes)
+  int threads;                             // block size
+  int table_bytes_per_thread[kMaxDim + 1];
+};
+
+const FamilyKernels& kernels_product_peak();
+const FamilyKernels& kernels_gaussian();
+const FamilyKernels& kernels_oscillatory();
+const FamilyKernels& kernels_corner_peak();
+const FamilyKernels& kernels_c0();
+
+constexpr int kSplitThreads = 256;
+constexpr int kItemsPerThread = 8;
+constexpr int kTile = kSplitThreads * kItemsPerThread;  // regions per compaction tile
+constexpr int kReduceThreads = 256;
+
+}  // namespace pg

@@ -1,0 +1,88 @@
+"""Helpers shared by the GPU parity tests: tolerances derived from the
+floating-point arithmetic, and the reference error formula applied to given
+null-rule values."""
+import math
+
+import numpy as np
+
+EPS = 2.0 ** -53
+
+
+def point_count(n):
+    return 1 + 8 * n + 6 * n * (n - 1) + 4 * n * (n - 1) * (n - 2) // 3 + 2 ** n
+
+
+def value_condition(family, n, params, lo, wd):
+    """Per-box rounding sensitivity of the integrand values: (k_rel, k_abs)
+    such that one evaluation of f at a point of the box carries an error of
+    at most k_rel eps |f| + k_abs eps, whichever way it is formed (products
+    of per-axis factors or the formula written out):
+      product peak  k_rel = 2n + 4 (n divisions and products)
+      Gaussian      k_rel = max sum a^2 (x - w)^2 (the exponent: exp
+                    turns an absolute error of its argument into a relative
+                    error of its value)
+      C0            k_rel = max sum a |x - w|
+      corner peak   k_rel = 4 (n + 1) (a power of a sum of n terms)
+      oscillatory   k_abs = 2 pi |u| + sum |a| max |x| (the cosine argument)"""
+    lo = np.atleast_2d(lo)
+    hi = lo + np.atleast_2d(wd)
+    m = lo.shape[0]
+    p = np.asarray(params, dtype=np.float64)
+    k_rel = np.full(m, 2.0 * n + 4)
+    k_abs = np.zeros(m)
+    if family == 1:
+        a, w = p[:n], p[n:]
+        k_rel = np.sum(a ** 2 * np.maximum((lo - w) ** 2, (hi - w) ** 2), axis=1)
+    elif family == 4:
+        a, w = p[:n], p[n:]
+        k_rel = np.sum(a * np.maximum(np.abs(lo - w), np.abs(hi - w)), axis=1)
+    elif family == 3:
+        k_rel = np.full(m, 4.0 * (n + 1))
+    elif family == 2:
+        k_abs = 2 * np.pi * abs(p[0]) + np.sum(np.abs(p[1:]) * np.maximum(np.abs(lo), np.abs(hi)), axis=1)
+    return k_rel, k_abs
+
+
+def sum_tolerance(n, scale, k_rel=0.0, abs_scale=0.0, k_abs=0.0):
+    """Bound on the difference of two evaluations of a weighted sum of the
+    N(n) integrand values of a box computed in different orders and ways:
+    (N + 2n + 16 + k_rel) eps sum |w f| + k_abs eps sum |w| vol (recursive
+    summation bound plus the per-value error of value_condition)."""
+    return (point_count(n) + 2 * n + 16 + k_rel) * EPS * scale + k_abs * EPS * abs_scale
+
+
+def null_error(n1, n2, n3, n4):
+    """Region error from four null values, the reading of Sec. 3.2 used by
+    both implementations (restated here to check the kernel's epilogue
+    against its own N_k)."""
+    def ratio(x, y):
+        return x / y if y > 0 else (math.inf if x > 0 else 0.0)
+    r = max(ratio(n1, n2), ratio(n2, n3))
+    if r >= 1:
+        return 10 * max(n1, n2, n3, n4)
+    if r >= 0.5:
+        return 10 * r * n1
+    return 40 * r ** 3 * n1
+
+
+def sibling_regions(n, m, seed, max_level=10):
+    """m regions forming sibling pairs (2i, 2i+1): halves of random dyadic
+    parents along random axes; returned as (m x n) lower, width lists."""
+    from paper_2104_06494_gb300.workloads import SplitMix64
+    rng = SplitMix64(seed)
+    lo, wd = [], []
+    while len(lo) < m:
+        plo, pwd = [], []
+        for _ in range(n):
+            lvl = int(rng.uniform(0, max_level + 1))
+            k = int(rng.uniform(0, 1 << lvl))
+            plo.append(k / (1 << lvl))
+            pwd.append(1.0 / (1 << lvl))
+        ax = int(rng.uniform(0, n))
+        a, b = list(plo), list(pwd)
+        b[ax] = pwd[ax] / 2
+        c, d = list(plo), list(b)
+        c[ax] = plo[ax] + b[ax]
+        lo += [a, c]
+        wd += [b, d]
+    return np.array(lo[:m]), np.array(wd[:m])

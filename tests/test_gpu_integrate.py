@@ -1,0 +1,126 @@
+"""GPU parity of the whole PAGANI loop (Algorithm 2 with Algorithm 3) through
+the C ABI against the oracle on the same seeded inputs: equal iteration
+counts, region counts and statuses, estimates within 1e-12 relative, and a
+per-iteration trace diff; plus graph vs host-driven loop, bitwise
+repeatability, the failure statuses and closed-form containment."""
+import numpy as np
+import pytest
+
+from oracle import capi as oracle, closed_forms as cf
+from paper_2104_06494_gb300.workloads import config_workloads, draw_params
+from tests.conftest import has_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    if not has_gpu():
+        pytest.skip("no CUDA device")
+    import paper_2104_06494_gb300 as m
+    m.load()
+    return m
+
+
+def close(a, b, rel=1e-12, floor=1e-300):
+    return abs(a - b) <= rel * max(abs(a), abs(b)) + floor
+
+
+def compare_runs(g, o, rel=1e-12):
+    """Equal region sets (statuses, iterations, per-iteration counts and
+    decisions), integral estimates within 1e-12 relative.  Error estimates are
+    sums of region errors computed from null-rule values, differences of
+    nearly equal sums known only to their rounding level; they are compared
+    to 1e-6 relative, or 1e-12 of the integral's magnitude where they are
+    themselves at that noise level."""
+    assert g.status == o.status, (g.status, o.status)
+    assert g.iterations == o.iterations
+    assert g.n_regions == o.n_regions
+    assert g.n_active_last == o.n_active_last
+    scale = max(abs(o.estimate), float(np.max(np.abs(o.trace["v"]) + np.abs(o.trace["vf"]))))
+    assert abs(g.estimate - o.estimate) <= rel * scale + 1e-300, (g.estimate, o.estimate)
+    efloor = 1e-12 * scale
+    assert close(g.errorest, o.errorest, rel=1e-6, floor=efloor), (g.errorest, o.errorest)
+    gt, ot = g.trace, o.trace
+    assert len(gt) == len(ot)
+    for a, b in zip(gt, ot):
+        for key in ("it", "trigger", "probes", "search_ok", "s", "n_relerr_active", "n_survivors"):
+            assert a[key] == b[key], (key, a, b)
+        assert abs(a["v"] - b["v"]) <= rel * scale
+        assert abs(a["vf"] - b["vf"]) <= rel * scale
+        assert close(a["e"], b["e"], rel=1e-6, floor=efloor), (a["e"], b["e"])
+        assert close(a["ef"], b["ef"], rel=1e-6, floor=efloor), (a["ef"], b["ef"])
+
+
+CASES = [
+    (0, 2, 1e-6, 1), (0, 3, 1e-3, 1), (0, 4, 1e-6, 1),
+    (1, 2, 1e-7, 1), (1, 3, 1e-5, 1), (1, 5, 1e-4, 1),
+    (2, 2, 1e-8, 0), (2, 3, 1e-7, 0), (2, 6, 1e-6, 0),
+    (3, 3, 1e-7, 1), (3, 5, 1e-6, 1), (3, 8, 1e-4, 1),
+    (4, 2, 1e-5, 1), (4, 3, 1e-4, 1), (4, 8, 1e-3, 1),
+]
+
+
+@pytest.mark.parametrize("family,n,tau,relerr", CASES)
+def test_loop_matches_oracle(pg, family, n, tau, relerr):
+    params = draw_params(family, n, 700 + 13 * family + n)
+    o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, relerr_filter=relerr)
+    g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=4_000_000, relerr_filter=relerr, trace=True)
+    compare_runs(g, o)
+
+
+def test_config_product_peak_d3_full_size(pg):
+    """The d=3 product-peak workload at its full size (epsrel 1e-3, 1e5 regions)."""
+    w = config_workloads()["product_peak_d3"]
+    o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions)
+    g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
+    compare_runs(g, o)
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    assert abs(g.estimate - ex) <= g.errorest and g.status == 0
+
+
+def test_graph_and_host_loop_identical(pg):
+    params = draw_params(1, 4, 42)
+    a = pg.pagani_integrate_ex(4, 1, params, 1e-6, use_graph=1, trace=True)
+    b = pg.pagani_integrate_ex(4, 1, params, 1e-6, use_graph=0, trace=True)
+    assert (a.estimate, a.errorest, a.status, a.iterations, a.n_regions) == \
+           (b.estimate, b.errorest, b.status, b.iterations, b.n_regions)
+    assert a.trace.tobytes() == b.trace.tobytes()
+
+
+def test_bitwise_repeatable(pg):
+    params = draw_params(4, 5, 43)
+    r = [pg.pagani_integrate_ex(5, 4, params, 1e-4, trace=True) for _ in range(3)]
+    for x in r[1:]:
+        assert (x.estimate, x.errorest, x.n_regions) == (r[0].estimate, r[0].errorest, r[0].n_regions)
+
+
+def test_memory_exhausted_matches_oracle(pg):
+    params = draw_params(1, 3, 3)
+    o = oracle.integrate(1, 3, params, 1e-12, max_regions=6000, heuristic_filter=0)
+    g = pg.pagani_integrate_ex(3, 1, params, 1e-12, max_regions=6000, heuristic_filter=0, trace=True)
+    assert o.status == 2
+    compare_runs(g, o)
+
+
+def test_it_max_and_capacity(pg):
+    params = draw_params(1, 3, 3)
+    g = pg.pagani_integrate_ex(3, 1, params, 1e-12, it_max=1)
+    assert g.status == 1 and g.iterations == 1 and g.n_regions == 4096
+    with pytest.raises(pg.PaganiError):
+        pg.pagani_integrate(3, 1, params, 1e-3, max_regions=100)
+
+
+def test_nonfinite_integrand(pg):
+    g = pg.pagani_integrate_ex(2, 3, [-2.0, 0.5], 1e-3, raise_on_error=False)
+    assert g.status == -6
+
+
+@pytest.mark.parametrize("name", ["product_peak_d3", "oscillatory_d6", "corner_peak_d8"])
+def test_configs_within_errorest_of_closed_form(pg, name):
+    w = config_workloads()[name]
+    g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions,
+                               relerr_filter=w.relerr_filter)
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    assert g.status in (0, 3)
+    assert abs(g.estimate - ex) <= g.errorest

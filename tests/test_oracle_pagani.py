@@ -177,3 +177,14 @@ def test_status_nonfinite_integrand():
 
 def test_default_initial_divisions():
     assert [capi.default_init_div(n) for n in range(2, 9)] == [64, 16, 8, 4, 4, 2, 2]
+
+
+@pytest.mark.parametrize("p", [[4, 0], [2, 2], [5, 0], [3, 1], [1, 1]])
+def test_error_vanishes_for_exactly_integrated_polynomials(p):
+    """Degree <= 5: the degree-7 and degree-5 null rules annihilate f, so
+    N_1 and N_2 are pure rounding; below their noise floors they count as
+    zero, r = 0 and the region error is exactly 0 (the rule is exact here)."""
+    V, E, K, D = capi.evaluate(100, 2, p, [[0.1, 0.2]], [[0.5, 0.25]], diag=True)
+    assert E[0] == 0.0
+    n = 2
+    assert D[0, 0] <= D[0, 9 + 2 * n] and D[0, 1] <= D[0, 10 + 2 * n]
