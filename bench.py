@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 PAGANI engine: time-to-epsrel and integrand evals/s.
+
+One step = one complete adaptive integration (every iteration of Algorithm 2,
+all steps of the hot path) of each integral of the workload, through the C ABI
+(pagani_integrate_ex).  Default workload: the 5-D Gaussian at epsrel 1e-7 and
+the 6-D oscillatory integrand at epsrel 1e-8 (rel-err filtering off), seeded
+synthetic parameters.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank integrates the same workload independently
+(replicas: the method has no cross-GPU step on one box); value = all ranks'
+evaluations / the slowest rank's time.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_DEFAULT = "gaussian_d5+oscillatory_d6"
+METRIC = "integrand evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle time budget per integral")
+    ap.add_argument("--quiet", action="store_true")
+    return ap.parse_args()
+
+
+def workloads(spec: str):
+    from paper_2104_06494_gb300.workloads import config_workloads
+    allw = config_workloads()
+    return [allw[name] for name in spec.split("+")]
+
+
+def npoints(n: int) -> int:
+    return 1 + 8 * n + 6 * n * (n - 1) + 4 * n * (n - 1) * (n - 2) // 3 + 2 ** n
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
+                                                         if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------- oracle (CPU)
+def oracle_sample(w, budget_s: float, gpu_trace=None):
+    """The oracle on a bounded sample of one integral: its first k iterations
+    (status it_max), k chosen so the work fits about budget_s seconds."""
+    import numpy as np
+    from oracle import capi
+    t = time.perf_counter()
+    r1 = capi.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions, relerr_filter=w.relerr_filter,
+                        it_max=1)
+    dt1 = time.perf_counter() - t
+    rate = r1.n_regions / max(dt1, 1e-9)            # regions/s of the oracle on this integral
+    k = 1
+    if gpu_trace is not None and len(gpu_trace) > 1:
+        cum = np.cumsum(gpu_trace["s"])
+        k = int(max(1, np.searchsorted(cum, rate * budget_s, side="right")))
+        k = min(k, len(gpu_trace))
+    if k > 1:
+        t = time.perf_counter()
+        r = capi.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions,
+                           relerr_filter=w.relerr_filter, it_max=k)
+        dt = time.perf_counter() - t
+    else:
+        r, dt = r1, dt1
+    return {"name": w.name, "iterations": r.iterations, "regions": r.n_regions,
+            "evals": r.n_regions * npoints(w.dim), "seconds": dt, "status": r.status}
+
+
+def cpu_baseline(ws, budget_s, gpu_traces):
+    parts = [oracle_sample(w, budget_s, gpu_traces.get(w.name)) for w in ws]
+    evals = sum(p["evals"] for p in parts)
+    secs = sum(p["seconds"] for p in parts)
+    sample = "; ".join(f"{p['name']}: first {p['iterations']} iterations ({p['regions']} regions, "
+                       f"{p['seconds']:.1f} s)" for p in parts)
+    return {"value": evals / secs, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "single-threaded C oracle, " + sample}
+
+
+# --------------------------------------------------------------- helpers
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pagani_eval.cuh", "pagani_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2104_06494_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_bytes_per_region():
+    """DRAM bytes per evaluated region of Evaluate from the committed ncu
+    summary, or None when the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "k_evaluate_loop_gaussian_d5.md")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if ":" in line and line.split(":")[0].strip() in ("bytes_per_region", "kernel_source_hash",
+                                                           "fp64_pipe_active"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_hash") != source_hash():
+        return None
+    return float(kv["bytes_per_region"]), float(kv.get("fp64_pipe_active", "nan"))
+
+
+def main():
+    args = parse()
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    ws = workloads(args.workload)
+    wl_name = args.workload
+
+    if args.impl == "reference":
+        # the reference arm of this build is the CPU oracle, on rank 0 only
+        if rank != 0:
+            if world > 1:
+                dist.destroy_process_group()
+            return
+        from oracle import capi
+        capi.build()
+        step_secs, step_evals = [], []
+        for i in range(args.warmup + args.steps):
+            parts = [oracle_sample(w, args.cpu_seconds / 4) for w in ws]
+            if i >= args.warmup:
+                step_secs.append(sum(p["seconds"] for p in parts))
+                step_evals.append(sum(p["evals"] for p in parts))
+        value = sum(step_evals) / sum(step_secs)
+        sample = "; ".join(f"{p['name']}: first {p['iterations']} iterations ({p['regions']} regions)" for p in parts)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(step_secs) / len(step_secs),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded splitmix64 parameters)",
+                "config": {"workload": wl_name, "sample": "each step: the oracle's first iterations of every integral"},
+                "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                                 "sample": "single-threaded C oracle, " + sample},
+                "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2104_06494_gb300 as pg
+    from paper_2104_06494_gb300 import build as pbuild, roofline
+    pbuild.build()
+    pg.load()
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    # workspace outside the timed region (the paper times integration only)
+    pg.pagani_workspace_reserve(max(w.max_regions for w in ws), max(w.dim for w in ws))
+    peaks = pg.pagani_fp64_peak(stream)
+
+    def run(w, **kw):
+        return pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions,
+                                      relerr_filter=w.relerr_filter, stream=stream, **kw)
+
+    # one traced run per integral (untimed): iteration structure and results
+    traced = {w.name: run(w, trace=True) for w in ws}
+    # roofline of Evaluate: the same kernels, host-driven, CUDA events around
+    # every Evaluate launch on the launching stream
+    roof_parts = []
+    for w in ws:
+        r = run(w, use_graph=0, trace=True)
+        work = roofline.evaluate_work(w.family, w.dim, r.trace["s"])
+        roof_parts.append({"name": w.name, "eval_ms": r.eval_ms, "launches": r.eval_launches, **work})
+    fl = sum(p["flops"] for p in roof_parts)
+    ins = sum(p["inst"] for p in roof_parts)
+    ems = sum(p["eval_ms"] for p in roof_parts)
+    nl = sum(p["launches"] for p in roof_parts)
+    calls = {k: sum(p.get(k, 0) for p in roof_parts) for k in ("exp", "sincos", "div")}
+    achieved = fl / (ems * 1e-3) / 1e12
+    regions_per_launch = sum(int(traced[w.name].trace["s"].sum()) for w in ws) / nl
+    prof = traffic_bytes_per_region()
+    traffic = prof[0] * regions_per_launch if prof is not None else None
+    pipe_ncu = prof[1] if prof is not None else None
+    # FP64 issue slots the algorithm needs, library calls at their measured cost
+    fma_rate = peaks["fma_tflops"] * 1e12 / 2
+    slots = ins + sum(calls[k] * fma_rate / (peaks[f"{k}_gps"] * 1e9) for k in calls)
+    pipe_frac = slots / (ems * 1e-3) / fma_rate
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def step():
+        res = []
+        for w in ws:
+            res.append(run(w))
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall0 = time.perf_counter()
+    results = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        results.append(step())
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) * 1e-3
+
+    # e2e: the public call with host buffers, wall clock, copies included
+    e2e_times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        for w in ws:
+            pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions,
+                                   relerr_filter=w.relerr_filter)
+        e2e_times.append(time.perf_counter() - t0)
+
+    evals_step = sum(r.n_regions * npoints(w.dim) for r, w in zip(results[0], ws))
+    launches = sum(r.kernel_launches for res in results for r in res)
+    h2d = sum(r.h2d_bytes for r in results[0])
+    d2h = sum(r.d2h_bytes for r in results[0])
+    t_max = dev_s
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        tt = torch.tensor([dev_s, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e2e_s = float(tt[0]), float(tt[1])
+    value = world * evals_step * args.steps / t_max
+    e2e_value = world * evals_step * args.steps / e2e_s
+
+    if rank == 0:
+        from oracle import closed_forms as cf
+        per = {}
+        for w, r in zip(ws, results[0]):
+            ex = cf.closed_form(w.family, w.dim, w.params)
+            per[w.name] = {"dim": w.dim, "family": w.family, "epsrel": w.epsrel, "status": r.status,
+                           "iterations": r.iterations, "regions": r.n_regions,
+                           "estimate": r.estimate, "errorest": r.errorest,
+                           "true_relerr": abs(r.estimate - ex) / abs(ex), "within_errorest": abs(r.estimate - ex) <= r.errorest,
+                           "relerr_filter": w.relerr_filter}
+        cpu = None
+        if not args.no_cpu_baseline and world >= 1:
+            cpu = cpu_baseline(ws, args.cpu_seconds, {w.name: traced[w.name].trace for w in ws})
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded splitmix64 parameters, BASELINE ranges)",
+            "config": {"workload": wl_name, "time_to_result_ms": {n: None for n in per},
+                       "integrals": per, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "wall_s": wall},
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fma_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fma_tflops"], "traffic": traffic,
+                         "regions_per_launch": regions_per_launch,
+                         "fp64_pipe_active_ncu": pipe_ncu,
+                         "kernel": "k_evaluate_loop", "peak_source": "measured FP64 FMA chain (pagani_fp64_peak)",
+                         "avg_launch_ms": ems / nl, "flops_per_launch": fl / nl,
+                         "fp64_issue_frac_est": pipe_frac, "library_calls_per_launch":
+                             {k: v / nl for k, v in calls.items()},
+                         "measured_rates_gps": {k: peaks[k] for k in ("exp_gps", "sincos_gps", "div_gps")},
+                         "parts": [{k: p[k] for k in ("name", "eval_ms", "launches", "flops")} for p in roof_parts]},
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        # time to result of each integral (device events, from a dedicated pass)
+        for w in ws:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record()
+            run(w)
+            b.record()
+            torch.cuda.synchronize()
+            line["config"]["time_to_result_ms"][w.name] = a.elapsed_time(b)
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

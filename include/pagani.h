@@ -73,6 +73,12 @@ typedef struct {
   int64_t n_regions;      /* regions evaluated, summed over iterations       */
   int64_t n_active_last;  /* regions evaluated in the last iteration         */
   double finished_volume; /* volume of the regions classified finished       */
+  double eval_ms;         /* host-driven loop only: summed device time of the Evaluate
+                             launches, CUDA events on the launching stream; -1 otherwise */
+  int32_t eval_launches;  /* Evaluate launches of this call                   */
+  int32_t kernel_launches;/* kernels of this library launched by this call   */
+  int64_t h2d_bytes;      /* host-to-device bytes copied by this call        */
+  int64_t d2h_bytes;      /* device-to-host bytes copied by this call        */
 } pagani_result;
 
 typedef struct {
@@ -137,10 +143,12 @@ int pagani_evaluate(int dim, int integrand_id, const double* params, int64_t m, 
  * the number of rule points N(dim), or < 0 on error. */
 int pagani_rule_tables(int dim, double* radius, double* weights, int64_t* counts);
 
-/* Measures this GPU's FP64 FMA throughput with an independent-chain
- * microbenchmark (used as the roofline denominator of Evaluate).  Writes
- * TFLOP/s (2 flops per FMA) to *tflops.  Returns 0 or < 0. */
-int pagani_fp64_peak(double* tflops, void* cuda_stream);
+/* Measures this GPU's FP64 throughput with independent-chain
+ * microbenchmarks (the roofline denominators of Evaluate).  Writes up to
+ * n_out values to out: [0] FMA TFLOP/s (2 flops per FMA), [1] exp calls/s,
+ * [2] sincos calls/s, [3] divisions/s (each in units of 1e9).  Returns 0 or
+ * < 0. */
+int pagani_fp64_peak(double* out, int n_out, void* cuda_stream);
 
 /* Human-readable description of the last error on this thread. */
 const char* pagani_last_error(void);

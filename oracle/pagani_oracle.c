@@ -42,6 +42,10 @@
  *    0.95); give up after 10 direction changes or 64 probes; e_b uses |v_tot|.
  *  - Memory exhaustion (Sec. 3.5.2): if 2 (survivors) > max_regions after
  *    the threshold step, return the latest estimates with status 2.
+ *  Parity unpinned: the error formula's constants and noise floor and the
+ *  two-level formula are readings with no published values to pin them to;
+ *  they are checked only through estimates staying within their error
+ *  estimates of closed forms.
  *  - Unreachable tolerance (Sec. 3.5.3): when no region stays active, or the
  *    finished error e_f alone exceeds max(tau_rel |v + v_f|, tau_abs), stop
  *    with status 3 and the latest estimates.

@@ -33,7 +33,8 @@ class PaganiError(RuntimeError):
 class Result(ctypes.Structure):
     _fields_ = [("estimate", ctypes.c_double), ("errorest", ctypes.c_double), ("status", ctypes.c_int32),
                 ("iterations", ctypes.c_int32), ("n_regions", ctypes.c_int64), ("n_active_last", ctypes.c_int64),
-                ("finished_volume", ctypes.c_double)]
+                ("finished_volume", ctypes.c_double), ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,7 +88,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.pagani_evaluate.restype = ctypes.c_int
     lib.pagani_rule_tables.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64)]
     lib.pagani_rule_tables.restype = ctypes.c_int
-    lib.pagani_fp64_peak.argtypes = [P(ctypes.c_double), ctypes.c_void_p]
+    lib.pagani_fp64_peak.argtypes = [P(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]
     lib.pagani_fp64_peak.restype = ctypes.c_int
     lib.pagani_last_error.argtypes = []
     lib.pagani_last_error.restype = ctypes.c_char_p
@@ -121,11 +122,22 @@ class Integration:
     n_regions: int
     n_active_last: int
     finished_volume: float
+    eval_ms: float = -1.0
+    eval_launches: int = 0
+    kernel_launches: int = 0
+    h2d_bytes: int = 0
+    d2h_bytes: int = 0
     trace: np.ndarray | None = None
 
     @property
     def status_name(self) -> str:
         return STATUS_NAMES.get(self.status, str(self.status))
+
+
+def _integration(r: Result, trace=None) -> Integration:
+    return Integration(r.estimate, r.errorest, r.status, r.iterations, r.n_regions, r.n_active_last,
+                       r.finished_volume, r.eval_ms, r.eval_launches, r.kernel_launches, r.h2d_bytes, r.d2h_bytes,
+                       trace)
 
 
 def pagani_integrate(dim: int, integrand_id: int, params, epsrel: float, epsabs: float = 1e-20,
@@ -137,8 +149,7 @@ def pagani_integrate(dim: int, integrand_id: int, params, epsrel: float, epsabs:
     rc = lib.pagani_integrate(dim, integrand_id, pp, epsrel, epsabs, max_regions, ctypes.byref(r))
     if rc < 0:
         raise PaganiError(f"pagani_integrate failed ({rc}): {last_error()}")
-    return Integration(r.estimate, r.errorest, r.status, r.iterations, r.n_regions, r.n_active_last,
-                       r.finished_volume)
+    return _integration(r)
 
 
 def pagani_integrate_ex(dim: int, integrand_id: int, params, epsrel: float, epsabs: float = 1e-20,
@@ -159,8 +170,7 @@ def pagani_integrate_ex(dim: int, integrand_id: int, params, epsrel: float, epsa
         raise PaganiError(f"pagani_integrate_ex failed ({rc}): {last_error()}")
     if trace:
         tr = tr[:max(min(r.iterations, it_max), 0)].copy()
-    return Integration(r.estimate, r.errorest, r.status, r.iterations, r.n_regions, r.n_active_last,
-                       r.finished_volume, tr)
+    return _integration(r, tr)
 
 
 def pagani_workspace_reserve(max_regions: int, dim: int) -> None:
@@ -217,12 +227,13 @@ def pagani_rule_tables(dim: int):
     return npts, rad, w.reshape(9, 5), cnt
 
 
-def pagani_fp64_peak(stream: int | None = None) -> float:
-    out = ctypes.c_double(0.0)
-    rc = load().pagani_fp64_peak(ctypes.byref(out), ctypes.c_void_p(stream or 0))
+def pagani_fp64_peak(stream: int | None = None) -> dict:
+    """Measured FP64 throughput: FMA TFLOP/s and exp, sincos, division rates (1e9/s)."""
+    out = (ctypes.c_double * 4)()
+    rc = load().pagani_fp64_peak(out, 4, ctypes.c_void_p(stream or 0))
     if rc < 0:
         raise PaganiError(f"pagani_fp64_peak failed ({rc}): {last_error()}")
-    return out.value
+    return {"fma_tflops": out[0], "exp_gps": out[1], "sincos_gps": out[2], "div_gps": out[3]}
 
 
 def version() -> str:

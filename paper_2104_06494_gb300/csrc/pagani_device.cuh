@@ -94,6 +94,71 @@ __device__ __forceinline__ bool last_block_arrived(unsigned int* ticket) {
   return is_last;
 }
 
+// ---------------------------------------------------------------------------
+// Combining per-block partials in the last block.  A one-lane FP64 instruction
+// occupies the FP64 pipe like a full warp's, so the partials are combined by
+// every thread of the block (a strided pass, then warp shuffles and a fixed
+// warp order: the result is deterministic for a fixed grid).
+__device__ __forceinline__ EvalPartial eval_identity() {
+  EvalPartial p;
+  p.v.s = p.v.c = p.e.s = p.e.c = 0.0;
+  p.emin = __longlong_as_double(0x7ff0000000000000LL);
+  p.emax = -p.emin;
+  p.n_rel = 0;
+  p.nonfinite = 0;
+  p.pad = 0;
+  return p;
+}
+__device__ __forceinline__ EvalPartial eval_combine(EvalPartial a, const EvalPartial& b) {
+  a.v = ncomb(a.v, b.v);
+  a.e = ncomb(a.e, b.e);
+  a.emin = fmin(a.emin, b.emin);
+  a.emax = fmax(a.emax, b.emax);
+  a.n_rel += b.n_rel;
+  a.nonfinite |= b.nonfinite;
+  return a;
+}
+__device__ __forceinline__ EvalPartial eval_shfl(const EvalPartial& a, int off) {
+  EvalPartial b;
+  b.v = shfl_down_nsum(a.v, off);
+  b.e = shfl_down_nsum(a.e, off);
+  b.emin = __shfl_down_sync(0xffffffffu, a.emin, off);
+  b.emax = __shfl_down_sync(0xffffffffu, a.emax, off);
+  b.n_rel = __shfl_down_sync(0xffffffffu, a.n_rel, off);
+  b.nonfinite = __shfl_down_sync(0xffffffffu, a.nonfinite, off);
+  b.pad = 0;
+  return b;
+}
+template <int THREADS>
+__device__ __forceinline__ EvalPartial eval_block_combine(EvalPartial acc, EvalPartial* sh) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc = eval_combine(acc, eval_shfl(acc, off));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < THREADS / 32; ++w) acc = eval_combine(acc, sh[w]);
+  return acc;  // valid on thread 0
+}
+template <int THREADS>
+__device__ __forceinline__ EvalPartial eval_reduce_partials(const EvalPartial* parts, int n, EvalPartial* sh) {
+  EvalPartial acc = eval_identity();
+  for (int b = threadIdx.x; b < n; b += THREADS) acc = eval_combine(acc, parts[b]);
+  return eval_block_combine<THREADS>(acc, sh);
+}
+
+template <int THREADS>
+__device__ __forceinline__ NSum nsum_block_combine(NSum a, NSum* sh) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a = ncomb(a, shfl_down_nsum(a, off));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < THREADS / 32; ++w) a = ncomb(a, sh[w]);
+  return a;  // valid on thread 0
+}
+
 __device__ __forceinline__ void set_cond(int use_graph, cudaGraphConditionalHandle h, unsigned int v) {
   if (use_graph) cudaGraphSetConditional(h, v);
 }
@@ -167,6 +232,7 @@ __device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long 
 // another probe is needed.
 __device__ inline int threshold_step(Ctrl& c, long long n_active, double sum_ae) {
   c.probes += 1;
+  c.total_probes += 1;
   long long s_abar = c.s - n_active;
   int dir;
   if ((double)s_abar > 0.5 * (double)c.s) {       // memory requirement

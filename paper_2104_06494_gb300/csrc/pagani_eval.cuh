@@ -424,40 +424,28 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
     nonfinite |= __shfl_down_sync(0xffffffffu, nonfinite, off);
   }
   __shared__ EvalPartial wp[THREADS / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    wp[warp].v = sv;
-    wp[warp].e = se;
-    wp[warp].emin = emin;
-    wp[warp].emax = emax;
-    wp[warp].n_rel = nrel;
-    wp[warp].nonfinite = nonfinite;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    EvalPartial bp = wp[0];
-    for (int w = 1; w < THREADS / 32; ++w) {
-      bp.v = ncomb(bp.v, wp[w].v);
-      bp.e = ncomb(bp.e, wp[w].e);
-      bp.emin = fmin(bp.emin, wp[w].emin);
-      bp.emax = fmax(bp.emax, wp[w].emax);
-      bp.n_rel += wp[w].n_rel;
-      bp.nonfinite |= wp[w].nonfinite;
+  {
+    EvalPartial mine;
+    mine.v = sv;
+    mine.e = se;
+    mine.emin = emin;
+    mine.emax = emax;
+    mine.n_rel = nrel;
+    mine.nonfinite = nonfinite;
+    mine.pad = 0;
+    // (the shuffles above already combined each warp; combine the warps)
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      EvalPartial bp = wp[0];
+      for (int w = 1; w < THREADS / 32; ++w) bp = eval_combine(bp, wp[w]);
+      A.eval_part[blockIdx.x] = bp;
     }
-    A.eval_part[blockIdx.x] = bp;
   }
   if (!last_block_arrived(&c.ticket_eval)) return;
+  const EvalPartial tot = eval_reduce_partials<THREADS>(A.eval_part, gridDim.x, wp);
   if (threadIdx.x == 0) {
-    EvalPartial tot = A.eval_part[0];
-    for (unsigned b = 1; b < gridDim.x; ++b) {
-      const EvalPartial& bp = A.eval_part[b];
-      tot.v = ncomb(tot.v, bp.v);
-      tot.e = ncomb(tot.e, bp.e);
-      tot.emin = fmin(tot.emin, bp.emin);
-      tot.emax = fmax(tot.emax, bp.emax);
-      tot.n_rel += bp.n_rel;
-      tot.nonfinite |= bp.nonfinite;
-    }
     int search = finalize_iteration_head(c, nval(tot.v), nval(tot.e), tot.n_rel, tot.emin, tot.emax,
                                          tot.nonfinite, A.trace, A.trace_cap);
     set_cond(A.use_graph, A.h_probe, (unsigned)search);

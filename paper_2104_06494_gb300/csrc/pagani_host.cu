@@ -123,13 +123,15 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
     A.probe_part[blockIdx.x].n_active = bn;
   }
   if (!last_block_arrived(&c.ticket_probe)) return;
+  NSum pa = {0.0, 0.0};
+  long long pn = 0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS) {
+    pa = ncomb(pa, A.probe_part[b].ea);
+    pn += A.probe_part[b].n_active;
+  }
+  const NSum tot = nsum_block_combine<THREADS>(pa, shn);
+  const long long n = block_sum_ll<THREADS>(pn, shl);
   if (threadIdx.x == 0) {
-    NSum tot = A.probe_part[0].ea;
-    long long n = A.probe_part[0].n_active;
-    for (unsigned b = 1; b < gridDim.x; ++b) {
-      tot = ncomb(tot, A.probe_part[b].ea);
-      n += A.probe_part[b].n_active;
-    }
     const int cont = threshold_step(c, n, nval(tot));
     c.search_cont = cont;
     set_cond(A.use_graph, A.h_probe, (unsigned)cont);
@@ -214,15 +216,20 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     A.pool.tile_offset[t] = run;
     run += x;
   }
-  __syncthreads();
-  if (threadIdx.x != THREADS - 1) return;
-  const long long n_surv = run;  // end of the last chunk = total survivors
-  NSum tva = A.count_part[0].va, tea = A.count_part[0].ea, tfv = A.count_part[0].finvol;
-  for (unsigned b = 1; b < gridDim.x; ++b) {
-    tva = ncomb(tva, A.count_part[b].va);
-    tea = ncomb(tea, A.count_part[b].ea);
-    tfv = ncomb(tfv, A.count_part[b].finvol);
+  __shared__ long long total_surv;
+  if (threadIdx.x == THREADS - 1) total_surv = run;  // end of the last chunk
+  NSum pva = {0.0, 0.0}, pea = {0.0, 0.0}, pfv = {0.0, 0.0};
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS) {
+    pva = ncomb(pva, A.count_part[b].va);
+    pea = ncomb(pea, A.count_part[b].ea);
+    pfv = ncomb(pfv, A.count_part[b].finvol);
   }
+  const NSum tva = nsum_block_combine<THREADS>(pva, shn);
+  const NSum tea = nsum_block_combine<THREADS>(pea, shn);
+  const NSum tfv = nsum_block_combine<THREADS>(pfv, shn);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const long long n_surv = total_surv;
   c.n_surv = n_surv;
   const bool tr_ok = c.trace_on && c.it - 1 < A.trace_cap;
   TraceRec* tr = tr_ok ? &A.trace[c.it - 1] : nullptr;
@@ -332,6 +339,24 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
 }
 
 // ------------------------------------------------------- FP64 peak probe
+__global__ void k_fp64_calls(double* out, int iters, int which) {
+  double x = 1e-3 * (threadIdx.x + 1), s = 0.0, c = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    if (which == 0) {
+      s += exp(-x);
+    } else if (which == 1) {
+      double sn, cs;
+      sincos(x, &sn, &cs);
+      s += sn;
+      c += cs;
+    } else {
+      s += 1.0 / x;
+    }
+    x += 1e-7;
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s + c;
+}
+
 __global__ void k_fp64_fma(double* out, int iters, double a, double b) {
   double x[8];
 #pragma unroll
@@ -538,7 +563,7 @@ static int launch_config(const FamilyKernels& fk, int n, Launch* L) {
     return fail(PAGANI_ERR_CUDA, std::string("evaluate kernel does not fit: ") + cudaGetErrorString(e));
   L->eval_grid = w.sms * occ;
   if (L->eval_grid > w.max_grid) L->eval_grid = w.max_grid;
-  L->mgmt_grid = w.sms * 8;
+  L->mgmt_grid = w.sms * 2;
   if (L->mgmt_grid > w.max_grid) L->mgmt_grid = w.max_grid;
   return 0;
 }
@@ -697,6 +722,9 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
     k_uniform_split<<<(int)((s0 + 255) / 256), 256, 0, st>>>(p, d0, log2d, s0);
     PG_CK(cudaGetLastError());
   }
+  int64_t h2d = sizeof(Ctrl) + sizeof(prm), d2h = 0;
+  int launches = 1, eval_launches = 0;  // the Uniform-Split kernel
+  out->eval_ms = -1.0;
   if (o.use_graph) {
     const int key = fam * 16 + n + (w.n << 8);
     auto it = w.graphs.find(key);
@@ -709,18 +737,35 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
     PG_CK(cudaGraphLaunch(it->second.exec, st));
     PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     PG_CK(cudaStreamSynchronize(st));
+    d2h += sizeof(Ctrl);
   } else {
+    // host-driven loop: the same kernels, one launch each, with CUDA events
+    // around every Evaluate launch on the launching stream
     const LoopArgs args = loop_args(0, 0, 0);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    PG_CK(cudaEventCreate(&ev0));
+    PG_CK(cudaEventCreate(&ev1));
+    double eval_ms = 0.0;
     for (int guard = 0; guard < o.it_max + 2; ++guard) {
+      PG_CK(cudaEventRecord(ev0, st));
       PG_CK(fk.loop[n](rule, args, L.eval_grid, L.eval_block, L.eval_smem, st));
+      PG_CK(cudaEventRecord(ev1, st));
+      ++launches;
       PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       PG_CK(cudaStreamSynchronize(st));
+      d2h += sizeof(Ctrl);
+      float ms = 0.f;
+      PG_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+      eval_ms += ms;
+      ++eval_launches;
       if (h.search) {
         for (int probe = 0; probe < 128; ++probe) {
           k_probe<kMgmtThreads><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
           PG_CK(cudaGetLastError());
+          ++launches;
           PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
           PG_CK(cudaStreamSynchronize(st));
+          d2h += sizeof(Ctrl);
           if (!h.search_cont) break;
         }
       }
@@ -728,10 +773,15 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
       PG_CK(cudaGetLastError());
       k_split<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
       PG_CK(cudaGetLastError());
+      launches += 2;
       PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       PG_CK(cudaStreamSynchronize(st));
+      d2h += sizeof(Ctrl);
       if (h.done) break;
     }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    out->eval_ms = eval_ms;
   }
   if (trace && trace_cap > 0) {
     const int nrec = std::min(std::min(h.it, trace_cap), w.trace_cap);
@@ -741,9 +791,19 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
       PG_CK(cudaStreamSynchronize(st));
       static_assert(sizeof(TraceRec) == sizeof(pagani_trace_record), "trace layout");
       std::memcpy(trace, tmp.data(), sizeof(TraceRec) * nrec);
+      d2h += (int64_t)sizeof(TraceRec) * nrec;
     }
   }
 #undef PG_CK
+  if (o.use_graph) {
+    // the graph ran one Evaluate, count and split per iteration plus the probes
+    eval_launches = h.it;
+    launches += 3 * h.it + h.total_probes;
+  }
+  out->eval_launches = eval_launches;
+  out->kernel_launches = launches;
+  out->h2d_bytes = h2d;
+  out->d2h_bytes = d2h;
   out->estimate = h.estimate;
   out->errorest = h.errorest;
   out->iterations = h.it;
@@ -865,37 +925,47 @@ int pagani_rule_tables(int dim, double* radius, double* weights, int64_t* counts
   return t.num_points;
 }
 
-int pagani_fp64_peak(double* tflops, void* cuda_stream) {
-  if (!tflops) return fail(PAGANI_ERR_ARGUMENT, "tflops is NULL");
+int pagani_fp64_peak(double* outv, int n_out, void* cuda_stream) {
+  if (!outv || n_out < 1) return fail(PAGANI_ERR_ARGUMENT, "out is NULL");
   std::lock_guard<std::mutex> lk(g_mu);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const int grid = sms * 4, block = 256, iters = 4096;
+  const int grid = sms * 4, block = 256;
   double* buf = nullptr;
   cudaError_t e = cudaMalloc(&buf, sizeof(double) * grid * block);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  k_fp64_fma<<<grid, block, 0, st>>>(buf, 64, 1.0000001, 1e-9);
-  float best = 1e30f;
-  for (int rep = 0; rep < 3; ++rep) {
-    cudaEventRecord(a, st);
-    k_fp64_fma<<<grid, block, 0, st>>>(buf, iters, 1.0000001, 1e-9);
-    cudaEventRecord(b, st);
-    cudaEventSynchronize(b);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (ms < best) best = ms;
+  auto best_ms = [&](auto launch) {
+    launch();  // warm-up
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(a, st);
+      launch();
+      cudaEventRecord(b, st);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) best = ms;
+    }
+    return (double)best;
+  };
+  const int iters = 4096;
+  double ms = best_ms([&] { k_fp64_fma<<<grid, block, 0, st>>>(buf, iters, 1.0000001, 1e-9); });
+  outv[0] = 2.0 * 8.0 * iters * (double)grid * block / (ms * 1e-3) / 1e12;
+  const int citers = 512;
+  for (int w = 0; w < 3 && 1 + w < n_out; ++w) {
+    ms = best_ms([&] { k_fp64_calls<<<grid, block, 0, st>>>(buf, citers, w); });
+    outv[1 + w] = citers * (double)grid * block / (ms * 1e-3) / 1e9;
   }
   e = cudaGetLastError();
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(buf);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
-  *tflops = 2.0 * 8.0 * iters * (double)grid * block / (best * 1e-3) / 1e12;
   return 0;
 }
 

@@ -99,6 +99,7 @@ struct Ctrl {
   unsigned int ticket_eval, ticket_probe, ticket_count, ticket_split;
   int32_t watchdog;          // set if a kernel saw an impossible state
   int32_t loop_guard;        // iterations counted by the count kernel
+  int32_t total_probes;      // threshold probes over the whole call
 };
 
 // One per-iteration record (mirrors pagani_trace_record in pagani.h).

@@ -1,0 +1,207 @@
+"""Algorithmic work of the Evaluate kernel, for its roofline.
+
+Evaluate is bound by the FP64 pipe (GB300 issues about 2 FP64 FMA per clock
+per SM), so its roofline is FP64 throughput.  The counts below follow the
+kernel's loop structure (csrc/pagani_eval.cuh) operation by operation, per
+sibling pair (one thread):
+
+* the per-axis factor table: 11 coordinate codes on n + 1 axes (the pair
+  shares n - 1 axes, and the split axis is patched for the right region);
+* per region: prefix/suffix partial products, the one-axis, pair, triple and
+  vertex orbits (one product or sum per point from shared partials), the
+  nine generator sums, the fourth differences, rule and null-rule weighting,
+  the noise floors, the error formula and the split axis;
+* per pair: the two-level refinement; per region: the compensated partial
+  sums and Rel-Err-Classify.
+
+flops count an FMA as 2 and every other add/mul as 1; `inst` counts FP64
+arithmetic instructions (an FMA is one).  Library calls (exp, sincos,
+division: CUDA's own implementations) are counted separately and never
+converted into flops.
+"""
+from __future__ import annotations
+
+from collections import Counter
+
+PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0 = 0, 1, 2, 3, 4
+
+
+def num_points(n: int) -> int:
+    return 1 + 8 * n + 6 * n * (n - 1) + 4 * n * (n - 1) * (n - 2) // 3 + 2 ** n
+
+
+def _pow_mults(e: int) -> int:
+    """Multiplications of the binary powering r^e as the kernel writes it
+    (the first multiply into y = 1 folds away)."""
+    mults, first = 0, True
+    while e > 0:
+        if e & 1:
+            mults += 0 if first else 1
+            first = False
+        if e > 1:
+            mults += 1
+        e >>= 1
+    return mults
+
+
+def region_points_work(family: int, n: int) -> Counter:
+    """FP64 work of the rule sums of one region (rule_sums in the kernel)."""
+    c = Counter()
+    cplx = family == OSCILLATORY
+    corner = family == CORNER_PEAK
+    base_identity = family in (PRODUCT_PEAK, GAUSSIAN, C0)
+
+    def mul(k=1):
+        if cplx:          # (a.x b.x - a.y b.y, a.x b.y + a.y b.x): 2 MUL + 2 FMA
+            c["flops"] += 6 * k
+            c["inst"] += 4 * k
+        else:             # one MUL (or ADD for the corner peak's sums)
+            c["flops"] += k
+            c["inst"] += k
+
+    def outer(k=1):       # corner peak: 1 / s, then r^(n+1)
+        c["div"] += k
+        pm = _pow_mults(n + 1)
+        c["flops"] += pm * k
+        c["inst"] += pm * k
+
+    def last(k=1):
+        if cplx:          # real part only: 1 MUL + 1 FMA
+            c["flops"] += 3 * k
+            c["inst"] += 2 * k
+        else:
+            c["flops"] += k
+            c["inst"] += k
+        if corner:
+            outer(k)
+
+    def add(k=1):
+        c["flops"] += k
+        c["inst"] += k
+
+    # prefix and suffix partial products
+    mul(n - 1 if base_identity else n)
+    mul(max(n - 2, 0))
+    if corner:
+        outer(1)          # f at the centre
+    # one-axis orbits and fourth differences
+    for j in range(n):
+        if j < n - 1:
+            mul()
+        last(8)
+        add(8)
+        c["flops"] += 8   # (p + m - 2 f0) - q (p' + m' - 2 f0): 3 FMA + 2 ADD
+        c["inst"] += 5
+    # axis pairs
+    for j in range(n - 1):
+        for k in range(j + 1, n):
+            if k > j + 1:
+                mul()
+            if k < n - 1:
+                mul()
+            mul(4)
+            last(12)
+            add(12)
+    # axis triples
+    for j in range(n - 2):
+        for k in range(j + 1, n - 1):
+            if k > j + 1:
+                mul()
+            mul(2 + 4)
+            mid_id = True
+            for l in range(k + 1, n):
+                if l > k + 1:
+                    if not mid_id:
+                        mul()
+                    mid_id = False
+                if l == n - 1:
+                    c_id = mid_id
+                else:
+                    if not mid_id:
+                        mul()
+                    c_id = False
+                for _ in range(4):
+                    if not c_id:
+                        mul()
+                    last(2)
+                    add(2)
+    # vertices: half tables
+    h1 = n // 2
+    h2 = n - h1
+    for t in range(1, h2):
+        mul(2 * (1 << t))
+    for _ in range(1 << h1):
+        mul(h1 - 1 if base_identity else h1)
+        last(1 << h2)
+        add(1 << h2)
+    return c
+
+
+def region_epilogue_work() -> Counter:
+    """Weighting (9 generators x (basic + 4 null + 4 floor scales) FMA), the
+    volume products, the noise floors, the error formula and the axis."""
+    c = Counter()
+    c["flops"] += 2 * 81 + 1 + 4 + 8 + 4 + 1
+    c["inst"] += 81 + 1 + 4 + 8 + 4 + 1
+    c["div"] += 2
+    return c
+
+
+def pair_table_work(family: int, n: int) -> Counter:
+    """The 11-code factor table on n + 1 axes, plus the axis set-up."""
+    c = Counter()
+    axes = n + 1
+    entries = 11 * axes
+    c["flops"] += 2 * axes          # h = w/2, c = lower + h
+    c["inst"] += 2 * axes
+    c["flops"] += 2 * entries       # x = fma(h, g, c)
+    c["inst"] += entries
+    if family == PRODUCT_PEAK:
+        c["flops"] += axes          # c^-2 = 1/(c c)
+        c["inst"] += axes
+        c["div"] += axes + entries  # and 1/(c^-2 + t^2) per entry
+        c["flops"] += 3 * entries   # t = x - w, fma(t, t, c^-2)
+        c["inst"] += 2 * entries
+    elif family == GAUSSIAN:
+        c["flops"] += 3 * entries   # x - w, a(x - w), u u
+        c["inst"] += 3 * entries
+        c["exp"] += entries
+    elif family == C0:
+        c["flops"] += 2 * entries   # x - w, a |x - w|
+        c["inst"] += 2 * entries
+        c["exp"] += entries
+    elif family == OSCILLATORY:
+        c["flops"] += entries       # a x
+        c["inst"] += entries
+        c["sincos"] += entries
+    elif family == CORNER_PEAK:
+        c["flops"] += entries       # a x
+        c["inst"] += entries
+    return c
+
+
+def pair_work(family: int, n: int, two_level: bool) -> Counter:
+    c = Counter()
+    c.update(pair_table_work(family, n))
+    for _ in range(2):
+        c.update(region_points_work(family, n))
+        c.update(region_epilogue_work())
+        c["flops"] += 9             # two compensated adds and the rel-err test
+        c["inst"] += 9
+    if two_level:
+        c["flops"] += 11
+        c["inst"] += 8
+        c["div"] += 1
+    return c
+
+
+def evaluate_work(family: int, n: int, regions_per_iteration) -> Counter:
+    """Total algorithmic work of the Evaluate launches of one integration,
+    given the region count of every iteration (first iteration: no parents,
+    no two-level refinement)."""
+    tot = Counter()
+    for it, s in enumerate(regions_per_iteration):
+        w = pair_work(family, n, two_level=it > 0)
+        for k, v in w.items():
+            tot[k] += v * (int(s) // 2)
+    return tot

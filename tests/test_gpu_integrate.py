@@ -124,3 +124,16 @@ def test_configs_within_errorest_of_closed_form(pg, name):
     ex = cf.closed_form(w.family, w.dim, w.params)
     assert g.status in (0, 3)
     assert abs(g.estimate - ex) <= g.errorest
+
+
+def test_bench_workload_gaussian_d5_full_size(pg):
+    """The bench's 5-D Gaussian at its full size (epsrel 1e-7, ~2.1e6
+    regions over 11 iterations), in the launch configuration bench.py times
+    (graph loop, library workspace): the same region-set evolution as the
+    oracle and the estimate within 1e-12."""
+    w = config_workloads()["gaussian_d5"]
+    o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions)
+    g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
+    compare_runs(g, o)
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    assert abs(g.estimate - ex) <= g.errorest
