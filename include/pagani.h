@@ -115,6 +115,32 @@ int pagani_integrate_ex(int dim, int integrand_id, const double* params, double 
                         int64_t max_regions, const pagani_options* opt, void* cuda_stream, pagani_result* out,
                         pagani_trace_record* trace, int trace_cap);
 
+/* Allocation-free integration, for callers that cannot allocate device
+ * memory: code that runs while a CUDA stream is being captured, applications
+ * whose own allocator owns the device memory, and loops that must not pay for
+ * an allocation.  The paper has no counterpart; it is a deployment variant of
+ * pagani_integrate.
+ *
+ * Same arguments and result as pagani_integrate (default options; rel-err
+ * filtering is off for the oscillatory family, on otherwise), plus a stream
+ * (NULL = the legacy default stream).  Instead of the library workspace it
+ * uses a 32 MiB array in the library's device memory, which every GPU that
+ * loads the library holds until the process exits.  It runs the loop kernels
+ * with one host synchronisation per step (no CUDA graph) and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * max_regions is limited by the array: on a 152-SM GPU about 540,000
+ * regions at dim 2, 420,000 at dim 3, 290,000 at dim 5 and 190,000 at dim 8;
+ * larger values return PAGANI_ERR_CAPACITY with the limit in
+ * pagani_last_error().  The first call on a device looks the array's
+ * address up with that device current; make that first call before any
+ * stream capture.  All calls share the array: calls whose GPU work overlaps
+ * (other streams, other host threads with their own device contexts) race
+ * on it.  Each call rewrites everything it reads, so the previous call's
+ * contents do not leak into a result.  Returns out->status. */
+int pagani_integrate_noalloc(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
+                             int64_t max_regions, void* cuda_stream, pagani_result* out);
+
 /* Allocates (or grows) the library workspace for up to max_regions regions
  * of dimension dim so that later calls do not allocate (the paper times
  * integration without workspace set-up, Sec. 4).  Returns 0 or < 0. */

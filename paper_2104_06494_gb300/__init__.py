@@ -53,7 +53,7 @@ TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.i
 # every symbol include/pagani.h declares
 EXPORTED = ["pagani_default_options", "pagani_integrate", "pagani_integrate_ex", "pagani_workspace_reserve",
             "pagani_workspace_release", "pagani_evaluate", "pagani_rule_tables", "pagani_fp64_peak",
-            "pagani_last_error", "pagani_version"]
+            "pagani_last_error", "pagani_version", "pagani_integrate_noalloc"]
 
 _lib = None
 
@@ -78,6 +78,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                         ctypes.c_double, ctypes.c_int64, P(Options), ctypes.c_void_p, P(Result),
                                         ctypes.c_void_p, ctypes.c_int]
     lib.pagani_integrate_ex.restype = ctypes.c_int
+    lib.pagani_integrate_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, P(Result)]
+    lib.pagani_integrate_noalloc.restype = ctypes.c_int
     lib.pagani_workspace_reserve.argtypes = [ctypes.c_int64, ctypes.c_int]
     lib.pagani_workspace_reserve.restype = ctypes.c_int
     lib.pagani_workspace_release.argtypes = []
@@ -171,6 +174,21 @@ def pagani_integrate_ex(dim: int, integrand_id: int, params, epsrel: float, epsa
     if trace:
         tr = tr[:max(min(r.iterations, it_max), 0)].copy()
     return _integration(r, tr)
+
+
+def pagani_integrate_noalloc(dim: int, integrand_id: int, params, epsrel: float, epsabs: float = 1e-20,
+                             max_regions: int = 100_000, stream: int | None = None,
+                             raise_on_error: bool = True) -> Integration:
+    """C ABI pagani_integrate_noalloc: the allocation-free integration for
+    callers that cannot allocate device memory (see include/pagani.h)."""
+    lib = load()
+    p, pp = _params_array(params)
+    r = Result()
+    rc = lib.pagani_integrate_noalloc(dim, integrand_id, pp, epsrel, epsabs, max_regions,
+                                      ctypes.c_void_p(stream or 0), ctypes.byref(r))
+    if rc < 0 and raise_on_error:
+        raise PaganiError(f"pagani_integrate_noalloc failed ({rc}): {last_error()}")
+    return _integration(r)
 
 
 def pagani_workspace_reserve(max_regions: int, dim: int) -> None:

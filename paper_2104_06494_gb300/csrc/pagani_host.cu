@@ -818,6 +818,210 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   return out->status;
 }
 
+// ------------------------------------------------------ allocation-free path
+// Some callers cannot call cudaMalloc: code running while a CUDA stream is
+// being captured, applications whose allocator owns all device memory, or
+// latency-critical loops that must not allocate.  pagani_integrate_noalloc
+// serves them: it runs the same loop kernels on scratch memory carved from
+// this file-scope array instead of the library workspace.  Every GPU that
+// loads the library holds the array until the process exits.
+constexpr size_t kNoallocBytes = (size_t)32 << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Host code may not use g_noalloc_scratch directly (its host-side name is a
+// stand-in, not a device address); this is the device address per device,
+// looked up once with that device current.
+static void* g_noalloc_base[64] = {nullptr};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct NoallocLayout {
+  size_t ctrl, prm, eval_part, probe_part, count_part, lower, level, V, E, K, Vp, tile_count, tile_offset, total;
+};
+
+static NoallocLayout noalloc_layout(int64_t cap, int n, int max_grid) {
+  NoallocLayout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  const int64_t ntiles = cap / kTile + 2;
+  L.ctrl = take(sizeof(Ctrl));
+  L.prm = take(sizeof(IntegrandParams));
+  L.eval_part = take(sizeof(EvalPartial) * (size_t)max_grid);
+  L.probe_part = take(sizeof(ProbePartial) * (size_t)max_grid);
+  L.count_part = take(sizeof(CountPartial) * (size_t)max_grid);
+  L.lower = take(sizeof(double) * 2 * (size_t)n * cap);
+  L.level = take((size_t)2 * n * cap);
+  L.V = take(sizeof(double) * (size_t)cap);
+  L.E = take(sizeof(double) * (size_t)cap);
+  L.K = take((size_t)cap);
+  L.Vp = take(sizeof(double) * (size_t)(cap / 2 + 1));
+  L.tile_count = take(sizeof(long long) * (size_t)ntiles);
+  L.tile_offset = take(sizeof(long long) * (size_t)ntiles);
+  L.total = off;
+  return L;
+}
+
+// Largest region capacity (a multiple of 4096) whose layout fits the array.
+static int64_t noalloc_capacity(int n, int max_grid) {
+  int64_t lo = 0, hi = (int64_t)(kNoallocBytes / (size_t)(18 * n + 25)) + 4096;
+  while (hi - lo > 4096) {
+    const int64_t mid = ((lo + hi) / 2 / 4096) * 4096;
+    if (mid <= lo) break;
+    if (noalloc_layout(mid, n, max_grid).total <= kNoallocBytes) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+static int integrate_noalloc_locked(int n, int fam, const double* params, double epsrel, double epsabs,
+                                    int64_t max_regions, cudaStream_t st, pagani_result* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->eval_ms = -1.0;
+  if (n < PAGANI_MIN_DIM || n > PAGANI_MAX_DIM) return out->status = fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
+  if (fam < 0 || fam >= kNumFamilies) return out->status = fail(PAGANI_ERR_INTEGRAND, "unknown integrand_id");
+  if (!params) return out->status = fail(PAGANI_ERR_ARGUMENT, "params is NULL");
+  if (!(epsrel > 0.0) || !(epsabs >= 0.0) || !std::isfinite(epsrel) || !std::isfinite(epsabs))
+    return out->status = fail(PAGANI_ERR_TOLERANCE, "need epsrel > 0 and epsabs >= 0, finite");
+  int rc = check_params(fam, n, params);
+  if (rc) return out->status = rc;
+  const int d0 = default_init_div(n);
+  int log2d = 0;
+  while ((1 << log2d) < d0) ++log2d;
+  int64_t s0 = 1;
+  for (int j = 0; j < n; ++j) s0 *= d0;
+  if (s0 > max_regions) return out->status = fail(PAGANI_ERR_CAPACITY, "max_regions below the initial split");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64)
+    return out->status = fail(PAGANI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int max_grid = sms * 16;
+  const int64_t cap_max = noalloc_capacity(n, max_grid);
+  if (max_regions > cap_max)
+    return out->status = fail(PAGANI_ERR_CAPACITY,
+                              "max_regions " + std::to_string(max_regions) + " exceeds the allocation-free capacity " +
+                                  std::to_string(cap_max) + " regions for dim " + std::to_string(n) +
+                                  " (32 MiB static scratch)");
+  if (!g_noalloc_base[dev]) {
+    // set-up, once per device, with that device current
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return out->status = fail(PAGANI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_base[dev] = ptr;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+  const RuleTable* rt = get_rule(n);
+  if (!rt) return out->status = fail(PAGANI_ERR_CUDA, "rule construction failed");
+  const FamilyKernels& fk = family_kernels(fam);
+  // launch shape as in the workspace path
+  Launch Lc;
+  Lc.eval_block = fk.threads;
+  Lc.eval_smem = (size_t)fk.table_bytes_per_thread[n] * fk.threads;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fk.loop_fn[n], fk.threads, Lc.eval_smem);
+  if (e != cudaSuccess || occ < 1) return out->status = fail(PAGANI_ERR_CUDA, "evaluate kernel does not fit");
+  Lc.eval_grid = sms * occ < max_grid ? sms * occ : max_grid;
+  Lc.mgmt_grid = sms * 2;
+  const int64_t cap = ((max_regions + 4095) / 4096) * 4096;
+  const NoallocLayout L = noalloc_layout(cap, n, max_grid);
+  LoopArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.pool.lower = reinterpret_cast<double*>(base + L.lower);
+  a.pool.level = base + L.level;
+  a.pool.V = reinterpret_cast<double*>(base + L.V);
+  a.pool.E = reinterpret_cast<double*>(base + L.E);
+  a.pool.K = base + L.K;
+  a.pool.Vp = reinterpret_cast<double*>(base + L.Vp);
+  a.pool.tile_count = reinterpret_cast<long long*>(base + L.tile_count);
+  a.pool.tile_offset = reinterpret_cast<long long*>(base + L.tile_offset);
+  a.pool.cap = cap;
+  a.pool.n = n;
+  a.ctrl = reinterpret_cast<Ctrl*>(base + L.ctrl);
+  a.prm = reinterpret_cast<const IntegrandParams*>(base + L.prm);
+  a.eval_part = reinterpret_cast<EvalPartial*>(base + L.eval_part);
+  a.probe_part = reinterpret_cast<ProbePartial*>(base + L.probe_part);
+  a.count_part = reinterpret_cast<CountPartial*>(base + L.count_part);
+  a.trace = nullptr;
+  a.trace_cap = 0;
+  a.use_graph = 0;
+  // every call starts from a fully written control block (tickets, sums and
+  // counters at zero) and parameter block; the pool, partials and tile
+  // arrays are written before they are read, so stale contents of the
+  // previous call do not matter
+  Ctrl h;
+  std::memset(&h, 0, sizeof(h));
+  h.tau_rel = epsrel;
+  h.tau_abs = epsabs;
+  h.max_regions = max_regions;
+  h.it_max = 100;
+  h.relerr_filter = fam == kFamOscillatory ? 0 : 1;
+  h.heuristic_filter = 1;
+  h.s = s0;
+  h.it = 1;
+  h.status = -100;
+  IntegrandParams prm = to_params(fam, n, params);
+  const EvalRule rule = to_eval_rule(*rt);
+#define PG_CK(x)                                                                          \
+  do {                                                                                    \
+    e = (x);                                                                              \
+    if (e != cudaSuccess) return out->status = fail(PAGANI_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e)); \
+  } while (0)
+  PG_CK(cudaMemcpyAsync(a.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  PG_CK(cudaMemcpyAsync(base + L.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
+  k_uniform_split<<<(int)((s0 + 255) / 256), 256, 0, st>>>(a.pool, d0, log2d, s0);
+  PG_CK(cudaGetLastError());
+  int launches = 1;
+  int64_t d2h = 0;
+  for (int guard = 0; guard < h.it_max + 2; ++guard) {
+    PG_CK(fk.loop[n](rule, a, Lc.eval_grid, Lc.eval_block, Lc.eval_smem, st));
+    ++launches;
+    PG_CK(cudaMemcpyAsync(&h, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    PG_CK(cudaStreamSynchronize(st));
+    d2h += sizeof(Ctrl);
+    if (h.search) {
+      for (int probe = 0; probe < 128; ++probe) {
+        k_probe<kMgmtThreads><<<Lc.mgmt_grid, kMgmtThreads, 0, st>>>(a);
+        PG_CK(cudaGetLastError());
+        ++launches;
+        PG_CK(cudaMemcpyAsync(&h, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        PG_CK(cudaStreamSynchronize(st));
+        d2h += sizeof(Ctrl);
+        if (!h.search_cont) break;
+      }
+    }
+    k_count<kMgmtThreads, kMgmtItems><<<Lc.mgmt_grid, kMgmtThreads, 0, st>>>(a);
+    PG_CK(cudaGetLastError());
+    k_split<kMgmtThreads, kMgmtItems><<<Lc.mgmt_grid, kMgmtThreads, 0, st>>>(a);
+    PG_CK(cudaGetLastError());
+    launches += 2;
+    PG_CK(cudaMemcpyAsync(&h, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    PG_CK(cudaStreamSynchronize(st));
+    d2h += sizeof(Ctrl);
+    if (h.done) break;
+  }
+#undef PG_CK
+  out->estimate = h.estimate;
+  out->errorest = h.errorest;
+  out->iterations = h.it;
+  out->n_regions = h.n_regions_total;
+  out->n_active_last = h.s;
+  out->finished_volume = nval(h.fin_volume_acc);
+  out->eval_launches = h.it;
+  out->kernel_launches = launches;
+  out->h2d_bytes = (int64_t)(sizeof(Ctrl) + sizeof(prm));
+  out->d2h_bytes = d2h;
+  if (h.watchdog) return out->status = fail(PAGANI_ERR_WATCHDOG, "device-side consistency check failed");
+  if (!h.done) return out->status = fail(PAGANI_ERR_WATCHDOG, "loop ended without a result");
+  out->status = h.status;
+  if (h.status == -6) g_err = "the integrand produced NaN or Inf";
+  return out->status;
+}
+
 }  // namespace pg
 
 // =================================================================== C ABI
@@ -854,6 +1058,18 @@ int pagani_integrate(int dim, int integrand_id, const double* params, double eps
                      int64_t max_regions, pagani_result* out) {
   return pagani_integrate_ex(dim, integrand_id, params, epsrel, epsabs, max_regions, nullptr, nullptr, out,
                              nullptr, 0);
+}
+
+int pagani_integrate_noalloc(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
+                             int64_t max_regions, void* cuda_stream, pagani_result* out) {
+  if (!out) return fail(PAGANI_ERR_ARGUMENT, "out is NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    return integrate_noalloc_locked(dim, integrand_id, params, epsrel, epsabs, max_regions,
+                                    (cudaStream_t)cuda_stream, out);
+  } catch (...) {
+    return out->status = fail(PAGANI_ERR_CUDA, "internal error");
+  }
 }
 
 int pagani_workspace_reserve(int64_t max_regions, int dim) {
