@@ -156,6 +156,37 @@ __device__ __forceinline__ void build_axis(typename F::T* tab, const EvalRule& R
   }
 }
 
+// k of a dyadic lower bound k 2^-level, from the IEEE fields (integer ops).
+__device__ __forceinline__ long long dyadic_index(double lower, int level) {
+  const long long bits = __double_as_longlong(lower);
+  if (bits == 0) return 0;
+  const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+  const long long mant = (bits & ((1LL << 52) - 1)) | (1LL << 52);
+  const int shift = e + level - 52;
+  return shift >= 0 ? (mant << shift) : (mant >> (-shift));
+}
+
+// Table entries of axis j for the box [lo, lo + 2^-lv): copied from the
+// per-axis factor cache when the level is cached, computed otherwise.  The
+// cache holds the same expression of the same arguments, so both give the
+// same bits.
+template <class F, int N, int THREADS>
+__device__ __forceinline__ void axis_entries(typename F::T* tab, const EvalRule& R, const IntegrandParams& prm,
+                                             const typename F::T* __restrict__ cache, int cache_levels, double lo,
+                                             int lv, int j) {
+  if (cache != nullptr && lv <= cache_levels) {
+    const typename F::T* src = cache + ((size_t)j * kCacheSlots + ((1 << lv) - 1) + dyadic_index(lo, lv)) * kCodes;
+#pragma unroll
+    for (int code = 0; code < kCodes; ++code) tab[(code * N + j) * THREADS] = src[code];
+  } else {
+    const double h = 0.5 * pow2_neg(lv);
+    const typename F::Ax ax = F::axis(prm, j);
+#pragma unroll
+    for (int code = 0; code < kCodes; ++code)
+      tab[(code * N + j) * THREADS] = F::factor(ax, fma(h, code_offset(R, code), lo + h));
+  }
+}
+
 // The nine generator sums S[g] = sum over the orbit of g of f, and the
 // fourth differences D[j], for one region whose factor table is `tab`.
 template <class F, int N, int THREADS>
@@ -348,6 +379,7 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
   const int relerr = c.relerr_filter;
   const IntegrandParams prm = *A.prm;
   const T base = F::base(prm);
+  const T* __restrict__ fcache = static_cast<const T*>(A.fcache);
 
   NSum sv = {0.0, 0.0}, se = {0.0, 0.0};
   double emin = __longlong_as_double(0x7ff0000000000000LL), emax = -emin;
@@ -358,7 +390,9 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
   for (int64_t p = (int64_t)blockIdx.x * THREADS + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * THREADS) {
     const int64_t iL = 2 * p;
     double loL[N], loR[N], wL[N], wR[N];
-    int lvL = 0, lvR = 0, diff_axis = -1;
+    int lvLj[N];
+    int lvL = 0, lvR = 0, diff_axis = -1, diff_lv = 0;
+    double diff_lo = 0.0;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       const double2 lo2 = *reinterpret_cast<const double2*>(lower + (size_t)j * cap + iL);
@@ -367,33 +401,27 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
       loR[j] = lo2.y;
       wL[j] = pow2_neg(lv2.x);
       wR[j] = pow2_neg(lv2.y);
+      lvLj[j] = lv2.x;
       lvL += lv2.x;
       lvR += lv2.y;
-      if (lo2.x != lo2.y || lv2.x != lv2.y) diff_axis = j;
+      if (lo2.x != lo2.y || lv2.x != lv2.y) {
+        diff_axis = j;
+        diff_lo = lo2.y;
+        diff_lv = lv2.y;
+      }
     }
     // factor table of the left region
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const double h = 0.5 * wL[j];
-      build_axis<F, N, THREADS>(tab, R, F::axis(prm, j), loL[j] + h, h, j);
-    }
+    for (int j = 0; j < N; ++j)
+      axis_entries<F, N, THREADS>(tab, R, prm, fcache, A.fcache_levels, loL[j], lvLj[j], j);
     double S[kNumGen], D[N];
     double VL, EL, VR, ER;
     int KL, KR;
     rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
     region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL), wL, VL, EL, KL, nullptr);
     // patch the one axis where the right sibling differs
-    if (diff_axis >= 0) {
-      double lo = 0.0, w = 1.0;
-#pragma unroll
-      for (int j = 0; j < N; ++j)
-        if (j == diff_axis) { lo = loR[j]; w = wR[j]; }
-      const double h = 0.5 * w;
-      const typename F::Ax ax = F::axis(prm, diff_axis);
-#pragma unroll
-      for (int code = 0; code < kCodes; ++code)
-        tab[(code * N + diff_axis) * THREADS] = F::factor(ax, fma(h, code_offset(R, code), lo + h));
-    }
+    if (diff_axis >= 0)
+      axis_entries<F, N, THREADS>(tab, R, prm, fcache, A.fcache_levels, diff_lo, diff_lv, diff_axis);
     rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
     region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR), wR, VR, ER, KR, nullptr);
 
@@ -450,6 +478,35 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
                                          tot.nonfinite, A.trace, A.trace_cap);
     set_cond(A.use_graph, A.h_probe, (unsigned)search);
     __threadfence();
+  }
+}
+
+// ------------------------------------------------------- factor-cache fill
+// Fills level L = l0 + it - 1 of the per-axis factor cache (the deepest level
+// a box can have reached by iteration it), if it is cached.  One thread per
+// (axis, interval, code).
+template <class F, int N>
+__global__ void __launch_bounds__(256) k_factor_cache(const EvalRule R, const LoopArgs A) {
+  typedef typename F::T T;
+  const Ctrl& c = *A.ctrl;
+  if (c.done || A.fcache == nullptr) return;
+  const int L = c.l0 + c.it - 1;
+  if (L > A.fcache_levels) return;
+  T* cache = static_cast<T*>(A.fcache);
+  const IntegrandParams prm = *A.prm;
+  const long long count = 1LL << L;
+  const long long total = (long long)N * count * kCodes;
+  const double w = pow2_neg(L);
+  const double h = 0.5 * w;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int code = (int)(idx % kCodes);
+    const long long rest = idx / kCodes;
+    const long long k = rest % count;
+    const int j = (int)(rest / count);
+    const double lo = (double)k * w;
+    cache[((size_t)j * kCacheSlots + (count - 1) + k) * kCodes + code] =
+        F::factor(F::axis(prm, j), fma(h, code_offset(R, code), lo + h));
   }
 }
 
@@ -510,6 +567,11 @@ cudaError_t launch_loop(const EvalRule& R, const LoopArgs& A, int grid, int bloc
   k_evaluate_loop<F, N, THREADS><<<grid, block, smem, st>>>(R, A);
   return cudaGetLastError();
 }
+template <class F, int N>
+cudaError_t launch_fill(const EvalRule& R, const LoopArgs& A, int grid, int block, size_t smem, cudaStream_t st) {
+  k_factor_cache<F, N><<<grid, block, smem, st>>>(R, A);
+  return cudaGetLastError();
+}
 template <class F, int N, int THREADS, bool DIAG>
 cudaError_t launch_standalone(const EvalRule& R, const StandaloneArgs& A, int grid, int block, size_t smem,
                               cudaStream_t st) {
@@ -523,6 +585,8 @@ FamilyKernels make_family_kernels() {
   k.threads = THREADS;
 #define PG_SET(NN)                                                                              \
   k.loop[NN] = &launch_loop<FamOf<NN>, NN, THREADS>;                                            \
+  k.fill[NN] = &launch_fill<FamOf<NN>, NN>;                                                     \
+  k.fill_fn[NN] = (const void*)&k_factor_cache<FamOf<NN>, NN>;                                  \
   k.standalone[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, false>;                         \
   k.standalone_diag[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, true>;                     \
   k.loop_fn[NN] = (const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS>;                        \

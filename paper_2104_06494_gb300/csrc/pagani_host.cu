@@ -390,6 +390,7 @@ struct Workspace {
   CountPartial* count_part = nullptr;
   TraceRec* trace = nullptr;
   int trace_cap = 0;
+  void* fcache = nullptr;
   int max_grid = 0;
   cudaStream_t own_stream = nullptr;
   std::vector<void*> allocs;
@@ -477,6 +478,11 @@ static int ensure_workspace(int64_t want_cap, int n) {
   PG_ALLOC(w.probe_part, w.max_grid);
   PG_ALLOC(w.count_part, w.max_grid);
   PG_ALLOC(w.trace, kTraceCap);
+  {
+    double2* fc = nullptr;  // sized for the widest element type (complex factors)
+    PG_ALLOC(fc, (size_t)kMaxDim * kCacheSlots * kCodes);
+    w.fcache = fc;
+  }
 #undef PG_ALLOC
   w.pool.cap = cap;
   w.pool.n = nn;
@@ -583,6 +589,8 @@ static LoopArgs loop_args(int use_graph, cudaGraphConditionalHandle hm, cudaGrap
   a.use_graph = use_graph;
   a.h_main = hm;
   a.h_probe = hp;
+  a.fcache = w.fcache;
+  a.fcache_levels = kCacheLevels;
   return a;
 }
 
@@ -620,7 +628,7 @@ static int build_graph(int fam, int n, const EvalRule& rule, const Launch& L, Gr
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("cudaGraphCreate: ") + cudaGetErrorString(e));
   cudaGraphConditionalHandle hm, hp;
-  cudaGraphNode_t wmain, nev, wprobe, nprobe, ncount, nsplit;
+  cudaGraphNode_t wmain, nev, wprobe, nprobe, ncount, nsplit;  // and the cache fill
   cudaGraph_t body = nullptr, pbody = nullptr;
   LoopArgs args;
   EvalRule r = rule;
@@ -641,7 +649,9 @@ static int build_graph(int fam, int n, const EvalRule& rule, const Launch& L, Gr
   eargs[0] = &r;
   eargs[1] = &args;
   margs[0] = &args;
-  PG_CK(add_kernel(&nev, body, nullptr, 0, fk.loop_fn[n], L.eval_grid, L.eval_block, L.eval_smem, eargs));
+  cudaGraphNode_t nfill;
+  PG_CK(add_kernel(&nfill, body, nullptr, 0, fk.fill_fn[n], L.mgmt_grid, 256, 0, eargs));
+  PG_CK(add_kernel(&nev, body, &nfill, 1, fk.loop_fn[n], L.eval_grid, L.eval_block, L.eval_smem, eargs));
   PG_CK(add_while(&wprobe, body, &nev, 1, hp, &pbody));
   PG_CK(add_kernel(&nprobe, pbody, nullptr, 0, (const void*)&k_probe<kMgmtThreads>, L.mgmt_grid, kMgmtThreads, 0,
                    margs));
@@ -706,6 +716,7 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   h.s = s0;
   h.it = 1;
   h.status = -100;
+  h.l0 = log2d;
   IntegrandParams prm = to_params(fam, n, params);
   cudaError_t e;
 #define PG_CK(x)                                                                          \
@@ -747,6 +758,8 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
     PG_CK(cudaEventCreate(&ev1));
     double eval_ms = 0.0;
     for (int guard = 0; guard < o.it_max + 2; ++guard) {
+      PG_CK(fk.fill[n](rule, args, L.mgmt_grid, 256, 0, st));
+      ++launches;
       PG_CK(cudaEventRecord(ev0, st));
       PG_CK(fk.loop[n](rule, args, L.eval_grid, L.eval_block, L.eval_smem, st));
       PG_CK(cudaEventRecord(ev1, st));
@@ -798,7 +811,7 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   if (o.use_graph) {
     // the graph ran one Evaluate, count and split per iteration plus the probes
     eval_launches = h.it;
-    launches += 3 * h.it + h.total_probes;
+    launches += 4 * h.it + h.total_probes;
   }
   out->eval_launches = eval_launches;
   out->kernel_launches = launches;

@@ -10,6 +10,11 @@ constexpr int kMaxDim = 8;
 constexpr int kNumGen = 9;
 constexpr int kCodes = 11;  // coordinate codes per axis (see below)
 
+// Per-axis factor cache: the 11 factor values of every dyadic interval
+// [k 2^-l, (k+1) 2^-l) of levels l <= kCacheLevels, per axis, slot 2^l - 1 + k.
+constexpr int kCacheLevels = 11;
+constexpr int kCacheSlots = (1 << (kCacheLevels + 1)) - 1;
+
 // Generator orbits of the degree-9 rule, in table order.
 enum Gen {
   kGenCentre = 0,   // centre
@@ -100,6 +105,7 @@ struct Ctrl {
   int32_t watchdog;          // set if a kernel saw an impossible state
   int32_t loop_guard;        // iterations counted by the count kernel
   int32_t total_probes;      // threshold probes over the whole call
+  int32_t l0;                // level of the Uniform-Split boxes (log2 of the divisions)
 };
 
 // One per-iteration record (mirrors pagani_trace_record in pagani.h).
@@ -164,6 +170,8 @@ struct LoopArgs {
   int trace_cap;
   int use_graph;
   cudaGraphConditionalHandle h_main, h_probe;
+  void* fcache;          // per-axis factor cache (element type of the family), or null
+  int fcache_levels;     // deepest cached level
 };
 
 // Arguments of the standalone evaluate entry point.
@@ -186,6 +194,8 @@ typedef cudaError_t (*StandaloneLauncher)(const EvalRule&, const StandaloneArgs&
 
 struct FamilyKernels {
   LoopEvalLauncher loop[kMaxDim + 1];
+  LoopEvalLauncher fill[kMaxDim + 1];      // factor-cache fill, one level per iteration
+  const void* fill_fn[kMaxDim + 1];
   StandaloneLauncher standalone[kMaxDim + 1];
   StandaloneLauncher standalone_diag[kMaxDim + 1];
   const void* loop_fn[kMaxDim + 1];        // kernel symbols (for occupancy queries / graph nodes)

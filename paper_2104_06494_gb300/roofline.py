@@ -6,7 +6,10 @@ kernel's loop structure (csrc/pagani_eval.cuh) operation by operation, per
 sibling pair (one thread):
 
 * the per-axis factor table: 11 coordinate codes on n + 1 axes (the pair
-  shares n - 1 axes, and the split axis is patched for the right region);
+  shares n - 1 axes, and the split axis is patched for the right region).
+  With the per-axis factor cache (levels <= 11) these entries are loads, not
+  FP64 work; the cache fill (one level per iteration, n 2^L 11 factors) is a
+  separate kernel, counted by `cache_fill_work`;
 * per region: prefix/suffix partial products, the one-axis, pair, triple and
   vertex orbits (one product or sum per point from shared partials), the
   nine generator sums, the fourth differences, rule and null-rule weighting,
@@ -180,9 +183,20 @@ def pair_table_work(family: int, n: int) -> Counter:
     return c
 
 
-def pair_work(family: int, n: int, two_level: bool) -> Counter:
+def cache_fill_work(family: int, n: int, level: int) -> Counter:
+    """FP64 work of filling one level of the per-axis factor cache: n 2^level
+    intervals, each with the 11 entries (and set-up) of one table axis."""
+    one_axis = Counter(pair_table_work(family, 1))
+    one_axis.subtract(pair_table_work(family, 0))
+    return Counter({k: v * n * (1 << level) for k, v in one_axis.items() if v})
+
+
+def pair_work(family: int, n: int, two_level: bool, cached: bool = True) -> Counter:
     c = Counter()
-    c.update(pair_table_work(family, n))
+    if cached:
+        c["cache_loads"] += 11 * (n + 1)
+    else:
+        c.update(pair_table_work(family, n))
     for _ in range(2):
         c.update(region_points_work(family, n))
         c.update(region_epilogue_work())
@@ -195,13 +209,13 @@ def pair_work(family: int, n: int, two_level: bool) -> Counter:
     return c
 
 
-def evaluate_work(family: int, n: int, regions_per_iteration) -> Counter:
+def evaluate_work(family: int, n: int, regions_per_iteration, cached: bool = True) -> Counter:
     """Total algorithmic work of the Evaluate launches of one integration,
     given the region count of every iteration (first iteration: no parents,
     no two-level refinement)."""
     tot = Counter()
     for it, s in enumerate(regions_per_iteration):
-        w = pair_work(family, n, two_level=it > 0)
+        w = pair_work(family, n, two_level=it > 0, cached=cached)
         for k, v in w.items():
             tot[k] += v * (int(s) // 2)
     return tot
