@@ -164,6 +164,46 @@ def traffic_bytes_per_region():
     return float(kv["bytes_per_region"]), float(kv.get("fp64_pipe_active", "nan"))
 
 
+def differentiation_report(pg, torch, flush, reps: int = 3):
+    """The differentiated form on the d = 6 parametric Gaussian next to the
+    plain single integral at the same accuracy: forward with the leaf set kept,
+    backward over it, and the gradient's error against the closed form."""
+    import numpy as np
+    from oracle import closed_forms as cf
+    from paper_2104_06494_gb300.workloads import config_workloads
+    w = config_workloads()["gaussian_d6_grad"]
+    n, p = w.dim, np.array(w.params)
+
+    def timed(fn):
+        best = None
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        return best, out
+    stream = torch.cuda.current_stream().cuda_stream
+    plain_ms, r0 = timed(lambda: pg.pagani_integrate_ex(n, w.family, p, w.epsrel, w.epsabs, w.max_regions,
+                                                        stream=stream))
+    fwd_ms, r = timed(lambda: pg.pagani_integrate_ex(n, w.family, p, w.epsrel, w.epsabs, w.max_regions,
+                                                     stream=stream, keep_leaves=1))
+    lower, level = pg.pagani_leaves(n)
+    bwd_ms, (v, g) = timed(lambda: pg.pagani_gradient(n, w.family, p, lower, level, stream=stream))
+    tot, gc = cf.gaussian_gradient(n, p)
+    scale = np.concatenate([np.full(n, abs(tot)), p[:n] * abs(tot)])
+    return {"workload": w.name, "theta": "a_1..a_6, w_1..w_6", "epsrel": w.epsrel,
+            "plain_ms": plain_ms, "forward_keep_leaves_ms": fwd_ms, "backward_ms": bwd_ms,
+            "n_leaves": r.n_leaves, "regions": r.n_regions, "status": r.status,
+            "value_true_relerr": abs(r.estimate - tot) / abs(tot),
+            "grad_max_err_vs_closed_form": float(np.max(np.abs(g - np.array(gc)) / scale)),
+            "grad_err_scale": "|I| for d/da, a_j |I| for d/dw",
+            "backward_evals_per_s": r.n_leaves * npoints(n) / (bwd_ms * 1e-3)}
+
+
 def main():
     args = parse()
     import torch
@@ -350,6 +390,7 @@ def main():
             b.record()
             torch.cuda.synchronize()
             line["config"]["time_to_result_ms"][w.name] = a.elapsed_time(b)
+        line["differentiation"] = differentiation_report(pg, torch, flush)
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))

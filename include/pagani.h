@@ -79,6 +79,10 @@ typedef struct {
   int32_t kernel_launches;/* kernels of this library launched by this call   */
   int64_t h2d_bytes;      /* host-to-device bytes copied by this call        */
   int64_t d2h_bytes;      /* device-to-host bytes copied by this call        */
+  double active_volume;   /* volume of the regions of the last iteration; with
+                             finished_volume it sums to 1 (dyadic boxes)    */
+  int64_t n_leaves;       /* with keep_leaves: boxes of the converged leaf set
+                             (see pagani_leaves); -1 otherwise             */
 } pagani_result;
 
 typedef struct {
@@ -88,6 +92,8 @@ typedef struct {
                                d >= 2 with d^dim <= 4096 (Sec. 3.1)                                 */
   int32_t it_max;           /* iteration limit (default 100)                                       */
   int32_t use_graph;        /* 1 (default): device-resident loop in one CUDA graph; 0: host-driven */
+  int32_t keep_leaves;      /* 1: keep the converged leaf set for pagani_leaves / differentiation;
+                               0 (default)                                                         */
 } pagani_options;
 
 /* One record per iteration (Algorithm 2 scalars after that iteration). */
@@ -160,6 +166,29 @@ int pagani_workspace_release(void);
  * < 0. */
 int pagani_evaluate(int dim, int integrand_id, const double* params, int64_t m, const double* lower,
                     const double* width, double* V, double* E, int32_t* K, double* diag, void* cuda_stream);
+
+/* The converged leaf set of the last integration run with keep_leaves: the
+ * boxes whose rule values make up the estimate v + v_f of Algorithm 2 (every
+ * box classified finished, in the iteration it finished, and every box of
+ * the last iteration).  Writes the count to *n_out; with lower and level
+ * non-NULL also copies the boxes into those DEVICE arrays, SoA [dim][cap]
+ * (box i: lower[j*cap+i] and width 2^-level[j*cap+i] on axis j; cap >=
+ * count).  Returns 0, or < 0 if no leaf set was kept or dim differs. */
+int pagani_leaves(int dim, int64_t cap, double* lower, uint8_t* level, int64_t* n_out, void* cuda_stream);
+
+/* Differentiation of the rule estimate over a fixed box list (typically the
+ * leaf set above): out[0] = sum over boxes of the basic-rule value V, and
+ * out[1 + k] = its derivative with respect to params[k] (the family's own
+ * parameter layout: out[1..dim] for the first vector, out[dim+1..2 dim] for
+ * the second), i.e. sum vol sum_points w d f/d theta.  Defined for the
+ * positive product families (PRODUCT_PEAK, GAUSSIAN, C0): f is a product of
+ * per-axis factors, so d f/d theta_j = f d log phi_j / d theta_j.  lower
+ * (f64) and level (u8) are DEVICE arrays SoA [dim][m]; params and out (2 dim
+ * + 1 doubles) are host arrays.  The paper defines no derivative; this is
+ * the backward pass of the converged integral with the region set frozen.
+ * Returns 0 or < 0. */
+int pagani_gradient(int dim, int integrand_id, const double* params, int64_t m, const double* lower,
+                    const uint8_t* level, double* out, void* cuda_stream);
 
 /* The rule tables this library generated for dimension dim (host outputs):
  * radius[5] = generator radii sqrt(l1), sqrt(l2), sqrt(l3), sqrt(lp), sqrt(l0);

@@ -129,11 +129,12 @@ class OracleResult:
     final_lower: np.ndarray | None
     final_width: np.ndarray | None
     finished_volume: float
+    leaves: tuple | None = None
 
 
 def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20, max_regions: int = 10 ** 6,
               relerr_filter: int = 1, heuristic_filter: int = 1, init_div: int = 0, it_max: int = 100,
-              want_regions: bool = False) -> OracleResult:
+              want_regions: bool = False, want_leaves: bool = False) -> OracleResult:
     lib = _load()
     p = np.ascontiguousarray(params, dtype=np.float64)
     opt = _Opt(relerr_filter, heuristic_filter, init_div, it_max)
@@ -146,18 +147,32 @@ def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20,
         fl = np.zeros((cap, n))
         fw = np.zeros((cap, n))
     fv = ctypes.c_double(0.0)
+    nleaf = ctypes.c_int64(0)
+    ll = lw = None
+    lcap = 0
+    if want_leaves:
+        lcap = 8 * max_regions
+        ll = np.zeros((lcap, n))
+        lw = np.zeros((lcap, n))
     lib.oracle_pagani(ctypes.byref(_rule_struct(n)), ctypes.c_int(family), _dp(p), ctypes.c_double(epsrel),
                       ctypes.c_double(epsabs), ctypes.c_int64(max_regions), ctypes.byref(opt), ctypes.byref(res),
                       trace.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(it_max),
                       _dp(fl) if want_regions else None, _dp(fw) if want_regions else None,
-                      ctypes.c_int64(cap), ctypes.byref(fv))
+                      ctypes.c_int64(cap), ctypes.byref(fv), _dp(ll) if want_leaves else None,
+                      _dp(lw) if want_leaves else None, ctypes.c_int64(lcap), ctypes.byref(nleaf))
     it = res.iterations
     tr = trace[:max(it, 0)].copy()
     if want_regions:
         m = int(tr["s"][-1]) if len(tr) else 0
         fl, fw = fl[:m].copy(), fw[:m].copy()
+    leaves = None
+    if want_leaves:
+        k = nleaf.value
+        if k > lcap:
+            raise RuntimeError("oracle leaf list overflow")
+        leaves = (ll[:k].copy(), lw[:k].copy())
     return OracleResult(res.estimate, res.errorest, res.status, it, res.n_regions, res.n_active_last, tr,
-                        fl, fw, fv.value)
+                        fl, fw, fv.value, leaves)
 
 
 def threshold_classify(A, E, v_tot: float, e_tot: float, e_it: float, tau_rel: float):
@@ -174,3 +189,17 @@ def threshold_classify(A, E, v_tot: float, e_tot: float, e_it: float, tau_rel: f
                                        ctypes.c_double(tau_rel), ctypes.byref(probes), ctypes.byref(t),
                                        ctypes.byref(chg))
     return ok, a, probes.value, t.value, chg.value
+
+
+def gradient(family: int, n: int, params, lower, width):
+    """Sum over the boxes (m x n arrays) of the basic rule applied to f and
+    to df/dparams: returns (value, gradient[2n], abs_scales[2n + 1])."""
+    lib = _load()
+    lo = np.ascontiguousarray(lower, dtype=np.float64).reshape(-1, n)
+    wd = np.ascontiguousarray(width, dtype=np.float64).reshape(-1, n)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    out = np.zeros(2 * n + 1)
+    ab = np.zeros(2 * n + 1)
+    lib.oracle_gradient(ctypes.byref(_rule_struct(n)), ctypes.c_int(family), _dp(p), ctypes.c_int64(lo.shape[0]),
+                        _dp(lo), _dp(wd), _dp(out), _dp(ab))
+    return out[0], out[1:], ab

@@ -59,3 +59,22 @@ def closed_form(family: int, n: int, params) -> float:
         a, w = p[:n], p[n:2 * n]
         return math.prod((2 - math.exp(-aj * wj) - math.exp(-aj * (1 - wj))) / aj for aj, wj in zip(a, w))
     raise ValueError(f"unknown family {family}")
+
+
+def gaussian_gradient(n: int, params):
+    """d/d(a, w) of the Gaussian family's closed form: with the 1-D factor
+    F_j = sqrt(pi)/(2 a) [erf(a (1 - w)) + erf(a w)],
+    dF_j/dw = exp(-a^2 w^2) - exp(-a^2 (1 - w)^2) and
+    dF_j/da = -F_j / a + [(1 - w) exp(-a^2 (1 - w)^2) + w exp(-a^2 w^2)] / a."""
+    p = [float(x) for x in params]
+    a, w = p[:n], p[n:2 * n]
+    F = [math.sqrt(math.pi) / (2 * aj) * (math.erf(aj * (1 - wj)) + math.erf(aj * wj)) for aj, wj in zip(a, w)]
+    tot = math.prod(F)
+    ga, gw = [], []
+    for j, (aj, wj) in enumerate(zip(a, w)):
+        rest = math.prod(F[:j] + F[j + 1:])
+        dw = math.exp(-aj * aj * wj * wj) - math.exp(-aj * aj * (1 - wj) ** 2)
+        da = -F[j] / aj + ((1 - wj) * math.exp(-aj * aj * (1 - wj) ** 2) + wj * math.exp(-aj * aj * wj * wj)) / aj
+        ga.append(da * rest)
+        gw.append(dw * rest)
+    return tot, ga + gw

@@ -414,12 +414,24 @@ static void uniform_split(int n, int d, double *lower, double *width) {
 }
 
 /* ------------------------------------------------------ PAGANI main loop -- */
+/* Appends box i of (lo, wd) to the leaf list (row-major, capacity cap). */
+static void leaf_append(int n, const double *lo, const double *wd, double *leaf_lo,
+                        double *leaf_w, int64_t cap, int64_t *count) {
+  if (leaf_lo && *count < cap) {
+    memcpy(leaf_lo + *count * n, lo, sizeof(double) * n);
+    memcpy(leaf_w + *count * n, wd, sizeof(double) * n);
+  }
+  ++*count;
+}
+
 int oracle_pagani(const oracle_rule *R, int fam, const double *params,
                   double tau_rel, double tau_abs, int64_t max_regions,
                   const oracle_options *opt, oracle_result *res,
                   oracle_trace *trace, int trace_cap,
                   double *final_lower, double *final_width, int64_t final_cap,
-                  double *fin_vol_out) {
+                  double *fin_vol_out, double *leaf_lo, double *leaf_w,
+                  int64_t leaf_cap, int64_t *n_leaves) {
+  int64_t leaves = 0;
   int n = R->n;
   int d = opt->init_div > 0 ? opt->init_div : oracle_default_init_div(n);
   int64_t s = 1;
@@ -533,6 +545,8 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
         double vol = 1.0;
         for (int j = 0; j < n; ++j) vol *= H_w[i * n + j];
         nadd(&finvol, vol);
+        /* finished boxes leave the list for good: they are leaves */
+        leaf_append(n, H_lo + i * n, H_w + i * n, leaf_lo, leaf_w, leaf_cap, &leaves);
       }
     /* H, V, E <- Filter(H, V, E, A); V_p <- V, E_p <- E */
     int64_t q = 0;
@@ -574,6 +588,11 @@ done:
     memcpy(final_width, H_w, sizeof(double) * (size_t)m * n);
   }
   if (fin_vol_out) *fin_vol_out = nval(&finvol);
+  /* every box of the last iteration is a leaf too */
+  if (status >= 0)
+    for (int64_t i = 0; i < s; ++i)
+      leaf_append(n, H_lo + i * n, H_w + i * n, leaf_lo, leaf_w, leaf_cap, &leaves);
+  if (n_leaves) *n_leaves = leaves;
   free(H_lo); free(H_w); free(V); free(E); free(K); free(A); free(Vp); free(Ep);
   return status;
 }
@@ -585,4 +604,96 @@ int oracle_threshold_classify(uint8_t *A, const double *E, double v_tot,
                               int *direction_changes) {
   return threshold_classify(A, E, v_tot, e_tot, e_it, s_it, tau_rel, probes, t,
                             direction_changes);
+}
+
+
+/* ------------------------------------------------------------- gradients -- */
+/* Integrand and its derivatives with respect to the parameter vector
+ * (family layout), written from the formulas: d[k] = df/dparams[k].
+ * Defined for the product peak, Gaussian and C0 families. */
+static double integrand_grad(int fam, int n, const double *p, const double *x,
+                             double *d) {
+  double f = integrand(fam, n, p, x);
+  for (int j = 0; j < n; ++j) {
+    double t = x[j] - p[n + j];
+    switch (fam) {
+    case FAM_PRODUCT_PEAK: { /* f = prod 1/(c^-2 + t^2) */
+      double den = pow(p[j], -2.0) + t * t;
+      d[j] = f * (2.0 * pow(p[j], -3.0)) / den;
+      d[n + j] = f * (2.0 * t) / den;
+      break;
+    }
+    case FAM_GAUSSIAN: /* f = exp(-sum a^2 t^2) */
+      d[j] = f * (-2.0 * p[j] * t * t);
+      d[n + j] = f * (2.0 * p[j] * p[j] * t);
+      break;
+    case FAM_C0: /* f = exp(-sum a |t|) */
+      d[j] = f * (-fabs(t));
+      d[n + j] = f * (t > 0.0 ? p[j] : (t < 0.0 ? -p[j] : 0.0));
+      break;
+    default:
+      d[j] = d[n + j] = NAN;
+    }
+  }
+  return f;
+}
+
+/* Sum over the boxes (row-major lower/width, m x n) of the basic rule
+ * applied to f and to each df/dparams[k]: out[0] = sum V, out[1 + k] = sum
+ * dV/dparams[k]; absout receives the same sums of absolute values (their
+ * rounding scale). */
+int oracle_gradient(const oracle_rule *R, int fam, const double *params,
+                    int64_t m, const double *lower, const double *width,
+                    double *out, double *absout) {
+  int n = R->n, K = 2 * n + 1;
+  nsum acc[17];
+  double sab[17];
+  memset(acc, 0, sizeof(acc));
+  memset(sab, 0, sizeof(sab));
+  for (int64_t i = 0; i < m; ++i) {
+    double c[16], h[16], vol = 1.0;
+    for (int j = 0; j < n; ++j) {
+      h[j] = 0.5 * width[i * n + j];
+      c[j] = lower[i * n + j] + h[j];
+      vol *= width[i * n + j];
+    }
+    double box[17], boxab[17];
+    memset(box, 0, sizeof(box));
+    memset(boxab, 0, sizeof(boxab));
+    for (int g = 0; g < R->G; ++g) {
+      double wg = R->wts[g * 5];
+      if (wg == 0.0) continue;
+      double v[16], x[16], d[16];
+      memcpy(v, R->gen + (size_t)g * n, sizeof(double) * n);
+      qsort(v, n, sizeof(double), cmp_double);
+      do {
+        int nzi[16], nz = 0;
+        for (int j = 0; j < n; ++j)
+          if (v[j] != 0.0) nzi[nz++] = j;
+        for (int mask = 0; mask < (1 << nz); ++mask) {
+          for (int j = 0; j < n; ++j) x[j] = c[j];
+          for (int t = 0; t < nz; ++t) {
+            int j = nzi[t];
+            x[j] = c[j] + h[j] * ((mask >> t & 1) ? -v[j] : v[j]);
+          }
+          double f = integrand_grad(fam, n, params, x, d);
+          box[0] += wg * f;
+          boxab[0] += fabs(wg * f);
+          for (int k = 0; k < 2 * n; ++k) {
+            box[1 + k] += wg * d[k];
+            boxab[1 + k] += fabs(wg * d[k]);
+          }
+        }
+      } while (next_perm(v, n));
+    }
+    for (int k = 0; k < K; ++k) {
+      nadd(&acc[k], vol * box[k]);
+      sab[k] += vol * boxab[k];
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    out[k] = nval(&acc[k]);
+    if (absout) absout[k] = sab[k];
+  }
+  return 0;
 }

@@ -34,7 +34,8 @@ class Result(ctypes.Structure):
     _fields_ = [("estimate", ctypes.c_double), ("errorest", ctypes.c_double), ("status", ctypes.c_int32),
                 ("iterations", ctypes.c_int32), ("n_regions", ctypes.c_int64), ("n_active_last", ctypes.c_int64),
                 ("finished_volume", ctypes.c_double), ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int32), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+                ("active_volume", ctypes.c_double), ("n_leaves", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -42,7 +43,8 @@ class Result(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("relerr_filter", ctypes.c_int32), ("heuristic_filter", ctypes.c_int32),
-                ("init_div", ctypes.c_int32), ("it_max", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("init_div", ctypes.c_int32), ("it_max", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("keep_leaves", ctypes.c_int32)]
 
 
 TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.int32), ("search_ok", np.int32),
@@ -53,7 +55,7 @@ TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.i
 # every symbol include/pagani.h declares
 EXPORTED = ["pagani_default_options", "pagani_integrate", "pagani_integrate_ex", "pagani_workspace_reserve",
             "pagani_workspace_release", "pagani_evaluate", "pagani_rule_tables", "pagani_fp64_peak",
-            "pagani_last_error", "pagani_version", "pagani_integrate_noalloc"]
+            "pagani_last_error", "pagani_version", "pagani_integrate_noalloc", "pagani_leaves", "pagani_gradient"]
 
 _lib = None
 
@@ -89,6 +91,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.pagani_evaluate.restype = ctypes.c_int
+    lib.pagani_leaves.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int64),
+                                  ctypes.c_void_p]
+    lib.pagani_leaves.restype = ctypes.c_int
+    lib.pagani_gradient.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, P(ctypes.c_double), ctypes.c_void_p]
+    lib.pagani_gradient.restype = ctypes.c_int
     lib.pagani_rule_tables.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64)]
     lib.pagani_rule_tables.restype = ctypes.c_int
     lib.pagani_fp64_peak.argtypes = [P(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]
@@ -131,6 +139,8 @@ class Integration:
     h2d_bytes: int = 0
     d2h_bytes: int = 0
     trace: np.ndarray | None = None
+    active_volume: float = 0.0
+    n_leaves: int = -1
 
     @property
     def status_name(self) -> str:
@@ -140,7 +150,7 @@ class Integration:
 def _integration(r: Result, trace=None) -> Integration:
     return Integration(r.estimate, r.errorest, r.status, r.iterations, r.n_regions, r.n_active_last,
                        r.finished_volume, r.eval_ms, r.eval_launches, r.kernel_launches, r.h2d_bytes, r.d2h_bytes,
-                       trace)
+                       trace, r.active_volume, r.n_leaves)
 
 
 def pagani_integrate(dim: int, integrand_id: int, params, epsrel: float, epsabs: float = 1e-20,
@@ -158,12 +168,12 @@ def pagani_integrate(dim: int, integrand_id: int, params, epsrel: float, epsabs:
 def pagani_integrate_ex(dim: int, integrand_id: int, params, epsrel: float, epsabs: float = 1e-20,
                         max_regions: int = 10_000_000, relerr_filter: int = 1, heuristic_filter: int = 1,
                         init_div: int = 0, it_max: int = 100, use_graph: int = 1, stream: int | None = None,
-                        trace: bool = False, raise_on_error: bool = True) -> Integration:
+                        trace: bool = False, raise_on_error: bool = True, keep_leaves: int = 0) -> Integration:
     """C ABI pagani_integrate_ex; stream is a raw cudaStream_t (e.g.
     torch.cuda.current_stream().cuda_stream) or None for the library stream."""
     lib = load()
     p, pp = _params_array(params)
-    o = Options(relerr_filter, heuristic_filter, init_div, it_max, use_graph)
+    o = Options(relerr_filter, heuristic_filter, init_div, it_max, use_graph, keep_leaves)
     r = Result()
     tr = np.zeros(it_max, dtype=TRACE_DTYPE) if trace else None
     rc = lib.pagani_integrate_ex(dim, integrand_id, pp, epsrel, epsabs, max_regions, ctypes.byref(o),
@@ -229,6 +239,48 @@ def pagani_evaluate(dim: int, integrand_id: int, params, lower, width, diag: boo
     if rc < 0:
         raise PaganiError(f"pagani_evaluate failed ({rc}): {last_error()}")
     return (V, E, K, D) if diag else (V, E, K)
+
+
+def pagani_leaves(dim: int, stream: int | None = None):
+    """The leaf set kept by the last integration with keep_leaves=1, as CUDA
+    tensors lower (dim, m) float64 and level (dim, m) uint8."""
+    import torch
+
+    lib = load()
+    n = ctypes.c_int64(0)
+    rc = lib.pagani_leaves(dim, 0, None, None, ctypes.byref(n), None)
+    if rc < 0:
+        raise PaganiError(f"pagani_leaves failed ({rc}): {last_error()}")
+    m = n.value
+    lower = torch.empty((dim, m), dtype=torch.float64, device="cuda")
+    level = torch.empty((dim, m), dtype=torch.uint8, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.pagani_leaves(dim, m, ctypes.c_void_p(lower.data_ptr()), ctypes.c_void_p(level.data_ptr()),
+                           ctypes.byref(n), ctypes.c_void_p(stream))
+    if rc < 0:
+        raise PaganiError(f"pagani_leaves failed ({rc}): {last_error()}")
+    return lower, level
+
+
+def pagani_gradient(dim: int, integrand_id: int, params, lower, level, stream: int | None = None):
+    """(value, gradient) of the rule estimate over the boxes (lower, level)
+    (CUDA tensors of shape (dim, m)); gradient in the params layout."""
+    import torch
+
+    lib = load()
+    p, pp = _params_array(params)
+    lower = lower.contiguous()
+    level = level.contiguous()
+    out = np.zeros(2 * dim + 1)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.pagani_gradient(dim, integrand_id, pp, lower.shape[1], ctypes.c_void_p(lower.data_ptr()),
+                             ctypes.c_void_p(level.data_ptr()), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             ctypes.c_void_p(stream))
+    if rc < 0:
+        raise PaganiError(f"pagani_gradient failed ({rc}): {last_error()}")
+    return out[0], out[1:]
 
 
 def pagani_rule_tables(dim: int):

@@ -101,7 +101,7 @@ __device__ __forceinline__ bool last_block_arrived(unsigned int* ticket) {
 // warp order: the result is deterministic for a fixed grid).
 __device__ __forceinline__ EvalPartial eval_identity() {
   EvalPartial p;
-  p.v.s = p.v.c = p.e.s = p.e.c = 0.0;
+  p.v.s = p.v.c = p.e.s = p.e.c = p.vol.s = p.vol.c = 0.0;
   p.emin = __longlong_as_double(0x7ff0000000000000LL);
   p.emax = -p.emin;
   p.n_rel = 0;
@@ -112,6 +112,7 @@ __device__ __forceinline__ EvalPartial eval_identity() {
 __device__ __forceinline__ EvalPartial eval_combine(EvalPartial a, const EvalPartial& b) {
   a.v = ncomb(a.v, b.v);
   a.e = ncomb(a.e, b.e);
+  a.vol = ncomb(a.vol, b.vol);
   a.emin = fmin(a.emin, b.emin);
   a.emax = fmax(a.emax, b.emax);
   a.n_rel += b.n_rel;
@@ -122,6 +123,7 @@ __device__ __forceinline__ EvalPartial eval_shfl(const EvalPartial& a, int off) 
   EvalPartial b;
   b.v = shfl_down_nsum(a.v, off);
   b.e = shfl_down_nsum(a.e, off);
+  b.vol = shfl_down_nsum(a.vol, off);
   b.emin = __shfl_down_sync(0xffffffffu, a.emin, off);
   b.emax = __shfl_down_sync(0xffffffffu, a.emax, off);
   b.n_rel = __shfl_down_sync(0xffffffffu, a.n_rel, off);
@@ -167,7 +169,9 @@ __device__ __forceinline__ void set_cond(int use_graph, cudaGraphConditionalHand
 // (Algorithm 2, from the termination test to the Threshold-Classify trigger).
 // Runs on one thread.  Returns 1 if a threshold search starts.
 __device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long long n_rel, double emin,
-                                              double emax, int nonfinite, TraceRec* trace, int trace_cap) {
+                                              double emax, int nonfinite, TraceRec* trace, int trace_cap,
+                                              double vol) {
+  c.active_volume = vol;
   c.v = v;
   c.e = e;
   c.n_rel = n_rel;

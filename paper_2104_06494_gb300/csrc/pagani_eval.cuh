@@ -28,6 +28,7 @@ namespace pg {
 struct RealProduct {
   typedef double T;
   static constexpr bool kUnitBounded = false;  // positive values: |S_g| = sum |f|
+  static constexpr bool kHasGrad = true;        // f = prod_j phi_j(x_j; p0_j, p1_j), phi > 0
   __device__ static __forceinline__ T mul(T a, T b) { return a * b; }
   __device__ static __forceinline__ double last(T a, T b) { return a * b; }
   __device__ static __forceinline__ double val(T a) { return a; }
@@ -47,6 +48,13 @@ struct ProductPeak : RealProduct {  // prod_j 1/(c_j^-2 + (x_j - w_j)^2)
     double t = x - a.w;
     return 1.0 / fma(t, t, a.cm2);
   }
+  // d log phi / d c and d log phi / d w at x (phi = 1/(c^-2 + t^2))
+  __device__ static __forceinline__ void dlog(const IntegrandParams& p, int j, double x, double phi, double& d0,
+                                              double& d1) {
+    const double c = p.p0[j], t = x - p.p1[j];
+    d0 = 2.0 * phi / (c * c * c);
+    d1 = 2.0 * t * phi;
+  }
 };
 
 struct Gaussian : RealProduct {  // exp(-sum_j a_j^2 (x_j - w_j)^2)
@@ -63,6 +71,13 @@ struct Gaussian : RealProduct {  // exp(-sum_j a_j^2 (x_j - w_j)^2)
     double u = a.a * (x - a.w);
     return exp(-(u * u));
   }
+  // d log phi / d a = -2 a t^2, d log phi / d w = 2 a^2 t (t = x - w)
+  __device__ static __forceinline__ void dlog(const IntegrandParams& p, int j, double x, double, double& d0,
+                                              double& d1) {
+    const double a = p.p0[j], t = x - p.p1[j];
+    d0 = -2.0 * a * t * t;
+    d1 = 2.0 * a * a * t;
+  }
 };
 
 struct C0Fam : RealProduct {  // exp(-sum_j a_j |x_j - w_j|)
@@ -76,11 +91,19 @@ struct C0Fam : RealProduct {  // exp(-sum_j a_j |x_j - w_j|)
   }
   __device__ static __forceinline__ T base(const IntegrandParams&) { return 1.0; }
   __device__ static __forceinline__ T factor(const Ax& a, double x) { return exp(-(a.a * fabs(x - a.w))); }
+  // d log phi / d a = -|t|, d log phi / d w = a sgn(t) (t = x - w)
+  __device__ static __forceinline__ void dlog(const IntegrandParams& p, int j, double x, double, double& d0,
+                                              double& d1) {
+    const double a = p.p0[j], t = x - p.p1[j];
+    d0 = -fabs(t);
+    d1 = t > 0.0 ? a : (t < 0.0 ? -a : 0.0);
+  }
 };
 
 struct Oscillatory {  // cos(2 pi u + sum_j a_j x_j) = Re[e^{2 pi i u} prod_j e^{i a_j x_j}]
   static constexpr int kFamily = kFamOscillatory;
   static constexpr bool kUnitBounded = true;  // signed values with |f| <= 1
+  static constexpr bool kHasGrad = false;
   typedef double2 T;
   struct Ax { double a; };
   __device__ static __forceinline__ T mul(T a, T b) {
@@ -112,6 +135,7 @@ template <int N>
 struct CornerPeak {  // (1 + sum_j a_j x_j)^-(N+1): per-axis terms add up
   static constexpr int kFamily = kFamCornerPeak;
   static constexpr bool kUnitBounded = false;
+  static constexpr bool kHasGrad = false;
   typedef double T;
   struct Ax { double a; };
   __device__ static __forceinline__ T mul(T a, T b) { return a + b; }
@@ -381,7 +405,7 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
   const T base = F::base(prm);
   const T* __restrict__ fcache = static_cast<const T*>(A.fcache);
 
-  NSum sv = {0.0, 0.0}, se = {0.0, 0.0};
+  NSum sv = {0.0, 0.0}, se = {0.0, 0.0}, svol = {0.0, 0.0};
   double emin = __longlong_as_double(0x7ff0000000000000LL), emax = -emin;
   long long nrel = 0;
   int nonfinite = 0;
@@ -435,6 +459,8 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
     nadd(sv, VR);
     nadd(se, EL);
     nadd(se, ER);
+    nadd(svol, pow2_neg(lvL));
+    nadd(svol, pow2_neg(lvR));
     emin = fmin(emin, fmin(EL, ER));
     emax = fmax(emax, fmax(EL, ER));
     nrel += relerr_active(VL, EL, tau_rel, relerr) + relerr_active(VR, ER, tau_rel, relerr);
@@ -446,6 +472,7 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
   for (int off = 16; off > 0; off >>= 1) {
     sv = ncomb(sv, shfl_down_nsum(sv, off));
     se = ncomb(se, shfl_down_nsum(se, off));
+    svol = ncomb(svol, shfl_down_nsum(svol, off));
     emin = fmin(emin, __shfl_down_sync(0xffffffffu, emin, off));
     emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, off));
     nrel += __shfl_down_sync(0xffffffffu, nrel, off);
@@ -456,6 +483,7 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
     EvalPartial mine;
     mine.v = sv;
     mine.e = se;
+    mine.vol = svol;
     mine.emin = emin;
     mine.emax = emax;
     mine.n_rel = nrel;
@@ -475,7 +503,7 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, con
   const EvalPartial tot = eval_reduce_partials<THREADS>(A.eval_part, gridDim.x, wp);
   if (threadIdx.x == 0) {
     int search = finalize_iteration_head(c, nval(tot.v), nval(tot.e), tot.n_rel, tot.emin, tot.emax,
-                                         tot.nonfinite, A.trace, A.trace_cap);
+                                         tot.nonfinite, A.trace, A.trace_cap, nval(tot.vol));
     set_cond(A.use_graph, A.h_probe, (unsigned)search);
     __threadfence();
   }
@@ -561,6 +589,96 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule 
   }
 }
 
+// ------------------------------------------------------------ gradient kernel
+// d/dtheta of the rule estimate summed over a fixed list of boxes (the leaf
+// set of an integration): vol * sum_points w_g f(x) d log phi_j(x_j)/d theta_j
+// for theta = (p0_j, p1_j) of every axis, and the estimate itself.  One warp
+// per box, lanes over the rule points (packed code table); per-axis factor and
+// log-derivative tables in shared memory per warp.  Each lane sums one box's
+// points plainly and adds that into Neumaier accumulators; the last block
+// combines the per-block partials.
+template <class F, int N>
+__global__ void __launch_bounds__(128) k_gradient(const EvalRule R, const GradArgs A) {
+  constexpr int K = 2 * N + 1;
+  __shared__ double tabs[4][3][N][kCodes];
+  __shared__ NSum red[4][K];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const IntegrandParams prm = *A.prm;
+  double (*phi)[kCodes] = tabs[wib][0];
+  double (*d0)[kCodes] = tabs[wib][1];
+  double (*d1)[kCodes] = tabs[wib][2];
+  NSum acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k].s = acc[k].c = 0.0;
+  const int64_t warps = (int64_t)gridDim.x * 4;
+  for (int64_t r = (int64_t)blockIdx.x * 4 + wib; r < A.m; r += warps) {
+    int L = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) L += A.level[(size_t)j * A.m + r];
+    const double vol = pow2_neg(L);
+    for (int e = lane; e < N * kCodes; e += 32) {
+      const int j = e / kCodes, code = e - j * kCodes;
+      const int lv = A.level[(size_t)j * A.m + r];
+      const double h = 0.5 * pow2_neg(lv);
+      const double x = fma(h, code_offset(R, code), A.lower[(size_t)j * A.m + r] + h);
+      const double ph = F::factor(F::axis(prm, j), x);
+      double a0, a1;
+      F::dlog(prm, j, x, ph, a0, a1);
+      phi[j][code] = ph;
+      d0[j][code] = a0;
+      d1[j][code] = a1;
+    }
+    __syncwarp();
+    double loc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) loc[k] = 0.0;
+    for (int p = lane; p < A.npts; p += 32) {
+      const uint64_t w = A.codes[p];
+      double f = 1.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) f *= phi[j][(w >> (4 * j)) & 15];
+      const double wf = vol * R.w[(int)(w >> 32)][0] * f;
+      loc[0] += wf;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int code = (int)((w >> (4 * j)) & 15);
+        loc[1 + j] = fma(wf, d0[j][code], loc[1 + j]);
+        loc[1 + N + j] = fma(wf, d1[j][code], loc[1 + N + j]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) nadd(acc[k], loc[k]);
+    __syncwarp();
+  }
+  // warp, then block reduction (fixed order)
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[k] = ncomb(acc[k], shfl_down_nsum(acc[k], off));
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[wib][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < K) {
+    NSum t = red[0][threadIdx.x];
+    for (int wq = 1; wq < 4; ++wq) t = ncomb(t, red[wq][threadIdx.x]);
+    A.part[((size_t)blockIdx.x * K + threadIdx.x) * 2] = t.s;
+    A.part[((size_t)blockIdx.x * K + threadIdx.x) * 2 + 1] = t.c;
+  }
+  if (!last_block_arrived(A.ticket)) return;
+  if (threadIdx.x < K) {
+    NSum t = {0.0, 0.0};
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      NSum q;
+      q.s = A.part[((size_t)b * K + threadIdx.x) * 2];
+      q.c = A.part[((size_t)b * K + threadIdx.x) * 2 + 1];
+      t = ncomb(t, q);
+    }
+    A.out[threadIdx.x] = nval(t);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 template <class F, int N, int THREADS>
 cudaError_t launch_loop(const EvalRule& R, const LoopArgs& A, int grid, int block, size_t smem, cudaStream_t st) {
@@ -579,6 +697,16 @@ cudaError_t launch_standalone(const EvalRule& R, const StandaloneArgs& A, int gr
   return cudaGetLastError();
 }
 
+template <class F, int N>
+cudaError_t launch_grad(const EvalRule& R, const GradArgs& A, int grid, cudaStream_t st) {
+  if constexpr (F::kHasGrad) {
+    k_gradient<F, N><<<grid, 128, 0, st>>>(R, A);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorNotSupported;
+  }
+}
+
 template <template <int> class FamOf, int THREADS>
 FamilyKernels make_family_kernels() {
   FamilyKernels k = {};
@@ -586,6 +714,7 @@ FamilyKernels make_family_kernels() {
 #define PG_SET(NN)                                                                              \
   k.loop[NN] = &launch_loop<FamOf<NN>, NN, THREADS>;                                            \
   k.fill[NN] = &launch_fill<FamOf<NN>, NN>;                                                     \
+  k.grad[NN] = &launch_grad<FamOf<NN>, NN>;                                                     \
   k.fill_fn[NN] = (const void*)&k_factor_cache<FamOf<NN>, NN>;                                  \
   k.standalone[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, false>;                         \
   k.standalone_diag[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, true>;                     \

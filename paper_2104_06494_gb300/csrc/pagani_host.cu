@@ -86,8 +86,8 @@ __global__ void k_uniform_split(Pool P, int d, int log2d, int64_t s0) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s0; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = i;
     for (int j = n - 1; j >= 0; --j) {
-      const int digit = (int)(r % d);
-      r /= d;
+      const int digit = (int)(r & (d - 1));  // d is a power of two
+      r >>= log2d;
       P.lower[(size_t)j * P.cap + i] = (double)digit / (double)d;
       P.level[(size_t)j * P.cap + i] = (uint8_t)log2d;
     }
@@ -161,9 +161,13 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   const int64_t ntiles = (s + TILE - 1) / TILE;
   __shared__ long long shl[THREADS / 32];
   __shared__ NSum shn[THREADS / 32];
+  // each thread sums its ITEMS regions of a tile plainly (relative error at
+  // most (ITEMS - 1) u) and adds that partial into Neumaier accumulators, so
+  // the sums stay compensated across all partials at a third of the FP64 work
   NSum va = {0.0, 0.0}, ea = {0.0, 0.0}, fv = {0.0, 0.0};
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     long long cnt = 0;
+    double tv = 0.0, te = 0.0, tf = 0.0;
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
@@ -171,15 +175,18 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
         const double v = V[i], e = E[i];
         if (final_active(v, e, c)) {
           ++cnt;
-          nadd(va, v);
-          nadd(ea, e);
+          tv += v;
+          te += e;
         } else {
           int L = 0;
           for (int j = 0; j < n; ++j) L += level[(size_t)j * cap + i];
-          nadd(fv, pow2_neg(L));
+          tf += pow2_neg(L);
         }
       }
     }
+    nadd(va, tv);
+    nadd(ea, te);
+    nadd(fv, tf);
     const long long tc = block_sum_ll<THREADS>(cnt, shl);
     if (threadIdx.x == 0) A.pool.tile_count[tile] = tc;
   }
@@ -283,7 +290,23 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
   Ctrl& c = *A.ctrl;
-  if (c.done) return;
+  const bool logl = c.keep_leaves && A.leaves.lower != nullptr;
+  if (c.done) {
+    // the integration ended in this iteration: every box of it is a leaf
+    if (logl) {
+      const int64_t s = c.s, base = c.leaf_count, cap = A.pool.cap, lcap = A.leaves.cap;
+      const int n = A.pool.n, src = (c.it - 1) & 1;
+      if (base + s > lcap && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&c.leaf_overflow, 1);
+      for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < s; i += (int64_t)gridDim.x * THREADS) {
+        if (base + i >= lcap) break;
+        for (int j = 0; j < n; ++j) {
+          A.leaves.lower[(size_t)j * lcap + base + i] = A.pool.lower[((size_t)src * n + j) * cap + i];
+          A.leaves.level[(size_t)j * lcap + base + i] = A.pool.level[((size_t)src * n + j) * cap + i];
+        }
+      }
+    }
+    return;
+  }
   constexpr int TILE = THREADS * ITEMS;
   const int64_t s = c.s;
   const int n = A.pool.n;
@@ -308,6 +331,18 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
       }
       int total;
       const int rank = block_rank<THREADS>(act, shr, &total);
+      if (logl && !act && i < s) {
+        // finished box: its rank among the finished ones is i - (survivors before i)
+        const int64_t pos = c.leaf_count + i - (base + rank);
+        if (pos < A.leaves.cap) {
+          for (int j = 0; j < n; ++j) {
+            A.leaves.lower[(size_t)j * A.leaves.cap + pos] = lo_s[(size_t)j * cap + i];
+            A.leaves.level[(size_t)j * A.leaves.cap + pos] = lv_s[(size_t)j * cap + i];
+          }
+        } else {
+          bad |= 2;
+        }
+      }
       if (act) {
         const int64_t q = base + rank;
         const int k = A.pool.K[i];
@@ -329,9 +364,11 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
       base += total;
     }
   }
-  if (bad) atomicExch(&c.watchdog, 1);
+  if (bad & 1) atomicExch(&c.watchdog, 1);
+  if (bad & 2) atomicExch(&c.leaf_overflow, 1);
   if (!last_block_arrived(&c.ticket_split)) return;
   if (threadIdx.x == 0) {
+    if (logl) c.leaf_count += c.s - c.n_surv;
     c.s = 2 * c.n_surv;
     c.it += 1;
     __threadfence();
@@ -391,6 +428,15 @@ struct Workspace {
   TraceRec* trace = nullptr;
   int trace_cap = 0;
   void* fcache = nullptr;
+  LeafLog leaves = {nullptr, nullptr, 0};
+  void* leaf_alloc[2] = {nullptr, nullptr};
+  int leaf_n = 0;
+  int64_t last_leaves = -1;   // leaf count of the last integration that kept them
+  uint64_t* codes[kMaxDim + 1] = {nullptr};
+  int ncodes[kMaxDim + 1] = {0};
+  double* grad_part = nullptr;
+  unsigned int* grad_ticket = nullptr;
+  double* grad_out = nullptr;
   int max_grid = 0;
   cudaStream_t own_stream = nullptr;
   std::vector<void*> allocs;
@@ -423,10 +469,25 @@ static void release_graphs(Workspace& w) {
   w.graphs.clear();
 }
 
+static void release_leaf_log(Workspace& w) {
+  for (void*& p : w.leaf_alloc) {
+    if (p) cudaFree(p);
+    p = nullptr;
+  }
+  w.leaves = LeafLog{nullptr, nullptr, 0};
+  w.leaf_n = 0;
+  w.last_leaves = -1;
+}
+
 static void release_ws(Workspace& w) {
   release_graphs(w);
+  release_leaf_log(w);
   for (void* p : w.allocs) cudaFree(p);
   w.allocs.clear();
+  for (int i = 0; i <= kMaxDim; ++i) {
+    w.codes[i] = nullptr;
+    w.ncodes[i] = 0;
+  }
   w.cap = 0;
   w.n = 0;
   w.pool = Pool{};
@@ -483,6 +544,18 @@ static int ensure_workspace(int64_t want_cap, int n) {
     PG_ALLOC(fc, (size_t)kMaxDim * kCacheSlots * kCodes);
     w.fcache = fc;
   }
+  PG_ALLOC(w.grad_part, (size_t)w.max_grid * (2 * kMaxDim + 1) * 2);
+  PG_ALLOC(w.grad_ticket, 1);
+  PG_ALLOC(w.grad_out, 2 * kMaxDim + 1);
+  for (int d = 2; d <= kMaxDim; ++d) {
+    std::vector<uint64_t> pc = point_codes(d);
+    PG_ALLOC(w.codes[d], pc.size());
+    w.ncodes[d] = (int)pc.size();
+    e = cudaMemcpy(w.codes[d], pc.data(), pc.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  }
+  e = cudaMemset(w.grad_ticket, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
 #undef PG_ALLOC
   w.pool.cap = cap;
   w.pool.n = nn;
@@ -492,6 +565,26 @@ static int ensure_workspace(int64_t want_cap, int n) {
   e = cudaMemset(w.ctrl, 0, sizeof(Ctrl));
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
   if (!w.own_stream) cudaStreamCreateWithFlags(&w.own_stream, cudaStreamNonBlocking);
+  return 0;
+}
+
+// Leaf log for up to cap boxes of dimension n (allocated on first request;
+// the cached graphs embed its pointers, so they are rebuilt when it moves).
+static int ensure_leaf_log(int64_t cap, int n) {
+  Workspace& w = g_ws;
+  if (w.leaves.lower && w.leaves.cap >= cap && w.leaf_n >= n) return 0;
+  release_graphs(w);
+  release_leaf_log(w);
+  cudaError_t e = cudaMalloc(&w.leaf_alloc[0], sizeof(double) * (size_t)n * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&w.leaf_alloc[1], (size_t)n * cap);
+  if (e != cudaSuccess) {
+    release_leaf_log(w);
+    return fail(PAGANI_ERR_CUDA, std::string("leaf log allocation: ") + cudaGetErrorString(e));
+  }
+  w.leaves.lower = static_cast<double*>(w.leaf_alloc[0]);
+  w.leaves.level = static_cast<uint8_t*>(w.leaf_alloc[1]);
+  w.leaves.cap = cap;
+  w.leaf_n = n;
   return 0;
 }
 
@@ -591,6 +684,7 @@ static LoopArgs loop_args(int use_graph, cudaGraphConditionalHandle hm, cudaGrap
   a.h_probe = hp;
   a.fcache = w.fcache;
   a.fcache_levels = kCacheLevels;
+  a.leaves = w.leaves;
   return a;
 }
 
@@ -694,6 +788,11 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   rc = ensure_workspace(max_regions > s0 ? max_regions : s0, n);
   if (rc) return out->status = rc;
   Workspace& w = g_ws;
+  if (o.keep_leaves) {
+    rc = ensure_leaf_log(4 * (max_regions > s0 ? max_regions : s0), n);
+    if (rc) return out->status = rc;
+  }
+  w.last_leaves = -1;
   if (!st) st = w.own_stream;
   const FamilyKernels& fk = family_kernels(fam);
   Launch L;
@@ -717,6 +816,7 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   h.it = 1;
   h.status = -100;
   h.l0 = log2d;
+  h.keep_leaves = o.keep_leaves ? 1 : 0;
   IntegrandParams prm = to_params(fam, n, params);
   cudaError_t e;
 #define PG_CK(x)                                                                          \
@@ -823,6 +923,17 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   out->n_regions = h.n_regions_total;
   out->n_active_last = h.s;
   out->finished_volume = nval(h.fin_volume_acc);
+  out->active_volume = h.active_volume;
+  out->n_leaves = -1;
+  if (o.keep_leaves && h.done) {
+    if (h.leaf_overflow) {
+      g_err = "the leaf log ran out of room; n_leaves = -1";
+    } else {
+      out->n_leaves = h.leaf_count + h.s;
+      w.last_leaves = out->n_leaves;
+      w.leaf_n = n;
+    }
+  }
   if (h.watchdog == 1) return out->status = fail(PAGANI_ERR_WATCHDOG, "region depth limit reached on one axis");
   if (h.watchdog) return out->status = fail(PAGANI_ERR_WATCHDOG, "device loop exceeded its iteration bound");
   if (!h.done) return out->status = fail(PAGANI_ERR_WATCHDOG, "device loop ended without a result");
@@ -1024,10 +1135,12 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   out->n_regions = h.n_regions_total;
   out->n_active_last = h.s;
   out->finished_volume = nval(h.fin_volume_acc);
+  out->active_volume = h.active_volume;
   out->eval_launches = h.it;
   out->kernel_launches = launches;
   out->h2d_bytes = (int64_t)(sizeof(Ctrl) + sizeof(prm));
   out->d2h_bytes = d2h;
+  out->n_leaves = -1;
   if (h.watchdog) return out->status = fail(PAGANI_ERR_WATCHDOG, "device-side consistency check failed");
   if (!h.done) return out->status = fail(PAGANI_ERR_WATCHDOG, "loop ended without a result");
   out->status = h.status;
@@ -1049,6 +1162,7 @@ void pagani_default_options(pagani_options* o) {
   o->init_div = 0;
   o->it_max = 100;
   o->use_graph = 1;
+  o->keep_leaves = 0;
 }
 
 int pagani_integrate_ex(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
@@ -1136,6 +1250,73 @@ int pagani_evaluate(int dim, int integrand_id, const double* params, int64_t m, 
            : fk.standalone[dim](rule, a, (int)grid, fk.threads, smem, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
+  return 0;
+}
+
+int pagani_leaves(int dim, int64_t cap, double* lower, uint8_t* level, int64_t* n_out, void* cuda_stream) {
+  if (!n_out) return fail(PAGANI_ERR_ARGUMENT, "n_out is NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace& w = g_ws;
+  if (w.last_leaves < 0 || !w.leaves.lower) return fail(PAGANI_ERR_ARGUMENT, "no leaf set kept by the last integration");
+  if (dim != w.leaf_n) return fail(PAGANI_ERR_DIM, "dim differs from the kept leaf set");
+  *n_out = w.last_leaves;
+  if (!lower || !level) return 0;  // size query
+  if (cap < w.last_leaves) return fail(PAGANI_ERR_ARGUMENT, "cap below the leaf count");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : w.own_stream;
+  const int64_t m = w.last_leaves;
+  for (int j = 0; j < dim; ++j) {
+    cudaError_t e = cudaMemcpyAsync(lower + (size_t)j * cap, w.leaves.lower + (size_t)j * w.leaves.cap,
+                                    sizeof(double) * m, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(level + (size_t)j * cap, w.leaves.level + (size_t)j * w.leaves.cap, m,
+                          cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  return 0;
+}
+
+int pagani_gradient(int dim, int integrand_id, const double* params, int64_t m, const double* lower,
+                    const uint8_t* level, double* out, void* cuda_stream) {
+  if (dim < PAGANI_MIN_DIM || dim > PAGANI_MAX_DIM) return fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
+  if (integrand_id != kFamProductPeak && integrand_id != kFamGaussian && integrand_id != kFamC0)
+    return fail(PAGANI_ERR_INTEGRAND, "gradients exist for the product peak, Gaussian and C0 families");
+  if (!params || !out || m < 0) return fail(PAGANI_ERR_ARGUMENT, "bad params, out or m");
+  int rc = check_params(integrand_id, dim, params);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  const RuleTable* rt = get_rule(dim);
+  if (!rt) return fail(PAGANI_ERR_CUDA, "rule construction failed");
+  rc = ensure_workspace(4096, dim);
+  if (rc) return rc;
+  Workspace& w = g_ws;
+  const int K = 2 * dim + 1;
+  if (m == 0) {
+    for (int k = 0; k < K; ++k) out[k] = 0.0;
+    return 0;
+  }
+  if (!lower || !level) return fail(PAGANI_ERR_ARGUMENT, "null device pointer");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : w.own_stream;
+  IntegrandParams prm = to_params(integrand_id, dim, params);
+  cudaError_t e = cudaMemcpyAsync(w.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  GradArgs a;
+  a.lower = lower;
+  a.level = level;
+  a.m = m;
+  a.codes = w.codes[dim];
+  a.npts = w.ncodes[dim];
+  a.prm = w.prm;
+  a.part = w.grad_part;
+  a.ticket = w.grad_ticket;
+  a.out = w.grad_out;
+  int64_t grid = (m + 3) / 4;
+  if (grid > w.max_grid) grid = w.max_grid;
+  e = family_kernels(integrand_id).grad[dim](to_eval_rule(*rt), a, (int)grid, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, w.grad_out, sizeof(double) * K, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("gradient: ") + cudaGetErrorString(e));
   return 0;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 PAGANI engine (not part of the C ABI).
 #pragma once
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -49,6 +50,7 @@ struct RuleTable {
 };
 
 bool build_rule(int n, RuleTable* out, double* max_residual);
+std::vector<uint64_t> point_codes(int n);
 int num_points(int n);
 int64_t orbit_count(int n, int g);
 
@@ -106,6 +108,10 @@ struct Ctrl {
   int32_t loop_guard;        // iterations counted by the count kernel
   int32_t total_probes;      // threshold probes over the whole call
   int32_t l0;                // level of the Uniform-Split boxes (log2 of the divisions)
+  double active_volume;      // volume of the regions evaluated in the last iteration
+  int32_t keep_leaves;       // append finished boxes to the leaf log
+  int32_t leaf_overflow;     // the leaf log ran out of room
+  int64_t leaf_count;        // boxes in the leaf log before this iteration's
 };
 
 // One per-iteration record (mirrors pagani_trace_record in pagani.h).
@@ -117,7 +123,7 @@ struct TraceRec {
 
 // Per-block partial results written by the evaluate kernel.
 struct EvalPartial {
-  NSum v, e;
+  NSum v, e, vol;
   double emin, emax;
   long long n_rel;
   int nonfinite;
@@ -158,6 +164,14 @@ struct Pool {
   int n;
 };
 
+// Leaf log: the boxes classified finished, appended per iteration, and at
+// the end every box of the last iteration (SoA [n][cap]).
+struct LeafLog {
+  double* lower;
+  uint8_t* level;
+  int64_t cap;
+};
+
 // Arguments of the loop kernels (by value).
 struct LoopArgs {
   Pool pool;
@@ -172,7 +186,22 @@ struct LoopArgs {
   cudaGraphConditionalHandle h_main, h_probe;
   void* fcache;          // per-axis factor cache (element type of the family), or null
   int fcache_levels;     // deepest cached level
+  LeafLog leaves;        // leaf log (null pointers: none)
 };
+
+// Arguments of the gradient kernel.
+struct GradArgs {
+  const double* lower;     // [n][m]
+  const uint8_t* level;    // [n][m]
+  int64_t m;
+  const uint64_t* codes;   // packed rule points
+  int npts;
+  const IntegrandParams* prm;
+  double* part;            // per block: 2n + 1 Neumaier pairs (value, gradient)
+  unsigned int* ticket;
+  double* out;             // 2n + 1 totals (value first)
+};
+typedef cudaError_t (*GradLauncher)(const EvalRule&, const GradArgs&, int grid, cudaStream_t);
 
 // Arguments of the standalone evaluate entry point.
 struct StandaloneArgs {
@@ -199,6 +228,7 @@ struct FamilyKernels {
   StandaloneLauncher standalone[kMaxDim + 1];
   StandaloneLauncher standalone_diag[kMaxDim + 1];
   const void* loop_fn[kMaxDim + 1];        // kernel symbols (for occupancy queries / graph nodes)
+  GradLauncher grad[kMaxDim + 1];          // gradient over a box list (positive product families)
   int threads;                             // block size
   int table_bytes_per_thread[kMaxDim + 1];
 };

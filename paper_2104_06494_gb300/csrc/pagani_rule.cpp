@@ -282,3 +282,59 @@ bool build_rule(int n, RuleTable* out, double* max_residual) {
 }
 
 }  // namespace pg
+
+namespace pg {
+
+// Every rule point of dimension n as a packed word: bits 4j..4j+3 hold the
+// coordinate code (Code enum) of axis j, bits 32..35 the generator orbit.
+// Orbits are enumerated from their structure: axes chosen in increasing
+// order, every sign pattern.
+std::vector<uint64_t> point_codes(int n) {
+  std::vector<uint64_t> out;
+  auto emit = [&](int g, const int* axes, const int* codes, int k) {
+    uint64_t w = (uint64_t)g << 32;
+    for (int t = 0; t < k; ++t) w |= (uint64_t)codes[t] << (4 * axes[t]);
+    out.push_back(w);
+  };
+  const int one_axis_gen[4] = {kGenL1, kGenL2, kGenL3, kGenLp};
+  const int one_axis_code[4] = {kR1P, kR2P, kR3P, kRpP};
+  emit(kGenCentre, nullptr, nullptr, 0);
+  for (int g = 0; g < 4; ++g)
+    for (int j = 0; j < n; ++j)
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        int axes[1] = {j}, codes[1] = {one_axis_code[g] + sgn};
+        emit(one_axis_gen[g], axes, codes, 1);
+      }
+  for (int j = 0; j < n; ++j)
+    for (int k = j + 1; k < n; ++k)
+      for (int s = 0; s < 4; ++s) {
+        int axes[2] = {j, k}, codes[2] = {kR1P + (s & 1), kR1P + (s >> 1)};
+        emit(kGenL1L1, axes, codes, 2);
+      }
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) {
+      if (j == k) continue;
+      for (int s = 0; s < 4; ++s) {
+        int axes[2] = {j, k}, codes[2] = {kR1P + (s & 1), kR2P + (s >> 1)};
+        emit(kGenL1L2, axes, codes, 2);
+      }
+    }
+  for (int j = 0; j < n; ++j)
+    for (int k = j + 1; k < n; ++k)
+      for (int l = k + 1; l < n; ++l)
+        for (int s = 0; s < 8; ++s) {
+          int axes[3] = {j, k, l}, codes[3] = {kR1P + (s & 1), kR1P + ((s >> 1) & 1), kR1P + (s >> 2)};
+          emit(kGenL1L1L1, axes, codes, 3);
+        }
+  for (int s = 0; s < (1 << n); ++s) {
+    int axes[8], codes[8];
+    for (int j = 0; j < n; ++j) {
+      axes[j] = j;
+      codes[j] = kR0P + ((s >> j) & 1);
+    }
+    emit(kGenL0All, axes, codes, n);
+  }
+  return out;
+}
+
+}  // namespace pg

@@ -99,6 +99,9 @@ def config_workloads() -> dict[str, Workload]:
         "corner_peak_d8": Workload("corner_peak_d8", CORNER_PEAK, 8, 1e-6,
                                    draw_params(CORNER_PEAK, 8, BASE_SEED + 4), 400_000_000),
         "c0_d8": Workload("c0_d8", C0, 8, 1e-6, draw_params(C0, 8, BASE_SEED + 5), 400_000_000),
+        "gaussian_d6_grad": Workload("gaussian_d6_grad", GAUSSIAN, 6, 1e-7,
+                                     draw_params(GAUSSIAN, 6, BASE_SEED + 6, [("n", 5.0, 15.0), ("n", 0.2, 0.8)]),
+                                     40_000_000, notes="differentiation: theta = (a_1..a_6, w_1..w_6)"),
     }
 
 

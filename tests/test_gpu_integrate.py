@@ -137,3 +137,40 @@ def test_bench_workload_gaussian_d5_full_size(pg):
     compare_runs(g, o)
     ex = cf.closed_form(w.family, w.dim, w.params)
     assert abs(g.estimate - ex) <= g.errorest
+
+
+def test_config_corner_peak_d8_full_size(pg):
+    """The 8-D corner peak at its full size (epsrel 1e-6): same region-set
+    evolution as the oracle (about 1.5e5 regions of 1105 points)."""
+    w = config_workloads()["corner_peak_d8"]
+    o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions)
+    g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
+    compare_runs(g, o)
+
+
+def test_config_c0_d8_full_size_properties(pg):
+    """The 8-D C0 workload at full size (epsrel 1e-6, pool capped at 4e8
+    regions: ~4.6e8 regions over 22 iterations, 2.2e8 in the last) is beyond
+    the oracle; properties that hold at any size: the estimate within its
+    error of the closed form, exact bookkeeping of the dyadic volume, and
+    s_{it+1} = 2 (survivors of it)."""
+    w = config_workloads()["c0_d8"]
+    g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    assert g.status in (0, 2, 3)
+    assert abs(g.estimate - ex) <= g.errorest
+    assert abs(g.finished_volume + g.active_volume - 1.0) <= 1e-13
+    tr = g.trace
+    for a, b in zip(tr[:-1], tr[1:]):
+        assert b["s"] == 2 * a["n_survivors"]
+    assert g.n_regions == int(tr["s"].sum())
+
+
+def test_volume_bookkeeping_matches_oracle(pg):
+    params = draw_params(1, 3, 61)
+    o = oracle.integrate(1, 3, params, 1e-7, max_regions=2_000_000, want_regions=True)
+    g = pg.pagani_integrate_ex(3, 1, params, 1e-7, max_regions=2_000_000)
+    act = float(np.sum(np.prod(o.final_width, axis=1)))
+    assert abs(g.finished_volume - o.finished_volume) <= 1e-15
+    assert abs(g.active_volume - act) <= 1e-15
+    assert abs(g.finished_volume + g.active_volume - 1.0) <= 1e-14
