@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form report")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle time budget per integral")
     ap.add_argument("--quiet", action="store_true")
     return ap.parse_args()
@@ -202,6 +203,51 @@ def differentiation_report(pg, torch, flush, reps: int = 3):
             "grad_max_err_vs_closed_form": float(np.max(np.abs(g - np.array(gc)) / scale)),
             "grad_err_scale": "|I| for d/da, a_j |I| for d/dw",
             "backward_evals_per_s": r.n_leaves * npoints(n) / (bwd_ms * 1e-3)}
+
+
+def batching_report(pg, torch, flush, slot: int = 16384):
+    """The batched form: 4096 independent integrals (dimension 3..8, five
+    families, epsrel 1e-4..1e-8, each with a pool of `slot` regions) in one
+    graph launch, next to the same 4096 integrals as looped single calls with
+    the same pool size."""
+    import numpy as np
+    from oracle import closed_forms as cf
+    from paper_2104_06494_gb300.workloads import batch_workloads
+    items = batch_workloads()
+    pg.pagani_integrate_batch(items, slot)          # warm-up: workspace, autotune, graph
+    flush.zero_()
+    torch.cuda.synchronize()
+    res, dev_ms = pg.pagani_integrate_batch(items, slot)
+    t0 = time.perf_counter()
+    res, _ = pg.pagani_integrate_batch(items, slot)
+    batch_wall_ms = (time.perf_counter() - t0) * 1e3
+    stream = torch.cuda.current_stream().cuda_stream
+    for w in items[:32]:                             # warm the single-call graphs
+        pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, slot, relerr_filter=w.relerr_filter,
+                               stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    a.record()
+    singles = [pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, slot,
+                                      relerr_filter=w.relerr_filter, stream=stream) for w in items]
+    b.record()
+    torch.cuda.synchronize()
+    loop_wall_ms = (time.perf_counter() - t0) * 1e3
+    loop_dev_ms = a.elapsed_time(b)
+    same = sum(int(r["status"] == g.status and r["n_regions"] == g.n_regions and
+                   abs(r["estimate"] - g.estimate) <= 1e-12 * abs(g.estimate) + 1e-300)
+               for r, g in zip(res, singles))
+    ex = np.array([cf.closed_form(w.family, w.dim, w.params) for w in items])
+    inside = np.abs(res["estimate"] - ex) <= res["errorest"]
+    evals = int(sum(int(r["n_regions"]) * npoints(w.dim) for r, w in zip(res, items)))
+    return {"items": len(items), "max_regions_per_item": slot, "batch_device_ms": dev_ms,
+            "batch_wall_ms": batch_wall_ms, "looped_single_wall_ms": loop_wall_ms,
+            "looped_single_device_ms": loop_dev_ms, "speedup_wall": loop_wall_ms / batch_wall_ms,
+            "integrals_per_s": len(items) / (batch_wall_ms * 1e-3), "evals_per_s": evals / (dev_ms * 1e-3),
+            "items_equal_to_single_calls": same,
+            "status_counts": {int(k): int(v) for k, v in zip(*np.unique(res["status"], return_counts=True))},
+            "within_errorest_of_closed_form": float(inside.mean())}
 
 
 def main():
@@ -391,6 +437,8 @@ def main():
             torch.cuda.synchronize()
             line["config"]["time_to_result_ms"][w.name] = a.elapsed_time(b)
         line["differentiation"] = differentiation_report(pg, torch, flush)
+        if not args.no_batch:
+            line["batching"] = batching_report(pg, torch, flush)
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))

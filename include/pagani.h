@@ -147,6 +147,40 @@ int pagani_integrate_ex(int dim, int integrand_id, const double* params, double 
 int pagani_integrate_noalloc(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
                              int64_t max_regions, void* cuda_stream, pagani_result* out);
 
+/* Batched integration: many independent integrals in one CUDA-graph
+ * launch.  Not in the paper: a throughput form of Algorithm 2 for workloads
+ * made of many small integrals.  Every item runs its own Algorithm 2/3 state
+ * (same decisions as pagani_integrate) in a fixed region pool of
+ * max_regions_per_item regions (its memory requirement, Sec. 3.5.2).  Items
+ * are grouped by (integrand_id, dim); per iteration one Evaluate kernel runs
+ * per group over all its items' regions, then one block per item reduces,
+ * classifies, searches a threshold, compacts and splits.  Each group's
+ * Evaluate grid is chosen by an autotuner on the first batch that contains
+ * the group (timed on that batch's first iteration) and cached.
+ * items: host array of count items; results: host array of count results (in
+ * item order).  opt: NULL = defaults (heuristic_filter, it_max and
+ * use_graph are used).  device_ms (may be NULL) receives the device time of
+ * the loop (CUDA events on the stream).  Returns 0 when the batch ran (each
+ * item's status in its result), < 0 on an argument or CUDA error. */
+typedef struct {
+  int32_t dim;
+  int32_t integrand_id;
+  int32_t relerr_filter;  /* 1: Rel-Err-Classify on; 0 for sign-changing integrands */
+  int32_t reserved;
+  double epsrel, epsabs;
+  double params[17];      /* family layout (see above) */
+} pagani_batch_item;
+
+typedef struct {
+  double estimate, errorest;
+  int32_t status, iterations;
+  int64_t n_regions;
+} pagani_batch_result;
+
+int pagani_integrate_batch(int64_t count, const pagani_batch_item* items, int64_t max_regions_per_item,
+                           const pagani_options* opt, void* cuda_stream, pagani_batch_result* results,
+                           double* device_ms);
+
 /* Allocates (or grows) the library workspace for up to max_regions regions
  * of dimension dim so that later calls do not allocate (the paper times
  * integration without workspace set-up, Sec. 4).  Returns 0 or < 0. */

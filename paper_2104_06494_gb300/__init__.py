@@ -41,6 +41,17 @@ class Result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("integrand_id", ctypes.c_int32), ("relerr_filter", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("epsrel", ctypes.c_double), ("epsabs", ctypes.c_double),
+                ("params", ctypes.c_double * 17)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("errorest", ctypes.c_double), ("status", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("n_regions", ctypes.c_int64)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("relerr_filter", ctypes.c_int32), ("heuristic_filter", ctypes.c_int32),
                 ("init_div", ctypes.c_int32), ("it_max", ctypes.c_int32), ("use_graph", ctypes.c_int32),
@@ -55,7 +66,8 @@ TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.i
 # every symbol include/pagani.h declares
 EXPORTED = ["pagani_default_options", "pagani_integrate", "pagani_integrate_ex", "pagani_workspace_reserve",
             "pagani_workspace_release", "pagani_evaluate", "pagani_rule_tables", "pagani_fp64_peak",
-            "pagani_last_error", "pagani_version", "pagani_integrate_noalloc", "pagani_leaves", "pagani_gradient"]
+            "pagani_last_error", "pagani_version", "pagani_integrate_noalloc", "pagani_leaves", "pagani_gradient",
+            "pagani_integrate_batch"]
 
 _lib = None
 
@@ -97,6 +109,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.pagani_gradient.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p, P(ctypes.c_double), ctypes.c_void_p]
     lib.pagani_gradient.restype = ctypes.c_int
+    lib.pagani_integrate_batch.argtypes = [ctypes.c_int64, P(BatchItem), ctypes.c_int64, P(Options), ctypes.c_void_p,
+                                           P(BatchResult), P(ctypes.c_double)]
+    lib.pagani_integrate_batch.restype = ctypes.c_int
     lib.pagani_rule_tables.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64)]
     lib.pagani_rule_tables.restype = ctypes.c_int
     lib.pagani_fp64_peak.argtypes = [P(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]
@@ -281,6 +296,36 @@ def pagani_gradient(dim: int, integrand_id: int, params, lower, level, stream: i
     if rc < 0:
         raise PaganiError(f"pagani_gradient failed ({rc}): {last_error()}")
     return out[0], out[1:]
+
+
+def pagani_integrate_batch(items, max_regions_per_item: int, heuristic_filter: int = 1, it_max: int = 100,
+                           use_graph: int = 1, stream: int | None = None):
+    """C ABI pagani_integrate_batch.  items: sequence of Workload-like objects
+    (dim, family, params, epsrel, epsabs, relerr_filter).  Returns (numpy
+    structured results in item order, device milliseconds of the loop)."""
+    lib = load()
+    n = len(items)
+    arr = (BatchItem * n)()
+    for i, w in enumerate(items):
+        arr[i].dim = w.dim
+        arr[i].integrand_id = w.family
+        arr[i].relerr_filter = w.relerr_filter
+        arr[i].epsrel = w.epsrel
+        arr[i].epsabs = w.epsabs
+        for k, v in enumerate(w.params):
+            arr[i].params[k] = v
+    res = (BatchResult * n)()
+    o = Options(1, heuristic_filter, 0, it_max, use_graph, 0)
+    ms = ctypes.c_double(0.0)
+    rc = lib.pagani_integrate_batch(n, arr, max_regions_per_item, ctypes.byref(o), ctypes.c_void_p(stream or 0), res,
+                                    ctypes.byref(ms))
+    if rc < 0:
+        raise PaganiError(f"pagani_integrate_batch failed ({rc}): {last_error()}")
+    out = np.zeros(n, dtype=[("estimate", np.float64), ("errorest", np.float64), ("status", np.int32),
+                             ("iterations", np.int32), ("n_regions", np.int64)])
+    for i in range(n):
+        out[i] = (res[i].estimate, res[i].errorest, res[i].status, res[i].iterations, res[i].n_regions)
+    return out, ms.value
 
 
 def pagani_rule_tables(dim: int):

@@ -589,6 +589,70 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule 
   }
 }
 
+// ------------------------------------------------------ batched evaluate
+// Evaluate for one (family, n) group of a batch: one thread per sibling pair
+// over every instance's slot of the group's pool; each pair reads its
+// instance's parameters and iteration.  Writes V (rule), E (null-rule error
+// refined by the two-level estimate from the second iteration on) and K; the
+// per-instance sums are taken by the batch reduce kernel.
+template <class F, int N, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_evaluate_batch(const EvalRule R, const BatchArgs A,
+                                                            const BatchGroup G) {
+  typedef typename F::T T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
+  const int64_t slots = (int64_t)G.count * G.slot_cap;
+  const int64_t npairs = slots >> 1;
+  for (int64_t p = (int64_t)blockIdx.x * THREADS + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * THREADS) {
+    const int64_t iL = 2 * p;
+    const int li = (int)(iL / G.slot_cap);
+    const Ctrl& c = A.inst[G.first + li].c;
+    if (c.done || iL - (int64_t)li * G.slot_cap >= c.s) continue;
+    const int it = c.it;
+    const int buf = (it - 1) & 1;
+    const double* __restrict__ lower = G.lower + (size_t)buf * N * slots;
+    const uint8_t* __restrict__ level = G.level + (size_t)buf * N * slots;
+    const IntegrandParams& prm = A.prm[G.first + li];
+    const T base = F::base(prm);
+    double loL[N], wL[N], wR[N];
+    int lvLj[N];
+    int lvL = 0, lvR = 0, diff_axis = -1, diff_lv = 0;
+    double diff_lo = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const double2 lo2 = *reinterpret_cast<const double2*>(lower + (size_t)j * slots + iL);
+      const uchar2 lv2 = *reinterpret_cast<const uchar2*>(level + (size_t)j * slots + iL);
+      loL[j] = lo2.x;
+      wL[j] = pow2_neg(lv2.x);
+      wR[j] = pow2_neg(lv2.y);
+      lvLj[j] = lv2.x;
+      lvL += lv2.x;
+      lvR += lv2.y;
+      if (lo2.x != lo2.y || lv2.x != lv2.y) {
+        diff_axis = j;
+        diff_lo = lo2.y;
+        diff_lv = lv2.y;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      axis_entries<F, N, THREADS>(tab, R, prm, (const T*)nullptr, 0, loL[j], lvLj[j], j);
+    double S[kNumGen], D[N];
+    double VL, EL, VR, ER;
+    int KL, KR;
+    rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
+    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL), wL, VL, EL, KL, nullptr);
+    if (diff_axis >= 0)
+      axis_entries<F, N, THREADS>(tab, R, prm, (const T*)nullptr, 0, diff_lo, diff_lv, diff_axis);
+    rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
+    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR), wR, VR, ER, KR, nullptr);
+    if (it > 1) two_level(VL, VR, G.Vp[p], EL, ER);
+    *reinterpret_cast<double2*>(G.V + iL) = make_double2(VL, VR);
+    *reinterpret_cast<double2*>(G.E + iL) = make_double2(EL, ER);
+    *reinterpret_cast<uchar2*>(G.K + iL) = make_uchar2((unsigned char)KL, (unsigned char)KR);
+  }
+}
+
 // ------------------------------------------------------------ gradient kernel
 // d/dtheta of the rule estimate summed over a fixed list of boxes (the leaf
 // set of an integration): vol * sum_points w_g f(x) d log phi_j(x_j)/d theta_j
@@ -707,6 +771,12 @@ cudaError_t launch_grad(const EvalRule& R, const GradArgs& A, int grid, cudaStre
   }
 }
 
+template <class F, int N, int THREADS>
+cudaError_t launch_batch_eval(const EvalRule& R, const BatchArgs& A, const BatchGroup& G, int grid, cudaStream_t st) {
+  k_evaluate_batch<F, N, THREADS><<<grid, THREADS, sizeof(typename F::T) * kCodes * N * THREADS, st>>>(R, A, G);
+  return cudaGetLastError();
+}
+
 template <template <int> class FamOf, int THREADS>
 FamilyKernels make_family_kernels() {
   FamilyKernels k = {};
@@ -715,6 +785,11 @@ FamilyKernels make_family_kernels() {
   k.loop[NN] = &launch_loop<FamOf<NN>, NN, THREADS>;                                            \
   k.fill[NN] = &launch_fill<FamOf<NN>, NN>;                                                     \
   k.grad[NN] = &launch_grad<FamOf<NN>, NN>;                                                     \
+  k.batch_eval[NN] = &launch_batch_eval<FamOf<NN>, NN, THREADS>;                                \
+  k.batch_eval_fn[NN] = (const void*)&k_evaluate_batch<FamOf<NN>, NN, THREADS>;                 \
+  cudaFuncSetAttribute((const void*)&k_evaluate_batch<FamOf<NN>, NN, THREADS>,                  \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
   k.fill_fn[NN] = (const void*)&k_factor_cache<FamOf<NN>, NN>;                                  \
   k.standalone[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, false>;                         \
   k.standalone_diag[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, true>;                     \

@@ -1148,6 +1148,523 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   return out->status;
 }
 
+// ======================================================================
+// Batched integration: many independent integrals in one graph launch.
+// Each instance keeps its own control block (the single-integral Ctrl: the
+// same decision code of Algorithms 2 and 3 runs per instance) and a fixed
+// slot of slot_cap regions in the pool of its (family, n) group.  Per
+// iteration: one Evaluate kernel per group (all instances' pairs), then one
+// block per instance reduces, classifies, searches a threshold, compacts and
+// splits within its slot.
+constexpr int kBatchThreads = 256;
+
+__device__ __forceinline__ void batch_slot(const BatchArgs& A, const BatchInst& I, int64_t& base, int64_t& slots,
+                                           const BatchGroup*& G) {
+  G = &A.groups[I.group];
+  slots = (int64_t)G->count * G->slot_cap;
+  base = (int64_t)I.local * G->slot_cap;
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch_uniform(const BatchArgs A) {
+  for (int b = blockIdx.x; b < A.n_inst; b += gridDim.x) {
+    const BatchInst& I = A.inst[b];
+    const BatchGroup* G;
+    int64_t base, slots;
+    batch_slot(A, I, base, slots, G);
+    const int n = I.n, l0 = I.c.l0, d = 1 << l0;
+    const int64_t s0 = I.c.s;
+    for (int64_t i = threadIdx.x; i < s0; i += kBatchThreads) {
+      int64_t r = i;
+      for (int j = n - 1; j >= 0; --j) {
+        const int digit = (int)(r & (d - 1));
+        r >>= l0;
+        G->lower[(size_t)j * slots + base + i] = (double)digit / (double)d;
+        G->level[(size_t)j * slots + base + i] = (uint8_t)l0;
+      }
+    }
+  }
+}
+
+// Sums, Rel-Err-Classify, termination and the Threshold-Classify trigger of
+// every instance (Algorithm 2), one block per instance.
+__global__ void __launch_bounds__(kBatchThreads) k_batch_reduce(const BatchArgs A) {
+  __shared__ EvalPartial sh[kBatchThreads / 32];
+  for (int b = blockIdx.x; b < A.n_inst; b += gridDim.x) {
+    BatchInst& I = A.inst[b];
+    Ctrl& c = I.c;
+    if (c.done) continue;
+    const BatchGroup* G;
+    int64_t base, slots;
+    batch_slot(A, I, base, slots, G);
+    const int buf = (c.it - 1) & 1;
+    const int64_t s_cur = c.s;  // read once: thread 0 updates c later in this pass
+    EvalPartial acc = eval_identity();
+    for (int64_t i = threadIdx.x; i < s_cur; i += kBatchThreads) {
+      const double v = G->V[base + i], e = G->E[base + i];
+      nadd(acc.v, v);
+      nadd(acc.e, e);
+      acc.emin = fmin(acc.emin, e);
+      acc.emax = fmax(acc.emax, e);
+      acc.n_rel += relerr_active(v, e, c.tau_rel, c.relerr_filter);
+      if (!isfinite(v) || !isfinite(e)) acc.nonfinite = 1;
+      int L = 0;
+      for (int j = 0; j < I.n; ++j) L += G->level[((size_t)buf * I.n + j) * slots + base + i];
+      nadd(acc.vol, pow2_neg(L));
+    }
+    const EvalPartial tot = eval_block_combine<kBatchThreads>(acc, sh);
+    if (threadIdx.x == 0) {
+      const int search = finalize_iteration_head(c, nval(tot.v), nval(tot.e), tot.n_rel, tot.emin, tot.emax,
+                                                 tot.nonfinite, nullptr, 0, nval(tot.vol));
+      if (search) atomicOr(&A.flags[0], 1);
+    }
+    __syncthreads();
+  }
+  if (!last_block_arrived(&A.tickets[0])) return;
+  if (threadIdx.x == 0) {
+    const int any = atomicExch(&A.flags[0], 0);
+    A.flags[2] = any;
+    set_cond(A.use_graph, A.h_probe, (unsigned)any);
+    __threadfence();
+  }
+}
+
+// One threshold-search probe for every instance still searching (Algorithm 3).
+__global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A) {
+  __shared__ NSum shn[kBatchThreads / 32];
+  __shared__ long long shl[kBatchThreads / 32];
+  for (int b = blockIdx.x; b < A.n_inst; b += gridDim.x) {
+    BatchInst& I = A.inst[b];
+    Ctrl& c = I.c;
+    if (c.done || !c.search_cont) continue;
+    const BatchGroup* G;
+    int64_t base, slots;
+    batch_slot(A, I, base, slots, G);
+    const int64_t s_cur = c.s;
+    const double t_cur = c.t;
+    NSum sa = {0.0, 0.0};
+    long long na = 0;
+    for (int64_t i = threadIdx.x; i < s_cur; i += kBatchThreads) {
+      const double e = G->E[base + i];
+      if (relerr_active(G->V[base + i], e, c.tau_rel, c.relerr_filter) && !(e < t_cur)) {
+        ++na;
+        nadd(sa, e);
+      }
+    }
+    const NSum tot = nsum_block_combine<kBatchThreads>(sa, shn);
+    const long long n = block_sum_ll<kBatchThreads>(na, shl);
+    if (threadIdx.x == 0) {
+      const int cont = threshold_step(c, n, nval(tot));
+      c.search_cont = cont;
+      if (cont) atomicOr(&A.flags[0], 1);
+    }
+    __syncthreads();
+  }
+  if (!last_block_arrived(&A.tickets[1])) return;
+  if (threadIdx.x == 0) {
+    const int any = atomicExch(&A.flags[0], 0);
+    A.flags[2] = any;
+    set_cond(A.use_graph, A.h_probe, (unsigned)any);
+    __threadfence();
+  }
+}
+
+// v_f, e_f, the memory and reachability checks, then Filter + parent update
+// + Split inside the instance's slot (Algorithm 2), one block per instance.
+__global__ void __launch_bounds__(kBatchThreads) k_batch_split(const BatchArgs A) {
+  __shared__ NSum shn[kBatchThreads / 32];
+  __shared__ long long shl[kBatchThreads / 32];
+  __shared__ int shr[kBatchThreads / 32];
+  __shared__ int go_on;
+  for (int b = blockIdx.x; b < A.n_inst; b += gridDim.x) {
+    BatchInst& I = A.inst[b];
+    Ctrl& c = I.c;
+    if (c.done) continue;
+    const BatchGroup* G;
+    int64_t base, slots;
+    batch_slot(A, I, base, slots, G);
+    const int n = I.n;
+    const int src = (c.it - 1) & 1, dst = src ^ 1;
+    const int64_t s_cur = c.s;  // read once: thread 0 rewrites c.s at the end of this pass
+    // pass 1: survivors and the finished accumulation
+    NSum va = {0.0, 0.0}, ea = {0.0, 0.0};
+    long long cnt = 0;
+    for (int64_t i = threadIdx.x; i < s_cur; i += kBatchThreads) {
+      const double v = G->V[base + i], e = G->E[base + i];
+      if (final_active(v, e, c)) {
+        ++cnt;
+        nadd(va, v);
+        nadd(ea, e);
+      }
+    }
+    const NSum tva = nsum_block_combine<kBatchThreads>(va, shn);
+    const NSum tea = nsum_block_combine<kBatchThreads>(ea, shn);
+    const long long n_surv = block_sum_ll<kBatchThreads>(cnt, shl);
+    if (threadIdx.x == 0) {
+      c.n_surv = n_surv;
+      go_on = 0;
+      if (2 * n_surv > c.max_regions) {
+        c.status = 2;
+        c.done = 1;
+        c.estimate = c.v + c.vf;
+        c.errorest = c.e + c.ef;
+      } else {
+        const double vf_new = c.v - nval(tva) + c.vf;
+        const double ef_new = c.e - nval(tea) + c.ef;
+        if (n_surv == 0 || ef_new > fmax(c.tau_rel * fabs(c.v + c.vf), c.tau_abs)) {
+          c.status = 3;
+          c.done = 1;
+          c.estimate = c.v + c.vf;
+          c.errorest = c.e + c.ef;
+        } else {
+          c.vf = vf_new;
+          c.ef = ef_new;
+          go_on = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (go_on) {
+      // pass 2: survivors in region order -> children 2q, 2q+1 of the other buffer
+      const double* lo_s = G->lower + (size_t)src * n * slots;
+      const uint8_t* lv_s = G->level + (size_t)src * n * slots;
+      double* lo_d = G->lower + (size_t)dst * n * slots;
+      uint8_t* lv_d = G->level + (size_t)dst * n * slots;
+      long long run = 0;
+      for (int64_t i0 = 0; i0 < s_cur; i0 += kBatchThreads) {
+        const int64_t i = i0 + threadIdx.x;
+        bool act = false;
+        double v = 0.0;
+        if (i < s_cur) {
+          v = G->V[base + i];
+          act = final_active(v, G->E[base + i], c);
+        }
+        int total;
+        const int rank = block_rank<kBatchThreads>(act, shr, &total);
+        if (act) {
+          const int64_t q = run + rank;
+          const int k = G->K[base + i];
+          G->Vp[base / 2 + q] = v;
+          for (int j = 0; j < n; ++j) {
+            const double lo = lo_s[(size_t)j * slots + base + i];
+            const int lv = lv_s[(size_t)j * slots + base + i];
+            double2 o = make_double2(lo, lo);
+            uchar2 ol = make_uchar2((unsigned char)lv, (unsigned char)lv);
+            if (j == k) {
+              if (lv >= 62) atomicExch(&c.watchdog, 1);
+              o.y = lo + pow2_neg(lv + 1);
+              ol = make_uchar2((unsigned char)(lv + 1), (unsigned char)(lv + 1));
+            }
+            *reinterpret_cast<double2*>(lo_d + (size_t)j * slots + base + 2 * q) = o;
+            *reinterpret_cast<uchar2*>(lv_d + (size_t)j * slots + base + 2 * q) = ol;
+          }
+        }
+        run += total;
+      }
+      if (threadIdx.x == 0) {
+        c.s = 2 * n_surv;
+        c.it += 1;
+        atomicOr(&A.flags[1], 1);
+      }
+    }
+    __syncthreads();
+  }
+  if (!last_block_arrived(&A.tickets[2])) return;
+  if (threadIdx.x == 0) {
+    const int any = atomicExch(&A.flags[1], 0);
+    A.flags[3] = any;
+    set_cond(A.use_graph, A.h_main, (unsigned)any);
+    __threadfence();
+  }
+}
+
+struct BatchWorkspace {
+  int dev = -1;
+  size_t bytes = 0;
+  void* mem = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::vector<int64_t> key;   // composition the cached graph was built for
+};
+static BatchWorkspace g_bws;
+static std::map<int, int> g_batch_grid;  // autotuned Evaluate grid per (family, n)
+
+static void release_batch(BatchWorkspace& b) {
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  if (b.graph) cudaGraphDestroy(b.graph);
+  b.exec = nullptr;
+  b.graph = nullptr;
+  b.key.clear();
+  if (b.mem) cudaFree(b.mem);
+  b.mem = nullptr;
+  b.bytes = 0;
+}
+
+static int integrate_batch_locked(int64_t count, const pagani_batch_item* items, int64_t slot_cap_req,
+                                  const pagani_options& o, cudaStream_t st, pagani_batch_result* res,
+                                  double* ms_out) {
+  if (count <= 0 || !items || !res) return fail(PAGANI_ERR_ARGUMENT, "empty batch or null pointer");
+  if (count > (1 << 24)) return fail(PAGANI_ERR_ARGUMENT, "batch too large");
+  if (o.it_max < 1 || o.it_max > kTraceCap) return fail(PAGANI_ERR_ARGUMENT, "it_max out of range");
+  int64_t slot_cap = ((slot_cap_req + 1) / 2) * 2;
+  // group the instances by (family, n)
+  std::map<int, std::vector<int64_t>> by_group;
+  for (int64_t i = 0; i < count; ++i) {
+    const pagani_batch_item& it = items[i];
+    if (it.dim < PAGANI_MIN_DIM || it.dim > PAGANI_MAX_DIM) return fail(PAGANI_ERR_DIM, "item dim must be in [2, 8]");
+    if (it.integrand_id < 0 || it.integrand_id >= kNumFamilies) return fail(PAGANI_ERR_INTEGRAND, "unknown integrand_id");
+    if (!(it.epsrel > 0.0) || !(it.epsabs >= 0.0)) return fail(PAGANI_ERR_TOLERANCE, "bad item tolerance");
+    int rc = check_params(it.integrand_id, it.dim, it.params);
+    if (rc) return rc;
+    int64_t s0 = 1;
+    for (int j = 0; j < it.dim; ++j) s0 *= default_init_div(it.dim);
+    if (s0 > slot_cap) return fail(PAGANI_ERR_CAPACITY, "max_regions_per_item below an item's initial split");
+    by_group[it.integrand_id * 16 + it.dim].push_back(i);
+  }
+  std::vector<BatchGroup> groups;
+  std::vector<int64_t> order;  // instance position -> item index
+  size_t bytes = 0;
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  bytes += align(sizeof(BatchInst) * count) + align(sizeof(IntegrandParams) * count) + 256 * 4;
+  for (auto& kv : by_group) {
+    BatchGroup g;
+    std::memset(&g, 0, sizeof(g));
+    g.family = kv.first / 16;
+    g.n = kv.first % 16;
+    g.first = (int32_t)order.size();
+    g.count = (int32_t)kv.second.size();
+    g.slot_cap = slot_cap;
+    const size_t slots = (size_t)g.count * slot_cap;
+    bytes += align(sizeof(double) * 2 * g.n * slots) + align((size_t)2 * g.n * slots) + 2 * align(8 * slots) +
+             align(slots) + align(4 * slots + 8);
+    for (int64_t i : kv.second) order.push_back(i);
+    groups.push_back(g);
+  }
+  bytes += align(sizeof(BatchGroup) * groups.size());
+  BatchWorkspace& bw = g_bws;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (bw.dev != dev || bw.bytes < bytes) {
+    release_batch(bw);
+    e = cudaMalloc(&bw.mem, bytes);
+    if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("batch workspace: ") + cudaGetErrorString(e));
+    bw.bytes = bytes;
+    bw.dev = dev;
+  }
+  // carve the workspace
+  unsigned char* p = static_cast<unsigned char*>(bw.mem);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    unsigned char* q = p + off;
+    off += align(b);
+    return q;
+  };
+  BatchArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.inst = reinterpret_cast<BatchInst*>(take(sizeof(BatchInst) * count));
+  IntegrandParams* prm_d = reinterpret_cast<IntegrandParams*>(take(sizeof(IntegrandParams) * count));
+  a.prm = prm_d;
+  a.tickets = reinterpret_cast<unsigned int*>(take(256));
+  a.flags = reinterpret_cast<int32_t*>(take(256));
+  take(512);
+  for (auto& g : groups) {
+    const size_t slots = (size_t)g.count * slot_cap;
+    g.lower = reinterpret_cast<double*>(take(sizeof(double) * 2 * g.n * slots));
+    g.level = take((size_t)2 * g.n * slots);
+    g.V = reinterpret_cast<double*>(take(8 * slots));
+    g.E = reinterpret_cast<double*>(take(8 * slots));
+    g.K = take(slots);
+    g.Vp = reinterpret_cast<double*>(take(4 * slots + 8));
+  }
+  BatchGroup* groups_d = reinterpret_cast<BatchGroup*>(take(sizeof(BatchGroup) * groups.size()));
+  a.groups = groups_d;
+  a.n_inst = (int)count;
+  // host images of the instance blocks and parameters
+  std::vector<BatchInst> hi(count);
+  std::vector<IntegrandParams> hp(count);
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const BatchGroup& g = groups[gi];
+    for (int k = 0; k < g.count; ++k) {
+      const int64_t pos = g.first + k;
+      const pagani_batch_item& it = items[order[pos]];
+      BatchInst& I = hi[pos];
+      std::memset(&I, 0, sizeof(I));
+      I.family = g.family;
+      I.n = g.n;
+      I.group = (int32_t)gi;
+      I.local = k;
+      const int d0 = default_init_div(g.n);
+      int l0 = 0;
+      while ((1 << l0) < d0) ++l0;
+      int64_t s0 = 1;
+      for (int j = 0; j < g.n; ++j) s0 *= d0;
+      Ctrl& c = I.c;
+      c.tau_rel = it.epsrel;
+      c.tau_abs = it.epsabs;
+      c.max_regions = slot_cap;
+      c.it_max = o.it_max;
+      c.relerr_filter = it.relerr_filter ? 1 : 0;
+      c.heuristic_filter = o.heuristic_filter ? 1 : 0;
+      c.s = s0;
+      c.it = 1;
+      c.status = -100;
+      c.l0 = l0;
+      hp[pos] = to_params(g.family, g.n, it.params);
+    }
+  }
+#define PG_CK(x)                                                                            \
+  do {                                                                                      \
+    e = (x);                                                                                \
+    if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e)); \
+  } while (0)
+  PG_CK(cudaMemcpyAsync(a.inst, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st));
+  PG_CK(cudaMemcpyAsync(prm_d, hp.data(), sizeof(IntegrandParams) * count, cudaMemcpyHostToDevice, st));
+  PG_CK(cudaMemcpyAsync(groups_d, groups.data(), sizeof(BatchGroup) * groups.size(), cudaMemcpyHostToDevice, st));
+  PG_CK(cudaMemsetAsync(a.tickets, 0, 256, st));
+  PG_CK(cudaMemsetAsync(a.flags, 0, 256, st));
+  const int inst_grid = (int)std::min<int64_t>(count, (int64_t)sms * 8);
+  k_batch_uniform<<<inst_grid, kBatchThreads, 0, st>>>(a);
+  PG_CK(cudaGetLastError());
+  std::vector<EvalRule> rules(groups.size());
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const RuleTable* rt = get_rule(groups[gi].n);
+    if (!rt) return fail(PAGANI_ERR_CUDA, "rule construction failed");
+    rules[gi] = to_eval_rule(*rt);
+  }
+  // autotune each group's Evaluate grid on this batch's first iteration
+  std::vector<int> egrid(groups.size());
+  cudaEvent_t ev0, ev1;
+  PG_CK(cudaEventCreate(&ev0));
+  PG_CK(cudaEventCreate(&ev1));
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const BatchGroup& g = groups[gi];
+    const FamilyKernels& fk = family_kernels(g.family);
+    const int key = g.family * 16 + g.n;
+    auto hit = g_batch_grid.find(key);
+    if (hit != g_batch_grid.end()) {
+      egrid[gi] = hit->second;
+      continue;
+    }
+    const size_t smem = (size_t)fk.table_bytes_per_thread[g.n] * fk.threads;
+    int occ = 0;
+    PG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fk.batch_eval_fn[g.n], fk.threads, smem));
+    if (occ < 1) return fail(PAGANI_ERR_CUDA, "batched evaluate kernel does not fit");
+    float best = 1e30f;
+    int best_grid = sms * occ;
+    for (int k = 1; k <= occ; ++k) {
+      const int grid = sms * k;
+      for (int rep = 0; rep < 2; ++rep) {
+        PG_CK(cudaEventRecord(ev0, st));
+        PG_CK(fk.batch_eval[g.n](rules[gi], a, g, grid, st));
+        PG_CK(cudaEventRecord(ev1, st));
+        PG_CK(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        PG_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+        if (rep == 1 && ms < best) {
+          best = ms;
+          best_grid = grid;
+        }
+      }
+    }
+    g_batch_grid[key] = best_grid;
+    egrid[gi] = best_grid;
+  }
+  PG_CK(cudaEventRecord(ev0, st));
+  if (o.use_graph) {
+    std::vector<int64_t> key = {count, slot_cap};
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      key.push_back(groups[gi].family * 16 + groups[gi].n);
+      key.push_back(groups[gi].count);
+      key.push_back(egrid[gi]);
+    }
+    key.push_back((int64_t)(uintptr_t)bw.mem);
+    if (!bw.exec || bw.key != key) {
+      if (bw.exec) cudaGraphExecDestroy(bw.exec);
+      if (bw.graph) cudaGraphDestroy(bw.graph);
+      bw.exec = nullptr;
+      bw.graph = nullptr;
+      cudaGraph_t gph = nullptr;
+      PG_CK(cudaGraphCreate(&gph, 0));
+      cudaGraphConditionalHandle hm, hpr;
+      cudaGraphNode_t wmain, wprobe, nred, nprobe, nsplit;
+      cudaGraph_t body = nullptr, pbody = nullptr;
+      PG_CK(cudaGraphConditionalHandleCreate(&hm, gph, 1, cudaGraphCondAssignDefault));
+      PG_CK(add_while(&wmain, gph, nullptr, 0, hm, &body));
+      PG_CK(cudaGraphConditionalHandleCreate(&hpr, body, 0, 0));
+      BatchArgs ga = a;
+      ga.use_graph = 1;
+      ga.h_main = hm;
+      ga.h_probe = hpr;
+      std::vector<cudaGraphNode_t> evals(groups.size());
+      std::vector<void*> gargs(3 * groups.size());
+      std::vector<BatchGroup> gcopy = groups;
+      for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const FamilyKernels& fk = family_kernels(groups[gi].family);
+        gargs[3 * gi] = &rules[gi];
+        gargs[3 * gi + 1] = &ga;
+        gargs[3 * gi + 2] = &gcopy[gi];
+        PG_CK(add_kernel(&evals[gi], body, nullptr, 0, fk.batch_eval_fn[groups[gi].n], egrid[gi], fk.threads,
+                         (size_t)fk.table_bytes_per_thread[groups[gi].n] * fk.threads, &gargs[3 * gi]));
+      }
+      void* margs[1] = {&ga};
+      PG_CK(add_kernel(&nred, body, evals.data(), evals.size(), (const void*)&k_batch_reduce, inst_grid,
+                       kBatchThreads, 0, margs));
+      PG_CK(add_while(&wprobe, body, &nred, 1, hpr, &pbody));
+      PG_CK(add_kernel(&nprobe, pbody, nullptr, 0, (const void*)&k_batch_probe, inst_grid, kBatchThreads, 0, margs));
+      PG_CK(add_kernel(&nsplit, body, &wprobe, 1, (const void*)&k_batch_split, inst_grid, kBatchThreads, 0, margs));
+      PG_CK(cudaGraphInstantiate(&bw.exec, gph, 0));
+      bw.graph = gph;
+      bw.key = key;
+    }
+    PG_CK(cudaGraphLaunch(bw.exec, st));
+  } else {
+    int32_t fl[4];
+    for (int guard = 0; guard < o.it_max + 2; ++guard) {
+      for (size_t gi = 0; gi < groups.size(); ++gi)
+        PG_CK(family_kernels(groups[gi].family).batch_eval[groups[gi].n](rules[gi], a, groups[gi], egrid[gi], st));
+      k_batch_reduce<<<inst_grid, kBatchThreads, 0, st>>>(a);
+      PG_CK(cudaGetLastError());
+      PG_CK(cudaMemcpyAsync(fl, a.flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+      PG_CK(cudaStreamSynchronize(st));
+      for (int pr = 0; fl[2] && pr < 128; ++pr) {
+        k_batch_probe<<<inst_grid, kBatchThreads, 0, st>>>(a);
+        PG_CK(cudaGetLastError());
+        PG_CK(cudaMemcpyAsync(fl, a.flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+        PG_CK(cudaStreamSynchronize(st));
+      }
+      k_batch_split<<<inst_grid, kBatchThreads, 0, st>>>(a);
+      PG_CK(cudaGetLastError());
+      PG_CK(cudaMemcpyAsync(fl, a.flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+      PG_CK(cudaStreamSynchronize(st));
+      if (!fl[3]) break;
+    }
+  }
+  PG_CK(cudaEventRecord(ev1, st));
+  PG_CK(cudaMemcpyAsync(hi.data(), a.inst, sizeof(BatchInst) * count, cudaMemcpyDeviceToHost, st));
+  PG_CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  PG_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+#undef PG_CK
+  if (ms_out) *ms_out = ms;
+  int bad = 0;
+  for (int64_t pos = 0; pos < count; ++pos) {
+    const Ctrl& c = hi[pos].c;
+    pagani_batch_result& r = res[order[pos]];
+    r.estimate = c.estimate;
+    r.errorest = c.errorest;
+    r.status = c.done ? c.status : PAGANI_ERR_WATCHDOG;
+    r.iterations = c.it;
+    r.n_regions = c.n_regions_total;
+    if (c.watchdog) r.status = PAGANI_ERR_WATCHDOG;
+    if (!c.done || c.watchdog) bad = 1;
+  }
+  if (bad) g_err = "some batch items ended without a result (see their status)";
+  return 0;
+}
+
 }  // namespace pg
 
 // =================================================================== C ABI
@@ -1199,6 +1716,26 @@ int pagani_integrate_noalloc(int dim, int integrand_id, const double* params, do
   }
 }
 
+int pagani_integrate_batch(int64_t count, const pagani_batch_item* items, int64_t max_regions_per_item,
+                           const pagani_options* opt, void* cuda_stream, pagani_batch_result* results,
+                           double* device_ms) {
+  pagani_options o;
+  pagani_default_options(&o);
+  if (opt) o = *opt;
+  std::lock_guard<std::mutex> lk(g_mu);
+  try {
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : nullptr;
+    if (!st) {
+      int rc = ensure_workspace(4096, 2);
+      if (rc) return rc;
+      st = g_ws.own_stream;
+    }
+    return integrate_batch_locked(count, items, max_regions_per_item, o, st, results, device_ms);
+  } catch (...) {
+    return fail(PAGANI_ERR_CUDA, "internal error");
+  }
+}
+
 int pagani_workspace_reserve(int64_t max_regions, int dim) {
   if (dim < PAGANI_MIN_DIM || dim > PAGANI_MAX_DIM) return fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
   if (max_regions < 1) return fail(PAGANI_ERR_ARGUMENT, "max_regions must be positive");
@@ -1209,6 +1746,7 @@ int pagani_workspace_reserve(int64_t max_regions, int dim) {
 int pagani_workspace_release(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   release_ws(g_ws);
+  release_batch(g_bws);
   return 0;
 }
 

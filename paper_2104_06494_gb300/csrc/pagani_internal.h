@@ -215,6 +215,38 @@ struct StandaloneArgs {
   const IntegrandParams* prm;
 };
 
+// ------------------------------------------------------------------ batch
+// One instance of a batch: its loop state (the single-integral control
+// block, reused) and where its regions live.  Instances of one (family, n)
+// group share a pool; instance k of the group owns regions
+// [k * slot_cap, (k + 1) * slot_cap).
+struct BatchInst {
+  Ctrl c;
+  int32_t family, n, group, local;
+};
+
+struct BatchGroup {
+  int32_t family, n, first, count;   // instances [first, first + count)
+  int64_t slot_cap;
+  double* lower;    // [2][n][count * slot_cap]
+  uint8_t* level;   // [2][n][count * slot_cap]
+  double* V;
+  double* E;
+  uint8_t* K;
+  double* Vp;       // [count * slot_cap / 2]
+};
+
+struct BatchArgs {
+  BatchInst* inst;
+  const IntegrandParams* prm;   // per instance
+  const BatchGroup* groups;     // device copy
+  int n_inst;
+  unsigned int* tickets;        // [0] reduce, [1] probe, [2] split
+  int32_t* flags;               // [0] any searching, [1] any running
+  int use_graph;
+  cudaGraphConditionalHandle h_main, h_probe;
+};
+
 // Launchers implemented per family (eval_<family>.cu).
 typedef cudaError_t (*LoopEvalLauncher)(const EvalRule&, const LoopArgs&, int grid, int block, size_t smem,
                                         cudaStream_t);
@@ -229,6 +261,9 @@ struct FamilyKernels {
   StandaloneLauncher standalone_diag[kMaxDim + 1];
   const void* loop_fn[kMaxDim + 1];        // kernel symbols (for occupancy queries / graph nodes)
   GradLauncher grad[kMaxDim + 1];          // gradient over a box list (positive product families)
+  cudaError_t (*batch_eval[kMaxDim + 1])(const EvalRule&, const BatchArgs&, const BatchGroup&, int grid,
+                                         cudaStream_t);
+  const void* batch_eval_fn[kMaxDim + 1];
   int threads;                             // block size
   int table_bytes_per_thread[kMaxDim + 1];
 };

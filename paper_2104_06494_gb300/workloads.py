@@ -121,3 +121,20 @@ def random_dyadic_regions(n: int, m: int, seed: int, max_level: int = 12):
         lower.append(lo)
         width.append(wd)
     return lower, width
+
+
+def batch_workloads(count: int = 4096, seed: int = BASE_SEED + 100) -> list[Workload]:
+    """Independent integrals for the batched form: dimension uniform in
+    {3..8}, family uniform over the five families, epsrel uniform in
+    {1e-4, 1e-6, 1e-8}, parameters from each family's ranges with a per-item
+    seed (seed + 1 + index).  Rel-err filtering is off for the oscillatory
+    family (sign-changing)."""
+    rng = SplitMix64(seed)
+    out = []
+    for i in range(count):
+        dim = 3 + int(rng.uniform(0, 6))
+        fam = int(rng.uniform(0, 5))
+        tau = (1e-4, 1e-6, 1e-8)[int(rng.uniform(0, 3))]
+        out.append(Workload(f"batch_{i}", fam, dim, tau, draw_params(fam, dim, seed + 1 + i), 0,
+                            relerr_filter=0 if fam == OSCILLATORY else 1))
+    return out

@@ -1,0 +1,71 @@
+"""GPU batched integration (the batching row of the build): every item of a
+mixed batch (dimension 3..8, five families, epsrel 1e-4..1e-8, own region
+pool) gives the result of the single-integral path with the same pool size
+and of the oracle; the graph and host-driven loops agree bitwise; the full
+4096-item workload runs in one launch and reproduces the single-integral
+path on a random sample of its items."""
+import numpy as np
+import pytest
+
+from oracle import capi as oracle, closed_forms as cf
+from paper_2104_06494_gb300.workloads import batch_workloads
+from tests.conftest import has_gpu
+
+pytestmark = pytest.mark.gpu
+
+SLOT = 8192
+
+
+@pytest.fixture(scope="module")
+def pg():
+    if not has_gpu():
+        pytest.skip("no CUDA device")
+    import paper_2104_06494_gb300 as m
+    m.load()
+    return m
+
+
+def same(a, b, what):
+    assert a["status"] == b.status, (what, a, b.status)
+    assert a["iterations"] == b.iterations and a["n_regions"] == b.n_regions, (what, a, b)
+    scale = abs(b.estimate)
+    assert abs(a["estimate"] - b.estimate) <= 1e-12 * scale + 1e-300, (what, a["estimate"], b.estimate)
+    assert abs(a["errorest"] - b.errorest) <= 1e-6 * abs(b.errorest) + 1e-12 * scale, (what, a["errorest"], b.errorest)
+
+
+def test_batch_items_match_single_integrals(pg):
+    items = batch_workloads(96, seed=7)
+    res, ms = pg.pagani_integrate_batch(items, SLOT)
+    assert ms > 0
+    for w, r in zip(items, res):
+        g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, SLOT, relerr_filter=w.relerr_filter)
+        same(r, g, (w.family, w.dim, w.epsrel))
+
+
+def test_batch_items_match_oracle(pg):
+    items = [w for w in batch_workloads(40, seed=11) if w.dim <= 5][:12]
+    res, _ = pg.pagani_integrate_batch(items, SLOT)
+    for w, r in zip(items, res):
+        o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, SLOT, relerr_filter=w.relerr_filter)
+        same(r, o, (w.family, w.dim, w.epsrel))
+
+
+def test_batch_graph_and_host_loop_identical(pg):
+    items = batch_workloads(64, seed=3)
+    a, _ = pg.pagani_integrate_batch(items, SLOT, use_graph=1)
+    b, _ = pg.pagani_integrate_batch(items, SLOT, use_graph=0)
+    assert a.tobytes() == b.tobytes()
+
+
+def test_batch_full_workload(pg):
+    """4096 items in one launch; a random sample of 200 items reproduces the
+    single-integral path item by item."""
+    items = batch_workloads()
+    res, ms = pg.pagani_integrate_batch(items, 16384)
+    assert len(res) == 4096 and np.all((res["status"] >= 0) & (res["status"] <= 3))
+    assert np.all(np.isfinite(res["estimate"]))
+    rng = np.random.default_rng(4096)
+    for i in rng.choice(4096, size=200, replace=False):
+        w = items[i]
+        g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, 16384, relerr_filter=w.relerr_filter)
+        same(res[i], g, (i, w.family, w.dim, w.epsrel))
