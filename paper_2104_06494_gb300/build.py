@@ -40,7 +40,7 @@ def _headers():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or os.environ.get("PAGANI_EXTRA_NVCC_FLAGS"):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _sources() + _headers() + [os.path.abspath(__file__)])
@@ -51,7 +51,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
         return LIB
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + (extra_flags or [])
+    # PAGANI_EXTRA_NVCC_FLAGS: extra nvcc flags for tuning builds (e.g. -DPAGANI_EVAL_MINB=3)
+    env_flags = os.environ.get("PAGANI_EXTRA_NVCC_FLAGS", "").split()
+    flags = NVCC_FLAGS + env_flags + (extra_flags or [])
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT, os.path.basename(src) + ".o")

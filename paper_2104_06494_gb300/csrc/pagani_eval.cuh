@@ -18,6 +18,13 @@
 
 #include "pagani_device.cuh"
 
+// Minimum resident blocks per SM requested for the Evaluate kernels (a
+// register budget: 1 lets them use up to 255 registers, 3 caps them near
+// 168 for 12 warps per SM).  Set at build time with -DPAGANI_EVAL_MINB=k.
+#ifndef PAGANI_EVAL_MINB
+#define PAGANI_EVAL_MINB 1
+#endif
+
 namespace pg {
 
 // ------------------------------------------------------------------ families
@@ -27,6 +34,8 @@ namespace pg {
 
 struct RealProduct {
   typedef double T;
+  // S + f(point) where f(point) = a b: one FMA
+  __device__ static __forceinline__ double acc(double S, T a, T b) { return fma(a, b, S); }
   static constexpr bool kUnitBounded = false;  // positive values: |S_g| = sum |f|
   static constexpr bool kHasGrad = true;        // f = prod_j phi_j(x_j; p0_j, p1_j), phi > 0
   __device__ static __forceinline__ T mul(T a, T b) { return a * b; }
@@ -113,6 +122,7 @@ struct Oscillatory {  // cos(2 pi u + sum_j a_j x_j) = Re[e^{2 pi i u} prod_j e^
     return r;
   }
   __device__ static __forceinline__ double last(T a, T b) { return fma(a.x, b.x, -(a.y * b.y)); }
+  __device__ static __forceinline__ double acc(double S, T a, T b) { return fma(a.x, b.x, fma(-a.y, b.y, S)); }
   __device__ static __forceinline__ double val(T a) { return a.x; }
   __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
     Ax a;
@@ -152,6 +162,7 @@ struct CornerPeak {  // (1 + sum_j a_j x_j)^-(N+1): per-axis terms add up
     return y;
   }
   __device__ static __forceinline__ double last(T a, T b) { return outer(a + b); }
+  __device__ static __forceinline__ double acc(double S, T a, T b) { return S + outer(a + b); }
   __device__ static __forceinline__ double val(T a) { return outer(a); }
   __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
     Ax a;
@@ -237,15 +248,16 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     T Q = (j == N - 1) ? pre[N - 1] : F::mul(pre[j], suf[j + 1]);
-    double p1 = F::last(Q, PG_TB(kR1P, j)), m1 = F::last(Q, PG_TB(kR1M, j));
+    // the l2 and lp points also enter the fourth difference, so they are
+    // formed individually; the l1 and l3 points go straight into their sums
     double p2 = F::last(Q, PG_TB(kR2P, j)), m2 = F::last(Q, PG_TB(kR2M, j));
-    double p3 = F::last(Q, PG_TB(kR3P, j)), m3 = F::last(Q, PG_TB(kR3M, j));
     double pp = F::last(Q, PG_TB(kRpP, j)), mp = F::last(Q, PG_TB(kRpM, j));
-    S[kGenL1] += p1 + m1;
-    S[kGenL2] += p2 + m2;
-    S[kGenL3] += p3 + m3;
-    S[kGenLp] += pp + mp;
-    D[j] = fabs((pp + mp - 2.0 * f0) - q * (p2 + m2 - 2.0 * f0));
+    S[kGenL1] = F::acc(F::acc(S[kGenL1], Q, PG_TB(kR1P, j)), Q, PG_TB(kR1M, j));
+    S[kGenL3] = F::acc(F::acc(S[kGenL3], Q, PG_TB(kR3P, j)), Q, PG_TB(kR3M, j));
+    const double s2 = p2 + m2, sp = pp + mp;
+    S[kGenL2] += s2;
+    S[kGenLp] += sp;
+    D[j] = fabs((sp - 2.0 * f0) - q * (s2 - 2.0 * f0));
   }
 
   // axis pairs j < k: Q_jk = pre[j] * prod_{j<m<k} T0_m * suf[k+1]
@@ -260,9 +272,21 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
       T a2p = F::mul(Q, PG_TB(kR2P, j)), a2m = F::mul(Q, PG_TB(kR2M, j));
       const T b1p = PG_TB(kR1P, k), b1m = PG_TB(kR1M, k);
       const T b2p = PG_TB(kR2P, k), b2m = PG_TB(kR2M, k);
-      S[kGenL1L1] += F::last(a1p, b1p) + F::last(a1p, b1m) + F::last(a1m, b1p) + F::last(a1m, b1m);
-      S[kGenL1L2] += F::last(a1p, b2p) + F::last(a1p, b2m) + F::last(a1m, b2p) + F::last(a1m, b2m) +
-                     F::last(a2p, b1p) + F::last(a2p, b1m) + F::last(a2m, b1p) + F::last(a2m, b1m);
+      double s5 = S[kGenL1L1], s6 = S[kGenL1L2];
+      s5 = F::acc(s5, a1p, b1p);
+      s5 = F::acc(s5, a1p, b1m);
+      s5 = F::acc(s5, a1m, b1p);
+      s5 = F::acc(s5, a1m, b1m);
+      s6 = F::acc(s6, a1p, b2p);
+      s6 = F::acc(s6, a1p, b2m);
+      s6 = F::acc(s6, a1m, b2p);
+      s6 = F::acc(s6, a1m, b2m);
+      s6 = F::acc(s6, a2p, b1p);
+      s6 = F::acc(s6, a2p, b1m);
+      s6 = F::acc(s6, a2m, b1p);
+      s6 = F::acc(s6, a2m, b1m);
+      S[kGenL1L1] = s5;
+      S[kGenL1L2] = s6;
     }
   }
 
@@ -298,7 +322,7 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
 #pragma unroll
           for (int s4 = 0; s4 < 4; ++s4) {
             T B = c_id ? ajk[s4] : F::mul(ajk[s4], C);
-            S[kGenL1L1L1] += F::last(B, tp) + F::last(B, tm);
+            S[kGenL1L1L1] = F::acc(F::acc(S[kGenL1L1L1], B, tp), B, tm);
           }
         }
       }
@@ -328,7 +352,7 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
 #pragma unroll
       for (int t = 0; t < H1; ++t) Av = F::mul(Av, ((s1 >> t) & 1) ? PG_TB(kR0M, t) : PG_TB(kR0P, t));
 #pragma unroll
-      for (int s2 = 0; s2 < (1 << H2); ++s2) acc += F::last(Av, Bv[s2]);
+      for (int s2 = 0; s2 < (1 << H2); ++s2) acc = F::acc(acc, Av, Bv[s2]);
     }
     S[kGenL0All] = acc;
   }
@@ -342,24 +366,33 @@ template <int N, bool UNIT>
 __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double (&S)[kNumGen], const double (&D)[N],
                                                 double vol, const double (&width)[N], double& V, double& E, int& K,
                                                 double* nk_out) {
-  double b = 0.0, u[4] = {0.0, 0.0, 0.0, 0.0}, sc[4] = {0.0, 0.0, 0.0, 0.0};
+  double b = 0.0, u[4] = {0.0, 0.0, 0.0, 0.0}, msum = 0.0;
 #pragma unroll
   for (int g = 0; g < kNumGen; ++g) {
     b = fma(R.w[g][0], S[g], b);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      u[k] = fma(R.w[g][1 + k], S[g], u[k]);
-      sc[k] = fma(fabs(R.w[g][1 + k]), UNIT ? R.cnt[g] : fabs(S[g]), sc[k]);
-    }
+    for (int k = 0; k < 4; ++k) u[k] = fma(R.w[g][1 + k], S[g], u[k]);
+    if (!UNIT) msum += fabs(S[g]);
   }
   V = vol * b;
-  // null values at the rounding level of their own sums count as zero
+  // null values at the rounding level of their own sums count as zero: the
+  // floor is noise * vol * sum_g |u_kg| M_g; max_g |u_kg| * sum_g M_g bounds
+  // it from above, so the exact floor is formed only when the bound does not
+  // already clear N_k
   double nk[4], nu[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     nk[k] = vol * fabs(u[k]);
-    const double floor_k = R.noise * (vol * sc[k]);
-    nu[k] = nk[k] <= floor_k ? 0.0 : nk[k];
+    const double bound = UNIT ? R.floor_unit[k] : R.umax[k] * msum;
+    double floor_k = 0.0;
+    const bool need = nk[k] <= R.noise * (vol * bound);
+    if (need || nk_out) {
+      double sc = 0.0;
+#pragma unroll
+      for (int g = 0; g < kNumGen; ++g) sc = fma(fabs(R.w[g][1 + k]), UNIT ? R.cnt[g] : fabs(S[g]), sc);
+      floor_k = R.noise * (vol * sc);
+    }
+    nu[k] = (need && nk[k] <= floor_k) ? 0.0 : nk[k];
     if (nk_out) {
       nk_out[k] = nk[k];
       nk_out[4 + k] = floor_k;
@@ -387,7 +420,7 @@ __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double 
 // ------------------------------------------------------------- loop kernel
 // One thread per sibling pair (2p, 2p+1) of the current pool buffer.
 template <class F, int N, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_evaluate_loop(const EvalRule R, const LoopArgs A) {
+__global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(const EvalRule R, const LoopArgs A) {
   typedef typename F::T T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw) + threadIdx.x;

@@ -603,6 +603,14 @@ static EvalRule to_eval_rule(const RuleTable& t) {
   r.q = t.q;
   r.noise = 64.0 * (double)t.num_points * 0x1p-53;
   for (int g = 0; g < kNumGen; ++g) r.cnt[g] = (double)t.count[g];
+  for (int k = 0; k < 4; ++k) {
+    r.umax[k] = 0.0;
+    r.floor_unit[k] = 0.0;
+    for (int g = 0; g < kNumGen; ++g) {
+      r.umax[k] = std::fmax(r.umax[k], std::fabs(t.w[g][1 + k]));
+      r.floor_unit[k] = std::fma(std::fabs(t.w[g][1 + k]), (double)t.count[g], r.floor_unit[k]);
+    }
+  }
   for (int g = 0; g < kNumGen; ++g)
     for (int k = 0; k < 5; ++k) r.w[g][k] = t.w[g][k];
   return r;

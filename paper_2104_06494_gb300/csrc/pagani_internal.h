@@ -147,6 +147,8 @@ struct EvalRule {
   double noise;  // 64 N(n) u: null values below noise * vol * sum_g |u_kg| M_g count as zero
   double w[kNumGen][5];
   double cnt[kNumGen];  // orbit sizes
+  double umax[4];       // max_g |u_kg| (upper bound of the floor's weights)
+  double floor_unit[4]; // sum_g |u_kg| cnt_g (the unit-bounded family's floor scale)
 };
 
 // Region pool: SoA, two buffers (ping-pong).  lower[b][j][cap] doubles,

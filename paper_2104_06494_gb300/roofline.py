@@ -82,6 +82,17 @@ def region_points_work(family: int, n: int) -> Counter:
         c["flops"] += k
         c["inst"] += k
 
+    def acc(k=1):         # S += f(point) formed from its last two factors
+        if cplx:          # 2 FMA
+            c["flops"] += 4 * k
+            c["inst"] += 2 * k
+        elif corner:      # S + outer(a + b)
+            add(2 * k)
+            outer(k)
+        else:             # 1 FMA
+            c["flops"] += 2 * k
+            c["inst"] += k
+
     # prefix and suffix partial products
     mul(n - 1 if base_identity else n)
     mul(max(n - 2, 0))
@@ -91,10 +102,11 @@ def region_points_work(family: int, n: int) -> Counter:
     for j in range(n):
         if j < n - 1:
             mul()
-        last(8)
-        add(8)
-        c["flops"] += 8   # (p + m - 2 f0) - q (p' + m' - 2 f0): 3 FMA + 2 ADD
-        c["inst"] += 5
+        acc(4)            # the l1 and l3 points
+        last(4)           # the l2 and lp points (also used by D_j)
+        add(4)            # their pair sums and the two generator sums
+        c["flops"] += 6   # (sp - 2 f0) - q (s2 - 2 f0): 3 FMA
+        c["inst"] += 3
     # axis pairs
     for j in range(n - 1):
         for k in range(j + 1, n):
@@ -103,8 +115,7 @@ def region_points_work(family: int, n: int) -> Counter:
             if k < n - 1:
                 mul()
             mul(4)
-            last(12)
-            add(12)
+            acc(12)
     # axis triples
     for j in range(n - 2):
         for k in range(j + 1, n - 1):
@@ -126,8 +137,7 @@ def region_points_work(family: int, n: int) -> Counter:
                 for _ in range(4):
                     if not c_id:
                         mul()
-                    last(2)
-                    add(2)
+                    acc(2)
     # vertices: half tables
     h1 = n // 2
     h2 = n - h1
@@ -135,17 +145,18 @@ def region_points_work(family: int, n: int) -> Counter:
         mul(2 * (1 << t))
     for _ in range(1 << h1):
         mul(h1 - 1 if base_identity else h1)
-        last(1 << h2)
-        add(1 << h2)
+        acc(1 << h2)
     return c
 
 
 def region_epilogue_work() -> Counter:
-    """Weighting (9 generators x (basic + 4 null + 4 floor scales) FMA), the
-    volume products, the noise floors, the error formula and the axis."""
+    """Weighting (9 generators x (basic + 4 null rules) FMA), the magnitude
+    sum bounding the noise floors, the volume products, the floor tests (the
+    exact floor only where the bound does not clear N_k), the error formula
+    and the split axis."""
     c = Counter()
-    c["flops"] += 2 * 81 + 1 + 4 + 8 + 4 + 1
-    c["inst"] += 81 + 1 + 4 + 8 + 4 + 1
+    c["flops"] += 2 * 45 + 9 + 1 + 4 + 8 + 1
+    c["inst"] += 45 + 9 + 1 + 4 + 8 + 1
     c["div"] += 2
     return c
 
