@@ -34,18 +34,24 @@
 extern "C" {
 #endif
 
-/* Integrand families (the synthetic Genz families of Sec. 4.1).  params layout
- * (float64, n = dim):
+/* Integrand families (the Genz families and the box-integral family of the
+ * test integrands f1..f8, Sec. 4.1).  params layout (float64, n = dim):
  *   PRODUCT_PEAK  f = prod_j 1/(c_j^-2 + (x_j - w_j)^2)   params = c[n], w[n]
  *   GAUSSIAN      f = exp(-sum_j a_j^2 (x_j - w_j)^2)     params = a[n], w[n]
  *   OSCILLATORY   f = cos(2 pi u + sum_j a_j x_j)         params = u, a[n]
  *   CORNER_PEAK   f = (1 + sum_j a_j x_j)^-(n+1)          params = a[n]
- *   C0            f = exp(-sum_j a_j |x_j - w_j|)         params = a[n], w[n]   */
+ *   C0            f = exp(-sum_j a_j |x_j - w_j|)         params = a[n], w[n]
+ *   DISCONTINUOUS f = exp(sum_j a_j x_j) if every x_j < w_j, else 0
+ *                                                         params = a[n], w[n]
+ *   BOX_POWER     f = (sum_j x_j^2)^q                     params = q (q >= 0)
+ * Parameters must be finite; PRODUCT_PEAK needs c_j != 0.                     */
 #define PAGANI_PRODUCT_PEAK 0
 #define PAGANI_GAUSSIAN 1
 #define PAGANI_OSCILLATORY 2
 #define PAGANI_CORNER_PEAK 3
 #define PAGANI_C0 4
+#define PAGANI_DISCONTINUOUS 5
+#define PAGANI_BOX_POWER 6
 
 #define PAGANI_MIN_DIM 2
 #define PAGANI_MAX_DIM 8

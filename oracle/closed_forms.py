@@ -19,6 +19,11 @@ the family is a product:
   evaluated in exact rational arithmetic (the alternating sum cancels heavily)
 * C0            exp(-sum_j a_j |x_j - w_j|):
       prod_j (2 - exp(-a_j w_j) - exp(-a_j (1 - w_j))) / a_j
+* discontinuous exp(sum_j a_j x_j) if every x_j < w_j, else 0 (paper f6):
+      prod_j (exp(a_j min(w_j, 1)) - 1) / a_j
+* box power     (sum_j x_j^2)^q (paper f7, f8): for integer q the multinomial
+      expansion sum_{k_1+..+k_n=q} q!/prod k_j! prod 1/(2 k_j + 1), exact
+      rationals; no closed form for other q (None)
 
 Pinned in tests/test_oracle_closed_forms.py against tensor Gauss-Legendre
 quadrature (split at the kink for C0) in low dimension.
@@ -30,7 +35,7 @@ import itertools
 import math
 from fractions import Fraction
 
-PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0 = 0, 1, 2, 3, 4
+PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0, DISCONTINUOUS, BOX_POWER = 0, 1, 2, 3, 4, 5, 6
 
 
 def closed_form(family: int, n: int, params) -> float:
@@ -58,7 +63,36 @@ def closed_form(family: int, n: int, params) -> float:
     if family == C0:
         a, w = p[:n], p[n:2 * n]
         return math.prod((2 - math.exp(-aj * wj) - math.exp(-aj * (1 - wj))) / aj for aj, wj in zip(a, w))
+    if family == DISCONTINUOUS:
+        a, w = p[:n], p[n:2 * n]
+        out = 1.0
+        for aj, wj in zip(a, w):
+            hi = min(max(wj, 0.0), 1.0)
+            out *= math.expm1(aj * hi) / aj
+        return out
+    if family == BOX_POWER:
+        q = p[0]
+        if q != int(q) or q < 0:
+            return None
+        q = int(q)
+        tot = Fraction(0)
+        for ks in _compositions(q, n):
+            term = Fraction(math.factorial(q))
+            for k in ks:
+                term /= math.factorial(k) * (2 * k + 1)
+            tot += term
+        return float(tot)
     raise ValueError(f"unknown family {family}")
+
+
+def _compositions(total: int, parts: int):
+    """All (k_1..k_parts) of non-negative integers summing to total."""
+    if parts == 1:
+        yield (total,)
+        return
+    for first in range(total + 1):
+        for rest in _compositions(total - first, parts - 1):
+            yield (first,) + rest
 
 
 def gaussian_gradient(n: int, params):

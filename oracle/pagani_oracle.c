@@ -26,7 +26,9 @@
  *  - Split axis (Sec. 2.2, Sec. 3.2): fourth divided difference per axis,
  *    D_j = |(f(c+a h_j e_j) + f(c-a h_j e_j) - 2 f(c))
  *           - q (f(c+b h_j e_j) + f(c-b h_j e_j) - 2 f(c))|, q = a^2/b^2,
- *    K = smallest j with D_j >= (1 - 1e-10) max D; widest axis if max D = 0.
+ *    a D_j no larger than 2^12 u M_j (M_j the same sum over |f|) is rounding
+ *    noise and counts as zero; K = smallest j with D_j >= (1 - 1e-10) max D;
+ *    if every D_j counts as zero, the widest axis (smallest j among equals).
  *  - Two-level error (Sec. 2.1, Sec. 3.2): for siblings L, R of parent P,
  *    delta = |V_L + V_R - V_P| / 4, S = E_L + E_R; if S > 0 each child's error
  *    becomes E (1 + 2 delta / S) + delta, else E + delta.
@@ -63,6 +65,8 @@ enum {
   FAM_OSCILLATORY = 2,
   FAM_CORNER_PEAK = 3,
   FAM_C0 = 4,
+  FAM_DISCONTINUOUS = 5,
+  FAM_BOX_POWER = 6,
   FAM_MONOMIAL = 100 /* test-only: prod_j x_j^(p_j), integer p_j */
 };
 
@@ -125,6 +129,15 @@ static double integrand(int fam, int n, const double *p, const double *x) {
   case FAM_C0: /* exp(-sum_j a_j |x_j - w_j|); p = a[n], w[n] */
     for (j = 0; j < n; ++j) s += p[j] * fabs(x[j] - p[n + j]);
     return exp(-s);
+  case FAM_DISCONTINUOUS: /* exp(sum_j a_j x_j) if every x_j < w_j, else 0; p = a[n], w[n] */
+    for (j = 0; j < n; ++j) {
+      if (!(x[j] < p[n + j])) return 0.0;
+      s += p[j] * x[j];
+    }
+    return exp(s);
+  case FAM_BOX_POWER: /* (sum_j x_j^2)^q; p = q */
+    for (j = 0; j < n; ++j) s += x[j] * x[j];
+    return pow(s, p[0]);
   case FAM_MONOMIAL:
     for (j = 0; j < n; ++j) {
       int e, k = (int)p[j];
@@ -249,7 +262,7 @@ static void evaluate_region(const oracle_rule *R, int fam, const double *p,
   *E = null_rule_error(Nused);
 
   /* split axis from fourth divided differences */
-  double x[16], D[16], Dabs[16], f0, Dmax = 0.0;
+  double x[16], D[16], Dabs[16], Dused[16], f0, Dmax = 0.0;
   for (int j = 0; j < n; ++j) x[j] = c[j];
   f0 = integrand(fam, n, p, x);
   for (int j = 0; j < n; ++j) {
@@ -262,11 +275,16 @@ static void evaluate_region(const oracle_rule *R, int fam, const double *p,
     D[j] = fabs((fa_p + fa_m - 2.0 * f0) - R->q * (fb_p + fb_m - 2.0 * f0));
     Dabs[j] = fabs(fa_p) + fabs(fa_m) + 2.0 * fabs(f0) +
               R->q * (fabs(fb_p) + fabs(fb_m) + 2.0 * fabs(f0));
-    if (D[j] > Dmax) Dmax = D[j];
+    /* a difference within rounding noise of zero (2^12 unit roundoffs of
+     * the magnitude of its five values) tells nothing about the axis */
+    Dused[j] = D[j] <= 4096.0 * 0x1p-53 * Dabs[j] ? 0.0 : D[j];
+    if (Dused[j] > Dmax) Dmax = Dused[j];
   }
+  /* the largest difference, near-ties to the lowest axis; every difference
+   * at its noise floor: the widest axis, ties to the lowest */
   int k = 0;
   if (Dmax > 0.0) {
-    while (!(D[k] >= (1.0 - 1e-10) * Dmax)) ++k;
+    while (!(Dused[k] >= (1.0 - 1e-10) * Dmax)) ++k;
   } else {
     for (int j = 1; j < n; ++j)
       if (width[j] > width[k]) k = j;

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0 = 0, 1, 2, 3, 4
+PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0, DISCONTINUOUS, BOX_POWER = 0, 1, 2, 3, 4, 5, 6
 STATUS_NAMES = {0: "converged", 1: "it_max", 2: "memory exhausted", 3: "tolerance unreachable",
                 -1: "bad dim", -2: "bad integrand", -3: "bad tolerance", -4: "cuda error", -5: "watchdog",
                 -6: "non-finite integrand", -7: "capacity below initial split", -8: "bad argument"}

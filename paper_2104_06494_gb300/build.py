@@ -18,7 +18,7 @@ LIB = os.path.join(OUT, "libpagani_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(HERE, "..", "include")]
 CU_SOURCES = ["pagani_host.cu", "eval_product_peak.cu", "eval_gaussian.cu", "eval_oscillatory.cu",
-              "eval_corner_peak.cu", "eval_c0.cu"]
+              "eval_corner_peak.cu", "eval_c0.cu", "eval_discontinuous.cu", "eval_box_power.cu"]
 CPP_SOURCES = ["pagani_rule.cpp"]
 
 

@@ -173,6 +173,63 @@ struct CornerPeak {  // (1 + sum_j a_j x_j)^-(N+1): per-axis terms add up
   __device__ static __forceinline__ T factor(const Ax& a, double x) { return a.a * x; }
 };
 
+struct Discontinuous : RealProduct {  // prod_j exp(a_j x_j) [x_j < w_j] (Genz discontinuous)
+  static constexpr int kFamily = kFamDiscontinuous;
+  static constexpr bool kHasGrad = false;  // not differentiable in w
+  struct Ax { double a, w; };
+  __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
+    Ax a;
+    a.a = p.p0[j];
+    a.w = p.p1[j];
+    return a;
+  }
+  __device__ static __forceinline__ T base(const IntegrandParams&) { return 1.0; }
+  __device__ static __forceinline__ T factor(const Ax& a, double x) { return x < a.w ? exp(a.a * x) : 0.0; }
+  __device__ static __forceinline__ void dlog(const IntegrandParams&, int, double, double, double& d0, double& d1) {
+    d0 = d1 = 0.0;
+  }
+};
+
+// (sum_j x_j^2)^p, p >= 0: per-axis terms x_j^2 add up.  The element type
+// carries the exponent next to the partial sum, so the point formulas see it.
+struct BoxPower {
+  static constexpr int kFamily = kFamBoxPower;
+  static constexpr bool kUnitBounded = false;
+  static constexpr bool kHasGrad = false;
+  typedef double2 T;  // (partial sum, exponent)
+  struct Ax { double p; };
+  // out of line: inlined into every unrolled rule point its loop, square root
+  // and pow would multiply the kernel's code
+  __device__ static __noinline__ double outer(double s, double p) {
+    const double q = 2.0 * p;
+    if (q == rint(q) && p < 64.0) {  // integer or half-integer power
+      int k = (int)p;
+      double r = 1.0, b = s;
+      while (k > 0) {
+        if (k & 1) r *= b;
+        b *= b;
+        k >>= 1;
+      }
+      return (q - 2.0 * (double)(int)p) != 0.0 ? r * sqrt(s) : r;
+    }
+    return pow(s, p);
+  }
+  __device__ static __forceinline__ T mul(T a, T b) { return make_double2(a.x + b.x, a.y); }
+  __device__ static __forceinline__ double last(T a, T b) { return outer(a.x + b.x, a.y); }
+  __device__ static __forceinline__ double acc(double S, T a, T b) { return S + outer(a.x + b.x, a.y); }
+  __device__ static __forceinline__ double val(T a) { return outer(a.x, a.y); }
+  __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int) {
+    Ax a;
+    a.p = p.u;
+    return a;
+  }
+  __device__ static __forceinline__ T base(const IntegrandParams& p) { return make_double2(0.0, p.u); }
+  __device__ static __forceinline__ T factor(const Ax& a, double x) { return make_double2(x * x, a.p); }
+  __device__ static __forceinline__ void dlog(const IntegrandParams&, int, double, double, double& d0, double& d1) {
+    d0 = d1 = 0.0;
+  }
+};
+
 // Offset g of a coordinate code on [-1, 1] (radius order: l1, l2, l3, lp, l0).
 __device__ __forceinline__ double code_offset(const EvalRule& R, int code) {
   if (code == kC0) return 0.0;
@@ -257,7 +314,15 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
     const double s2 = p2 + m2, sp = pp + mp;
     S[kGenL2] += s2;
     S[kGenLp] += sp;
-    D[j] = fabs((sp - 2.0 * f0) - q * (s2 - 2.0 * f0));
+    // a difference within rounding noise of zero (2^12 u of the magnitude
+    // of its five values) says nothing about the axis: its sign bit marks it
+    // for region_epilogue, which then skips it
+    const double dj = fabs((sp - 2.0 * f0) - q * (s2 - 2.0 * f0));
+    // (for the positive families the values are their own magnitudes)
+    const double mj = F::kUnitBounded
+                          ? (fabs(pp) + fabs(mp)) + q * (fabs(p2) + fabs(m2)) + (2.0 + 2.0 * q) * fabs(f0)
+                          : fma(2.0 + 2.0 * q, fabs(f0), fma(q, fabs(s2), fabs(sp)));
+    D[j] = fma(-kDiffNoise, mj, dj) > 0.0 ? dj : -dj;
   }
 
   // axis pairs j < k: Q_jk = pre[j] * prod_{j<m<k} T0_m * suf[k+1]
@@ -399,6 +464,9 @@ __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double 
     }
   }
   E = null_error(nu[0], nu[1], nu[2], nu[3]);
+  // split axis: the largest fourth difference above its noise floor (floored
+  // ones carry a negative sign), near-ties to the lowest axis; with every
+  // difference at the floor, the widest axis
   double dmax = 0.0;
 #pragma unroll
   for (int j = 0; j < N; ++j) dmax = fmax(dmax, D[j]);
@@ -616,7 +684,7 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule 
 #pragma unroll
         for (int t = 0; t < 8; ++t) A.diag[(size_t)t * m + i] = nk[t];
 #pragma unroll
-        for (int j = 0; j < N; ++j) A.diag[(size_t)(8 + j) * m + i] = D[j];
+        for (int j = 0; j < N; ++j) A.diag[(size_t)(8 + j) * m + i] = fabs(D[j]);
       }
     }
   }

@@ -457,6 +457,8 @@ static const FamilyKernels& family_kernels(int fam) {
     case kFamGaussian: return kernels_gaussian();
     case kFamOscillatory: return kernels_oscillatory();
     case kFamCornerPeak: return kernels_corner_peak();
+    case kFamDiscontinuous: return kernels_discontinuous();
+    case kFamBoxPower: return kernels_box_power();
     default: return kernels_c0();
   }
 }
@@ -616,13 +618,23 @@ static EvalRule to_eval_rule(const RuleTable& t) {
   return r;
 }
 
+static int param_count(int fam, int n) {
+  switch (fam) {
+    case kFamOscillatory: return n + 1;
+    case kFamCornerPeak: return n;
+    case kFamBoxPower: return 1;
+    default: return 2 * n;
+  }
+}
+
 static int check_params(int fam, int n, const double* p) {
-  const int np = fam == kFamOscillatory ? n + 1 : (fam == kFamCornerPeak ? n : 2 * n);
+  const int np = param_count(fam, n);
   for (int i = 0; i < np; ++i)
     if (!std::isfinite(p[i])) return fail(PAGANI_ERR_INTEGRAND, "non-finite integrand parameter");
   if (fam == kFamProductPeak)
     for (int j = 0; j < n; ++j)
       if (p[j] == 0.0) return fail(PAGANI_ERR_INTEGRAND, "product peak needs c_j != 0");
+  if (fam == kFamBoxPower && p[0] < 0.0) return fail(PAGANI_ERR_INTEGRAND, "box power needs q >= 0");
   return 0;
 }
 
@@ -632,6 +644,8 @@ static IntegrandParams to_params(int fam, int n, const double* p) {
   if (fam == kFamOscillatory) {
     q.u = p[0];
     for (int j = 0; j < n; ++j) q.p0[j] = p[1 + j];
+  } else if (fam == kFamBoxPower) {
+    q.u = p[0];
   } else if (fam == kFamCornerPeak) {
     for (int j = 0; j < n; ++j) q.p0[j] = p[j];
   } else {

@@ -11,6 +11,11 @@ constexpr int kMaxDim = 8;
 constexpr int kNumGen = 9;
 constexpr int kCodes = 11;  // coordinate codes per axis (see below)
 
+// Noise level of a fourth difference relative to the magnitude sum of its
+// five integrand values: at or below it the difference counts as zero in the
+// split-axis choice (2^12 unit roundoffs).
+constexpr double kDiffNoise = 0x1p-41;
+
 // Per-axis factor cache: the 11 factor values of every dyadic interval
 // [k 2^-l, (k+1) 2^-l) of levels l <= kCacheLevels, per axis, slot 2^l - 1 + k.
 constexpr int kCacheLevels = 11;
@@ -60,14 +65,16 @@ enum Family {
   kFamOscillatory = 2,
   kFamCornerPeak = 3,
   kFamC0 = 4,
-  kNumFamilies = 5
+  kFamDiscontinuous = 5,
+  kFamBoxPower = 6,
+  kNumFamilies = 7
 };
 
 // Integrand parameters as the kernels read them (device buffer, one per call).
 struct IntegrandParams {
-  double p0[kMaxDim];   // c (product peak), a (Gaussian, corner peak, C0, oscillatory)
-  double p1[kMaxDim];   // w (product peak, Gaussian, C0)
-  double u;             // oscillatory phase parameter
+  double p0[kMaxDim];   // c (product peak), a (Gaussian, corner peak, C0, oscillatory, discontinuous)
+  double p1[kMaxDim];   // w (product peak, Gaussian, C0, discontinuous)
+  double u;             // oscillatory phase parameter; box-power exponent
 };
 
 // Neumaier pair used for compensated sums.
@@ -275,6 +282,8 @@ const FamilyKernels& kernels_gaussian();
 const FamilyKernels& kernels_oscillatory();
 const FamilyKernels& kernels_corner_peak();
 const FamilyKernels& kernels_c0();
+const FamilyKernels& kernels_discontinuous();
+const FamilyKernels& kernels_box_power();
 
 constexpr int kSplitThreads = 256;
 constexpr int kItemsPerThread = 8;

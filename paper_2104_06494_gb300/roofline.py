@@ -12,21 +12,22 @@ sibling pair (one thread):
   separate kernel, counted by `cache_fill_work`;
 * per region: prefix/suffix partial products, the one-axis, pair, triple and
   vertex orbits (one product or sum per point from shared partials), the
-  nine generator sums, the fourth differences, rule and null-rule weighting,
+  nine generator sums, the fourth differences and their noise floors, rule
+  and null-rule weighting,
   the noise floors, the error formula and the split axis;
 * per pair: the two-level refinement; per region: the compensated partial
   sums and Rel-Err-Classify.
 
 flops count an FMA as 2 and every other add/mul as 1; `inst` counts FP64
 arithmetic instructions (an FMA is one).  Library calls (exp, sincos,
-division: CUDA's own implementations) are counted separately and never
-converted into flops.
+division, sqrt, pow: CUDA's own implementations) are counted separately and
+never converted into flops.
 """
 from __future__ import annotations
 
 from collections import Counter
 
-PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0 = 0, 1, 2, 3, 4
+PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0, DISCONTINUOUS, BOX_POWER = 0, 1, 2, 3, 4, 5, 6
 
 
 def num_points(n: int) -> int:
@@ -47,12 +48,33 @@ def _pow_mults(e: int) -> int:
     return mults
 
 
-def region_points_work(family: int, n: int) -> Counter:
-    """FP64 work of the rule sums of one region (rule_sums in the kernel)."""
+def _box_power_outer(q: float) -> Counter:
+    """(s)^q as the box-power kernel forms it: binary powering for integer
+    and half-integer q (one multiply per bit and per set bit, plus a square
+    root and a multiply for the half), a library pow otherwise."""
+    c = Counter()
+    if 2 * q == int(2 * q) and q < 64:
+        k = int(q)
+        c["flops"] += k.bit_length() + bin(k).count("1")
+        c["inst"] += k.bit_length() + bin(k).count("1")
+        if 2 * q != 2 * k:
+            c["sqrt"] += 1
+            c["flops"] += 1
+            c["inst"] += 1
+    else:
+        c["pow"] += 1
+    return c
+
+
+def region_points_work(family: int, n: int, q: float = 11.0) -> Counter:
+    """FP64 work of the rule sums of one region (rule_sums in the kernel);
+    q is the box-power exponent."""
     c = Counter()
     cplx = family == OSCILLATORY
     corner = family == CORNER_PEAK
-    base_identity = family in (PRODUCT_PEAK, GAUSSIAN, C0)
+    box = family == BOX_POWER
+    additive = corner or box
+    base_identity = family in (PRODUCT_PEAK, GAUSSIAN, C0, DISCONTINUOUS)
 
     def mul(k=1):
         if cplx:          # (a.x b.x - a.y b.y, a.x b.y + a.y b.x): 2 MUL + 2 FMA
@@ -62,7 +84,11 @@ def region_points_work(family: int, n: int) -> Counter:
             c["flops"] += k
             c["inst"] += k
 
-    def outer(k=1):       # corner peak: 1 / s, then r^(n+1)
+    def outer(k=1):       # corner peak: 1 / s, then r^(n+1); box power: s^q
+        if box:
+            for key, v in _box_power_outer(q).items():
+                c[key] += v * k
+            return
         c["div"] += k
         pm = _pow_mults(n + 1)
         c["flops"] += pm * k
@@ -75,7 +101,7 @@ def region_points_work(family: int, n: int) -> Counter:
         else:
             c["flops"] += k
             c["inst"] += k
-        if corner:
+        if additive:
             outer(k)
 
     def add(k=1):
@@ -86,7 +112,7 @@ def region_points_work(family: int, n: int) -> Counter:
         if cplx:          # 2 FMA
             c["flops"] += 4 * k
             c["inst"] += 2 * k
-        elif corner:      # S + outer(a + b)
+        elif additive:    # S + outer(a + b)
             add(2 * k)
             outer(k)
         else:             # 1 FMA
@@ -96,7 +122,7 @@ def region_points_work(family: int, n: int) -> Counter:
     # prefix and suffix partial products
     mul(n - 1 if base_identity else n)
     mul(max(n - 2, 0))
-    if corner:
+    if additive:
         outer(1)          # f at the centre
     # one-axis orbits and fourth differences
     for j in range(n):
@@ -107,6 +133,12 @@ def region_points_work(family: int, n: int) -> Counter:
         add(4)            # their pair sums and the two generator sums
         c["flops"] += 6   # (sp - 2 f0) - q (s2 - 2 f0): 3 FMA
         c["inst"] += 3
+        if cplx:          # its noise floor over |values|: 3 ADD, 2 FMA (|x| is free)
+            c["flops"] += 7
+            c["inst"] += 5
+        else:             # positive values: 3 FMA
+            c["flops"] += 6
+            c["inst"] += 3
     # axis pairs
     for j in range(n - 1):
         for k in range(j + 1, n):
@@ -191,6 +223,13 @@ def pair_table_work(family: int, n: int) -> Counter:
     elif family == CORNER_PEAK:
         c["flops"] += entries       # a x
         c["inst"] += entries
+    elif family == DISCONTINUOUS:
+        c["flops"] += entries       # a x (the x < w test is not FP64 arithmetic)
+        c["inst"] += entries
+        c["exp"] += entries
+    elif family == BOX_POWER:
+        c["flops"] += entries       # x x
+        c["inst"] += entries
     return c
 
 
@@ -202,14 +241,14 @@ def cache_fill_work(family: int, n: int, level: int) -> Counter:
     return Counter({k: v * n * (1 << level) for k, v in one_axis.items() if v})
 
 
-def pair_work(family: int, n: int, two_level: bool, cached: bool = True) -> Counter:
+def pair_work(family: int, n: int, two_level: bool, cached: bool = True, q: float = 11.0) -> Counter:
     c = Counter()
     if cached:
         c["cache_loads"] += 11 * (n + 1)
     else:
         c.update(pair_table_work(family, n))
     for _ in range(2):
-        c.update(region_points_work(family, n))
+        c.update(region_points_work(family, n, q))
         c.update(region_epilogue_work())
         c["flops"] += 9             # two compensated adds and the rel-err test
         c["inst"] += 9
@@ -220,13 +259,13 @@ def pair_work(family: int, n: int, two_level: bool, cached: bool = True) -> Coun
     return c
 
 
-def evaluate_work(family: int, n: int, regions_per_iteration, cached: bool = True) -> Counter:
+def evaluate_work(family: int, n: int, regions_per_iteration, cached: bool = True, q: float = 11.0) -> Counter:
     """Total algorithmic work of the Evaluate launches of one integration,
     given the region count of every iteration (first iteration: no parents,
     no two-level refinement)."""
     tot = Counter()
     for it, s in enumerate(regions_per_iteration):
-        w = pair_work(family, n, two_level=it > 0, cached=cached)
+        w = pair_work(family, n, two_level=it > 0, cached=cached, q=q)
         for k, v in w.items():
             tot[k] += v * (int(s) // 2)
     return tot

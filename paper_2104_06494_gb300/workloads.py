@@ -17,14 +17,16 @@ Parameter layouts (all float64, dimension n):
   OSCILLATORY   cos(2 pi u + sum a_j x_j)          [u, a_0..a_{n-1}]
   CORNER_PEAK   (1 + sum a_j x_j)^-(n+1)           [a_0..a_{n-1}]
   C0            exp(-sum a_j |x_j - w_j|)          [a_0..a_{n-1}, w_0..w_{n-1}]
+  DISCONTINUOUS exp(sum a_j x_j) if all x_j < w_j    [a_0..a_{n-1}, w_0..w_{n-1}]
+  BOX_POWER     (sum x_j^2)^q                      [q]
 """
 from __future__ import annotations
 
 from dataclasses import dataclass, field
 
-PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0 = 0, 1, 2, 3, 4
+PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0, DISCONTINUOUS, BOX_POWER = 0, 1, 2, 3, 4, 5, 6
 FAMILY_NAMES = {PRODUCT_PEAK: "product_peak", GAUSSIAN: "gaussian", OSCILLATORY: "oscillatory",
-                CORNER_PEAK: "corner_peak", C0: "c0"}
+                CORNER_PEAK: "corner_peak", C0: "c0", DISCONTINUOUS: "discontinuous", BOX_POWER: "box_power"}
 BASE_SEED = 2104
 _MASK = (1 << 64) - 1
 
@@ -48,7 +50,8 @@ class SplitMix64:
 
 
 def param_count(family: int, n: int) -> int:
-    return {PRODUCT_PEAK: 2 * n, GAUSSIAN: 2 * n, OSCILLATORY: n + 1, CORNER_PEAK: n, C0: 2 * n}[family]
+    return {PRODUCT_PEAK: 2 * n, GAUSSIAN: 2 * n, OSCILLATORY: n + 1, CORNER_PEAK: n, C0: 2 * n,
+            DISCONTINUOUS: 2 * n, BOX_POWER: 1}[family]
 
 
 # default parameter ranges per family: list of (count_fn, lo, hi) in draw order
@@ -58,6 +61,8 @@ _RANGES = {
     OSCILLATORY: [("1", 0.0, 1.0), ("n", 1.0, 5.0)],
     CORNER_PEAK: [("n", 0.5, 2.0)],
     C0: [("n", 1.0, 5.0), ("n", 0.0, 1.0)],
+    DISCONTINUOUS: [("n", 1.0, 5.0), ("n", 0.2, 0.9)],
+    BOX_POWER: [("1", 1.0, 11.0)],
 }
 
 
@@ -137,4 +142,26 @@ def batch_workloads(count: int = 4096, seed: int = BASE_SEED + 100) -> list[Work
         tau = (1e-4, 1e-6, 1e-8)[int(rng.uniform(0, 3))]
         out.append(Workload(f"batch_{i}", fam, dim, tau, draw_params(fam, dim, seed + 1 + i), 0,
                             relerr_filter=0 if fam == OSCILLATORY else 1))
+    return out
+
+
+def paper_integrands() -> dict[str, Workload]:
+    """The paper's fixed-parameter test integrands (Sec. 4.1) on their
+    dimensions, mapped onto the families; epsrel and pool set per use."""
+    def w(name, fam, n, params, relerr=1):
+        return Workload(name, fam, n, 1e-3, params, 10_000_000, relerr_filter=relerr)
+    out = {
+        "f1_d8": w("f1_d8", OSCILLATORY, 8, [0.0] + [float(i) for i in range(1, 9)], relerr=0),
+        "f2_d6": w("f2_d6", PRODUCT_PEAK, 6, [50.0] * 6 + [0.5] * 6),
+        "f3_d3": w("f3_d3", CORNER_PEAK, 3, [1.0, 2.0, 3.0]),
+        "f3_d8": w("f3_d8", CORNER_PEAK, 8, [float(i) for i in range(1, 9)]),
+        "f4_d5": w("f4_d5", GAUSSIAN, 5, [25.0] * 5 + [0.5] * 5),
+        "f4_d8": w("f4_d8", GAUSSIAN, 8, [25.0] * 8 + [0.5] * 8),
+        "f5_d5": w("f5_d5", C0, 5, [10.0] * 5 + [0.5] * 5),
+        "f5_d8": w("f5_d8", C0, 8, [10.0] * 8 + [0.5] * 8),
+        "f6_d6": w("f6_d6", DISCONTINUOUS, 6, [float(i + 4) for i in range(1, 7)] +
+                   [(3 + i) / 10 for i in range(1, 7)]),
+        "f7_d8": w("f7_d8", BOX_POWER, 8, [11.0]),
+        "f8_d8": w("f8_d8", BOX_POWER, 8, [7.5]),
+    }
     return out

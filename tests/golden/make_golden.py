@@ -37,7 +37,12 @@ def paper_integrands():
     # f5 = exp(-10 sum |x_i - 1/2|), n = 5 and 8 (Eq. for f5): C0, a = 10, w = 1/2
     for n in (5, 8):
         cases.append((f"f5_d{n}", cf.C0, n, [10.0] * n + [0.5] * n))
-    out = {"_source": "paper Sec. 4.1 (test integrands f1..f5); values from oracle/closed_forms.py",
+    # f6 = exp(sum_i (i + 4) x_i) if x_i < (3 + i)/10, n = 6 (Eq. for f6): discontinuous family
+    cases.append(("f6", cf.DISCONTINUOUS, 6, [float(i + 4) for i in range(1, 7)] + [(3 + i) / 10 for i in range(1, 7)]))
+    # f7 = (sum x_i^2)^11, n = 8 (Eq. for f7): box power, exact rational
+    cases.append(("f7_d8", cf.BOX_POWER, 8, [11.0]))
+    out = {"_source": "paper Sec. 4.1 (test integrands f1..f7; f8 has no closed form); values from "
+                      "oracle/closed_forms.py",
            "cases": []}
     for name, fam, n, p in cases:
         out["cases"].append({"name": name, "family": fam, "dim": n, "params": p,

@@ -1,6 +1,6 @@
 """Helpers shared by the GPU parity tests: tolerances derived from the
-floating-point arithmetic, and the reference error formula applied to given
-null-rule values."""
+floating-point arithmetic, the reference error formula applied to given
+null-rule values, and the comparison of two integration runs."""
 import math
 
 import numpy as np
@@ -23,7 +23,14 @@ def value_condition(family, n, params, lo, wd):
                     error of its value)
       C0            k_rel = max sum a |x - w|
       corner peak   k_rel = 4 (n + 1) (a power of a sum of n terms)
-      oscillatory   k_abs = 2 pi |u| + sum |a| max |x| (the cosine argument)"""
+      oscillatory   k_abs = 2 pi |u| + sum |a| max |x| (the cosine argument)
+      discontinuous k_rel = 2n + 4 + max sum |a x| (the exponent)
+      box power     k_rel = q (n + 2 + 2 (1 + hi / x_min)) + 8: a point
+                    coordinate x = c + h g carries an absolute error of
+                    about eps hi, relative 1 + hi / x at its smallest x
+                    (the largest generator radius 0.956 leaves
+                    x_min >= lo + 0.022 w), squared, summed over n axes and
+                    raised to the power q"""
     lo = np.atleast_2d(lo)
     hi = lo + np.atleast_2d(wd)
     m = lo.shape[0]
@@ -40,6 +47,13 @@ def value_condition(family, n, params, lo, wd):
         k_rel = np.full(m, 4.0 * (n + 1))
     elif family == 2:
         k_abs = 2 * np.pi * abs(p[0]) + np.sum(np.abs(p[1:]) * np.maximum(np.abs(lo), np.abs(hi)), axis=1)
+    elif family == 5:
+        a = p[:n]
+        k_rel = 2.0 * n + 4 + np.sum(np.abs(a) * np.maximum(np.abs(lo), np.abs(hi)), axis=1)
+    elif family == 6:
+        q = abs(p[0])
+        xmin = lo + 0.022 * (hi - lo)
+        k_rel = q * (n + 2 + 2 * (1 + np.max(hi / xmin, axis=1))) + 8
     return k_rel, k_abs
 
 
@@ -86,3 +100,33 @@ def sibling_regions(n, m, seed, max_level=10):
         lo += [a, c]
         wd += [b, d]
     return np.array(lo[:m]), np.array(wd[:m])
+
+
+def close(a, b, rel=1e-12, floor=1e-300):
+    return abs(a - b) <= rel * max(abs(a), abs(b)) + floor
+
+
+def compare_runs(g, o, rel=1e-12):
+    """Equal region sets (statuses, iterations, per-iteration counts and
+    decisions), integral estimates within 1e-12 relative.  Error estimates are
+    sums of region errors computed from null-rule values, differences of
+    nearly equal sums known only to their rounding level; they are compared
+    to 1e-6 relative, or 1e-12 of the integral's magnitude where they are
+    themselves at that noise level."""
+    assert g.status == o.status, (g.status, o.status)
+    assert g.iterations == o.iterations
+    assert g.n_regions == o.n_regions
+    assert g.n_active_last == o.n_active_last
+    scale = max(abs(o.estimate), float(np.max(np.abs(o.trace["v"]) + np.abs(o.trace["vf"]))))
+    assert abs(g.estimate - o.estimate) <= rel * scale + 1e-300, (g.estimate, o.estimate)
+    efloor = 1e-12 * scale
+    assert close(g.errorest, o.errorest, rel=1e-6, floor=efloor), (g.errorest, o.errorest)
+    gt, ot = g.trace, o.trace
+    assert len(gt) == len(ot)
+    for a, b in zip(gt, ot):
+        for key in ("it", "trigger", "probes", "search_ok", "s", "n_relerr_active", "n_survivors"):
+            assert a[key] == b[key], (key, a, b)
+        assert abs(a["v"] - b["v"]) <= rel * scale
+        assert abs(a["vf"] - b["vf"]) <= rel * scale
+        assert close(a["e"], b["e"], rel=1e-6, floor=efloor), (a["e"], b["e"])
+        assert close(a["ef"], b["ef"], rel=1e-6, floor=efloor), (a["ef"], b["ef"])

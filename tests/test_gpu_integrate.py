@@ -9,6 +9,7 @@ import pytest
 from oracle import capi as oracle, closed_forms as cf
 from paper_2104_06494_gb300.workloads import config_workloads, draw_params
 from tests.conftest import has_gpu
+from tests.gpu_util import close, compare_runs
 
 pytestmark = pytest.mark.gpu
 
@@ -22,42 +23,13 @@ def pg():
     return m
 
 
-def close(a, b, rel=1e-12, floor=1e-300):
-    return abs(a - b) <= rel * max(abs(a), abs(b)) + floor
-
-
-def compare_runs(g, o, rel=1e-12):
-    """Equal region sets (statuses, iterations, per-iteration counts and
-    decisions), integral estimates within 1e-12 relative.  Error estimates are
-    sums of region errors computed from null-rule values, differences of
-    nearly equal sums known only to their rounding level; they are compared
-    to 1e-6 relative, or 1e-12 of the integral's magnitude where they are
-    themselves at that noise level."""
-    assert g.status == o.status, (g.status, o.status)
-    assert g.iterations == o.iterations
-    assert g.n_regions == o.n_regions
-    assert g.n_active_last == o.n_active_last
-    scale = max(abs(o.estimate), float(np.max(np.abs(o.trace["v"]) + np.abs(o.trace["vf"]))))
-    assert abs(g.estimate - o.estimate) <= rel * scale + 1e-300, (g.estimate, o.estimate)
-    efloor = 1e-12 * scale
-    assert close(g.errorest, o.errorest, rel=1e-6, floor=efloor), (g.errorest, o.errorest)
-    gt, ot = g.trace, o.trace
-    assert len(gt) == len(ot)
-    for a, b in zip(gt, ot):
-        for key in ("it", "trigger", "probes", "search_ok", "s", "n_relerr_active", "n_survivors"):
-            assert a[key] == b[key], (key, a, b)
-        assert abs(a["v"] - b["v"]) <= rel * scale
-        assert abs(a["vf"] - b["vf"]) <= rel * scale
-        assert close(a["e"], b["e"], rel=1e-6, floor=efloor), (a["e"], b["e"])
-        assert close(a["ef"], b["ef"], rel=1e-6, floor=efloor), (a["ef"], b["ef"])
-
-
 CASES = [
     (0, 2, 1e-6, 1), (0, 3, 1e-3, 1), (0, 4, 1e-6, 1),
     (1, 2, 1e-7, 1), (1, 3, 1e-5, 1), (1, 5, 1e-4, 1),
     (2, 2, 1e-8, 0), (2, 3, 1e-7, 0), (2, 6, 1e-6, 0),
     (3, 3, 1e-7, 1), (3, 5, 1e-6, 1), (3, 8, 1e-4, 1),
     (4, 2, 1e-5, 1), (4, 3, 1e-4, 1), (4, 8, 1e-3, 1),
+    (5, 4, 1e-3, 1), (6, 3, 1e-13, 1), (6, 5, 1e-10, 1), (6, 8, 1e-7, 1),
 ]
 
 
@@ -67,6 +39,26 @@ def test_loop_matches_oracle(pg, family, n, tau, relerr):
     o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, relerr_filter=relerr)
     g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=4_000_000, relerr_filter=relerr, trace=True)
     compare_runs(g, o)
+
+
+@pytest.mark.parametrize("n,tau", [(2, 1e-4), (3, 1e-3)])
+def test_discontinuous_without_heuristic_filter(pg, n, tau):
+    """The discontinuous family converges only with the heuristic filter off
+    (with it on, the finished error of the boxes cut by the jump exceeds the
+    tolerance and the loop stops with status 3, as the case above checks):
+    millions of regions, the pool grown and compacted over 14 to 26
+    iterations.  The null-rule estimate is not a bound across the jump: at
+    d = 3 it reports 8.7e-4 where the true error is 4.9e-3 (on both sides),
+    so containment is asserted for the d = 2 case only."""
+    family = 5
+    params = draw_params(family, n, 700 + 13 * family + n)
+    o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, heuristic_filter=0)
+    g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=4_000_000, heuristic_filter=0, trace=True)
+    assert o.status == 0
+    compare_runs(g, o)
+    if n == 2:
+        ex = cf.closed_form(family, n, params)
+        assert abs(g.estimate - ex) <= g.errorest
 
 
 def test_config_product_peak_d3_full_size(pg):

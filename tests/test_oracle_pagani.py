@@ -57,6 +57,24 @@ def test_split_axis_widest_when_flat():
     assert K[0] == 1
 
 
+def test_split_axis_ignores_differences_at_rounding_noise():
+    """f = x_0^4 on a box of half-width 2^-21 about 1/2: the exact D_0 =
+    2 a^2 h^4 |a^2 - b^2| is about 1e-27, far below the rounding noise of
+    its values (about 1e-17); f is constant along axes 1 and 2 (D = 0), so
+    the widest axis wins (1 over 2 on the tie), not the axis whose computed
+    difference is noise.  On a box where D_0 is resolvable, axis 0 wins
+    although it is the narrowest."""
+    lo = [[0.5, 0.5, 0.5]]
+    V, E, K, D = capi.evaluate(100, 3, [4, 0, 0], lo, [[2.0 ** -20, 2.0 ** -19, 2.0 ** -19]], diag=True)
+    assert D[0, 10] == 0.0 and D[0, 11] == 0.0
+    assert D[0, 9] <= 2.0 ** -41 * D[0, 12]
+    assert K[0] == 1
+    V, E, K, D = capi.evaluate(100, 3, [4, 0, 0], [[0.0, 0.0, 0.0]], [[0.5, 1.0, 1.0]], diag=True)
+    a2, b2, h = 1 / 16, float(rule.L2), 0.25
+    assert abs(D[0, 9] - 2 * a2 * h ** 4 * abs(a2 - b2)) < 1e-16
+    assert K[0] == 0
+
+
 def test_error_zero_for_linear():
     V, E, K = capi.evaluate(100, 4, [1, 0, 0, 0], [[0.1, 0.2, 0.3, 0.4]], [[0.5, 0.25, 0.125, 0.5]])
     # all four null rules annihilate degree 1: only rounding noise (~10 N(d) eps) remains
