@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form report")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form and filtering-ablation reports")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle time budget per integral")
     ap.add_argument("--quiet", action="store_true")
     return ap.parse_args()
@@ -203,6 +203,32 @@ def differentiation_report(pg, torch, flush, reps: int = 3):
             "grad_max_err_vs_closed_form": float(np.max(np.abs(g - np.array(gc)) / scale)),
             "grad_err_scale": "|I| for d/da, a_j |I| for d/dw",
             "backward_evals_per_s": r.n_leaves * npoints(n) / (bwd_ms * 1e-3)}
+
+
+def filtering_report(pg, torch, flush, max_regions: int = 1 << 27):
+    """The filtering ablation of Sec. 4.2 on the paper's own case, f4 in 8-D
+    at three digits: Threshold-Classify with both triggers (the default), the
+    memory trigger only, the unchanged-digits trigger only, and off."""
+    from oracle import closed_forms as cf
+    from paper_2104_06494_gb300.workloads import paper_integrands
+    w = paper_integrands()["f4_d8"]
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {"workload": "f4_d8 (Gaussian, a_j = 25, w_j = 1/2)", "epsrel": 1e-3, "max_regions": max_regions}
+    for mode, name in ((1, "both_triggers"), (2, "memory_trigger_only"), (3, "digits_trigger_only"), (0, "off")):
+        pg.pagani_integrate_ex(w.dim, w.family, w.params, 1e-3, max_regions=max_regions, heuristic_filter=mode,
+                               stream=stream)            # warm-up: graph, workspace
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = pg.pagani_integrate_ex(w.dim, w.family, w.params, 1e-3, max_regions=max_regions,
+                                   heuristic_filter=mode, stream=stream)
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = {"ms": a.elapsed_time(b), "status": r.status, "iterations": r.iterations,
+                     "regions": r.n_regions, "true_relerr": abs(r.estimate - ex) / abs(ex),
+                     "errorest_rel": r.errorest / abs(r.estimate)}
+    return out
 
 
 def batching_report(pg, torch, flush, slot: int = 16384):
@@ -439,6 +465,7 @@ def main():
         line["differentiation"] = differentiation_report(pg, torch, flush)
         if not args.no_batch:
             line["batching"] = batching_report(pg, torch, flush)
+            line["filtering"] = filtering_report(pg, torch, flush)
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))

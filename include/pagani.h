@@ -93,7 +93,11 @@ typedef struct {
 
 typedef struct {
   int32_t relerr_filter;    /* 1 (default): Rel-Err-Classify on; 0 for sign-changing f (Sec. 3.5.1) */
-  int32_t heuristic_filter; /* 1 (default): Threshold-Classify on (Sec. 3.5.2-3.5.3)               */
+  int32_t heuristic_filter; /* Threshold-Classify (Sec. 3.5.2-3.5.3) and its triggers: 1 (default)
+                               both triggers, the estimate's digits unchanged and memory about to
+                               be exhausted; 2 the memory trigger only; 3 the digits trigger only;
+                               0 off (the filtering ablation of Sec. 4.2).  Other values:
+                               PAGANI_ERR_ARGUMENT                                                */
   int32_t init_div;         /* divisions per axis of the Uniform-Split; 0 = largest power of two
                                d >= 2 with d^dim <= 4096 (Sec. 3.1)                                 */
   int32_t it_max;           /* iteration limit (default 100)                                       */
@@ -126,6 +130,21 @@ int pagani_integrate(int dim, int integrand_id, const double* params, double eps
 int pagani_integrate_ex(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
                         int64_t max_regions, const pagani_options* opt, void* cuda_stream, pagani_result* out,
                         pagani_trace_record* trace, int trace_cap);
+
+/* As pagani_integrate_ex over the box [lower, upper] (host arrays of dim
+ * doubles; both NULL = the unit cube): Algorithm 2 takes the bounds a, b of
+ * the integration region (Sec. 3.1) and starts with the Uniform-Split of
+ * that box.  Regions are kept as dyadic sub-boxes of the unit cube and every
+ * rule point x is evaluated at lower + (upper - lower) x, so a region's
+ * volume is its unit-cube volume times prod (upper - lower); estimates,
+ * errors, trace sums and the finished/active volumes are in that measure
+ * (epsabs too).  Needs lower[j] < upper[j], both finite, and a finite
+ * non-zero product of the lengths, else PAGANI_ERR_ARGUMENT.  The leaf set
+ * kept with keep_leaves is in unit-cube coordinates of that map. */
+int pagani_integrate_box(int dim, int integrand_id, const double* params, const double* lower,
+                         const double* upper, double epsrel, double epsabs, int64_t max_regions,
+                         const pagani_options* opt, void* cuda_stream, pagani_result* out,
+                         pagani_trace_record* trace, int trace_cap);
 
 /* Allocation-free integration, for callers that cannot allocate device
  * memory: code that runs while a CUDA stream is being captured, applications

@@ -43,7 +43,8 @@ class _Rule(ctypes.Structure):
 
 class _Opt(ctypes.Structure):
     _fields_ = [("relerr_filter", ctypes.c_int), ("heuristic_filter", ctypes.c_int),
-                ("init_div", ctypes.c_int), ("it_max", ctypes.c_int)]
+                ("init_div", ctypes.c_int), ("it_max", ctypes.c_int),
+                ("lower", ctypes.c_void_p), ("upper", ctypes.c_void_p)]
 
 
 class _Res(ctypes.Structure):
@@ -134,10 +135,16 @@ class OracleResult:
 
 def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20, max_regions: int = 10 ** 6,
               relerr_filter: int = 1, heuristic_filter: int = 1, init_div: int = 0, it_max: int = 100,
-              want_regions: bool = False, want_leaves: bool = False) -> OracleResult:
+              want_regions: bool = False, want_leaves: bool = False, bounds=None) -> OracleResult:
+    """bounds: None for the unit cube, else (a, b), each of length n."""
     lib = _load()
     p = np.ascontiguousarray(params, dtype=np.float64)
-    opt = _Opt(relerr_filter, heuristic_filter, init_div, it_max)
+    opt = _Opt(relerr_filter, heuristic_filter, init_div, it_max, None, None)
+    if bounds is not None:
+        ba = np.ascontiguousarray(bounds[0], dtype=np.float64)
+        bb = np.ascontiguousarray(bounds[1], dtype=np.float64)
+        assert ba.shape == (n,) and bb.shape == (n,)
+        opt.lower, opt.upper = ba.ctypes.data, bb.ctypes.data
     res = _Res()
     trace = np.zeros(it_max, dtype=TRACE_DTYPE)
     fl = fw = None

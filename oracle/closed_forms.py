@@ -25,6 +25,8 @@ the family is a product:
       expansion sum_{k_1+..+k_n=q} q!/prod k_j! prod 1/(2 k_j + 1), exact
       rationals; no closed form for other q (None)
 
+closed_form_box gives the same integrals over a general box [lo, hi].
+
 Pinned in tests/test_oracle_closed_forms.py against tensor Gauss-Legendre
 quadrature (split at the kink for C0) in low dimension.
 """
@@ -80,6 +82,93 @@ def closed_form(family: int, n: int, params) -> float:
             term = Fraction(math.factorial(q))
             for k in ks:
                 term /= math.factorial(k) * (2 * k + 1)
+            tot += term
+        return float(tot)
+    raise ValueError(f"unknown family {family}")
+
+
+def closed_form_box(family: int, n: int, params, lo, hi) -> float:
+    """The integral over the box [lo, hi] (Algorithm 2's bounds a, b), one
+    1-D antiderivative per axis for the product families:
+      product peak  c [atan(c (hi - w)) - atan(c (lo - w))]
+      Gaussian      sqrt(pi)/(2 a) [erf(a (hi - w)) - erf(a (lo - w))] (via
+                    erfc when both ends lie on one side of w, against
+                    cancellation)
+      oscillatory   Re[exp(2 pi i u) prod (exp(i a hi) - exp(i a lo))/(i a)]
+      C0            the kink at w splits the axis into up to two exponentials
+      discontinuous (exp(a min(hi, w)) - exp(a lo))/a, or 0 when w <= lo
+    the corner peak as the signed vertex sum 1/(n! prod a) sum_v
+    (-1)^{#v_j = hi_j} / (1 + a.v) (n integrations of (1 + a.x)^-(k+1)), in
+    exact rationals; the integer box power as the multinomial sum of
+    prod (hi^(2k+1) - lo^(2k+1))/(2k+1), exact."""
+    p = [float(x) for x in params]
+    lo = [float(x) for x in lo]
+    hi = [float(x) for x in hi]
+    if family == PRODUCT_PEAK:
+        c, w = p[:n], p[n:2 * n]
+        return math.prod(cj * (math.atan(cj * (h - wj)) - math.atan(cj * (l - wj)))
+                         for cj, wj, l, h in zip(c, w, lo, hi))
+    if family == GAUSSIAN:
+        a, w = p[:n], p[n:2 * n]
+        out = 1.0
+        for aj, wj, l, h in zip(a, w, lo, hi):
+            x0, x1 = aj * (l - wj), aj * (h - wj)
+            if x0 >= 0:
+                d = math.erfc(x0) - math.erfc(x1)
+            elif x1 <= 0:
+                d = math.erfc(-x1) - math.erfc(-x0)
+            else:
+                d = math.erf(x1) - math.erf(x0)
+            out *= math.sqrt(math.pi) / (2 * aj) * d
+        return out
+    if family == OSCILLATORY:
+        u, a = p[0], p[1:1 + n]
+        z = cmath.exp(2j * math.pi * u)
+        for aj, l, h in zip(a, lo, hi):
+            z *= (cmath.exp(1j * aj * h) - cmath.exp(1j * aj * l)) / (1j * aj)
+        return z.real
+    if family == CORNER_PEAK:
+        a = [Fraction(x) for x in p[:n]]
+        L = [Fraction(x) for x in lo]
+        H = [Fraction(x) for x in hi]
+        tot = Fraction(0)
+        for v in itertools.product((0, 1), repeat=n):
+            pt = [H[j] if v[j] else L[j] for j in range(n)]
+            tot += Fraction((-1) ** sum(v)) / (1 + sum((a[j] * pt[j] for j in range(n)), Fraction(0)))
+        return float(tot / (math.factorial(n) * math.prod(a)))
+    if family == C0:
+        a, w = p[:n], p[n:2 * n]
+        out = 1.0
+        for aj, wj, l, h in zip(a, w, lo, hi):
+            if h <= wj:
+                f = (math.exp(-aj * (wj - h)) - math.exp(-aj * (wj - l))) / aj
+            elif l >= wj:
+                f = (math.exp(-aj * (l - wj)) - math.exp(-aj * (h - wj))) / aj
+            else:
+                f = (2 - math.exp(-aj * (wj - l)) - math.exp(-aj * (h - wj))) / aj
+            out *= f
+        return out
+    if family == DISCONTINUOUS:
+        a, w = p[:n], p[n:2 * n]
+        out = 1.0
+        for aj, wj, l, h in zip(a, w, lo, hi):
+            top = min(h, wj)
+            if top <= l:
+                return 0.0
+            out *= math.exp(aj * l) * math.expm1(aj * (top - l)) / aj
+        return out
+    if family == BOX_POWER:
+        q = p[0]
+        if q != int(q) or q < 0:
+            return None
+        q = int(q)
+        L = [Fraction(x) for x in lo]
+        H = [Fraction(x) for x in hi]
+        tot = Fraction(0)
+        for ks in _compositions(q, n):
+            term = Fraction(math.factorial(q))
+            for j, k in enumerate(ks):
+                term *= (H[j] ** (2 * k + 1) - L[j] ** (2 * k + 1)) / (math.factorial(k) * (2 * k + 1))
             tot += term
         return float(tot)
     raise ValueError(f"unknown family {family}")

@@ -81,9 +81,12 @@ typedef struct {
 
 typedef struct {
   int relerr_filter;     /* Sec. 3.5.1: 0 turns rel-err classification off */
-  int heuristic_filter;  /* Sec. 3.5.2: 0 turns Threshold-Classify off */
+  int heuristic_filter;  /* Sec. 3.5.2 triggers of Threshold-Classify: 1 both,
+                            2 memory only, 3 unchanged digits only, 0 off */
   int init_div;          /* 0 = default Uniform-Split divisions */
   int it_max;
+  const double *lower;   /* integration bounds a[n], b[n] of Algorithm 2;  */
+  const double *upper;   /* both NULL: the unit cube                        */
 } oracle_options;
 
 typedef struct {
@@ -417,15 +420,18 @@ int oracle_default_init_div(int n) {
   return d;
 }
 
-/* Region i of the d^n grid: axis n-1 varies fastest. */
-static void uniform_split(int n, int d, double *lower, double *width) {
+/* Region i of the d^n grid over [a, b] (a, b NULL: the unit cube): axis
+ * n-1 varies fastest. */
+static void uniform_split(int n, int d, const double *a, const double *b, double *lower,
+                          double *width) {
   int64_t s = 1;
   for (int j = 0; j < n; ++j) s *= d;
   for (int64_t i = 0; i < s; ++i) {
     int64_t r = i;
     for (int j = n - 1; j >= 0; --j) {
-      lower[i * n + j] = (double)(r % d) / (double)d;
-      width[i * n + j] = 1.0 / (double)d;
+      double a_j = a ? a[j] : 0.0, len = a ? b[j] - a[j] : 1.0;
+      lower[i * n + j] = a_j + len * (double)(r % d) / (double)d;
+      width[i * n + j] = len / (double)d;
       r /= d;
     }
   }
@@ -456,6 +462,12 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
   for (int j = 0; j < n; ++j) s *= d;
   memset(res, 0, sizeof(*res));
   if (s > max_regions) { res->status = -7; return -7; }
+  if ((opt->lower == NULL) != (opt->upper == NULL)) { res->status = -8; return -8; }
+  for (int j = 0; opt->lower && j < n; ++j)
+    if (!(opt->upper[j] > opt->lower[j]) || !isfinite(opt->upper[j] - opt->lower[j])) {
+      res->status = -8;
+      return -8;
+    }
 
   int64_t cap = s > max_regions ? s : max_regions;
   double *H_lo = (double *)malloc(sizeof(double) * (size_t)cap * n);
@@ -470,7 +482,7 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
   nsum finvol = {0, 0};
   int status = 1, it;
 
-  uniform_split(n, d, H_lo, H_w);               /* H <- Uniform-Split(R_0, d) */
+  uniform_split(n, d, opt->lower, opt->upper, H_lo, H_w);   /* H <- Uniform-Split([a, b], d) */
   memset(A, 1, (size_t)s);                      /* A[1:s] <- 1 */
 
   for (it = 1; it <= opt->it_max; ++it) {
@@ -517,9 +529,11 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
     /* A <- Threshold-Classify(A, E, v + v_f, e + e_f, e, s) when triggered */
     double v_tot = v + vf;
     int trig = 0;
-    if (opt->heuristic_filter) {
-      if (it >= 2 && fabs(v_tot - v_tot_prev) <= tau_rel * fabs(v_tot)) trig |= 1;
-      if (2 * n_rel > max_regions) trig |= 2;
+    {
+      int digits = opt->heuristic_filter == 1 || opt->heuristic_filter == 3;
+      int memory = opt->heuristic_filter == 1 || opt->heuristic_filter == 2;
+      if (digits && it >= 2 && fabs(v_tot - v_tot_prev) <= tau_rel * fabs(v_tot)) trig |= 1;
+      if (memory && 2 * n_rel > max_regions) trig |= 2;
     }
     tr.trigger = trig;
     if (trig) {

@@ -67,7 +67,7 @@ TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.i
 EXPORTED = ["pagani_default_options", "pagani_integrate", "pagani_integrate_ex", "pagani_workspace_reserve",
             "pagani_workspace_release", "pagani_evaluate", "pagani_rule_tables", "pagani_fp64_peak",
             "pagani_last_error", "pagani_version", "pagani_integrate_noalloc", "pagani_leaves", "pagani_gradient",
-            "pagani_integrate_batch"]
+            "pagani_integrate_batch", "pagani_integrate_box"]
 
 _lib = None
 
@@ -92,6 +92,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                         ctypes.c_double, ctypes.c_int64, P(Options), ctypes.c_void_p, P(Result),
                                         ctypes.c_void_p, ctypes.c_int]
     lib.pagani_integrate_ex.restype = ctypes.c_int
+    lib.pagani_integrate_box.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
+                                         P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                         P(Options), ctypes.c_void_p, P(Result), ctypes.c_void_p, ctypes.c_int]
+    lib.pagani_integrate_box.restype = ctypes.c_int
     lib.pagani_integrate_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_double,
                                              ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, P(Result)]
     lib.pagani_integrate_noalloc.restype = ctypes.c_int
@@ -183,19 +187,30 @@ def pagani_integrate(dim: int, integrand_id: int, params, epsrel: float, epsabs:
 def pagani_integrate_ex(dim: int, integrand_id: int, params, epsrel: float, epsabs: float = 1e-20,
                         max_regions: int = 10_000_000, relerr_filter: int = 1, heuristic_filter: int = 1,
                         init_div: int = 0, it_max: int = 100, use_graph: int = 1, stream: int | None = None,
-                        trace: bool = False, raise_on_error: bool = True, keep_leaves: int = 0) -> Integration:
-    """C ABI pagani_integrate_ex; stream is a raw cudaStream_t (e.g.
+                        trace: bool = False, raise_on_error: bool = True, keep_leaves: int = 0,
+                        bounds=None) -> Integration:
+    """C ABI pagani_integrate_ex, or pagani_integrate_box when bounds = (a, b)
+    (each of length dim) is given; stream is a raw cudaStream_t (e.g.
     torch.cuda.current_stream().cuda_stream) or None for the library stream."""
     lib = load()
     p, pp = _params_array(params)
     o = Options(relerr_filter, heuristic_filter, init_div, it_max, use_graph, keep_leaves)
     r = Result()
     tr = np.zeros(it_max, dtype=TRACE_DTYPE) if trace else None
-    rc = lib.pagani_integrate_ex(dim, integrand_id, pp, epsrel, epsabs, max_regions, ctypes.byref(o),
-                                 ctypes.c_void_p(stream or 0), ctypes.byref(r),
-                                 tr.ctypes.data_as(ctypes.c_void_p) if trace else None, it_max if trace else 0)
+    tail = (ctypes.byref(o), ctypes.c_void_p(stream or 0), ctypes.byref(r),
+            tr.ctypes.data_as(ctypes.c_void_p) if trace else None, it_max if trace else 0)
+    if bounds is None:
+        name = "pagani_integrate_ex"
+        rc = lib.pagani_integrate_ex(dim, integrand_id, pp, epsrel, epsabs, max_regions, *tail)
+    else:
+        name = "pagani_integrate_box"
+        a, pa = _params_array(bounds[0])
+        b, pb = _params_array(bounds[1])
+        if a.shape != (dim,) or b.shape != (dim,):
+            raise ValueError("bounds must be two arrays of length dim")
+        rc = lib.pagani_integrate_box(dim, integrand_id, pp, pa, pb, epsrel, epsabs, max_regions, *tail)
     if rc < 0 and raise_on_error:
-        raise PaganiError(f"pagani_integrate_ex failed ({rc}): {last_error()}")
+        raise PaganiError(f"{name} failed ({rc}): {last_error()}")
     if trace:
         tr = tr[:max(min(r.iterations, it_max), 0)].copy()
     return _integration(r, tr)

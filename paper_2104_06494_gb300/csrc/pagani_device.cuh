@@ -210,10 +210,9 @@ __device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long 
   }
   double v_tot = v + c.vf;
   int trig = 0;
-  if (c.heuristic_filter) {
-    if (c.it >= 2 && fabs(v_tot - c.v_tot_prev) <= c.tau_rel * fabs(v_tot)) trig |= 1;
-    if (2 * n_rel > c.max_regions) trig |= 2;
-  }
+  // c.heuristic_filter is the mask of enabled triggers (bit 0 digits, bit 1 memory)
+  if ((c.heuristic_filter & 1) && c.it >= 2 && fabs(v_tot - c.v_tot_prev) <= c.tau_rel * fabs(v_tot)) trig |= 1;
+  if ((c.heuristic_filter & 2) && 2 * n_rel > c.max_regions) trig |= 2;
   c.v_tot_prev = v_tot;
   c.trigger = trig;
   tr.trigger = trig;

@@ -237,15 +237,22 @@ __device__ __forceinline__ double code_offset(const EvalRule& R, int code) {
   return (code & 1) ? r : -r;
 }
 
+// Coordinate on axis j of the rule point with offset g in the box of centre
+// c and half-width h (unit-cube coordinates), mapped onto the integration
+// bounds: lo_j + len_j (c + h g).  Every path (tables, cache, gradient) forms
+// it with this one expression; for the unit cube it is c + h g exactly.
+__device__ __forceinline__ double point_x(const IntegrandParams& p, int j, double c, double h, double g) {
+  return fma(p.len[j], fma(h, g, c), p.lo[j]);
+}
+
 // Build the 11 factor entries of one axis (centre c, half-width h).
 template <class F, int N, int THREADS>
-__device__ __forceinline__ void build_axis(typename F::T* tab, const EvalRule& R, const typename F::Ax& ax,
+__device__ __forceinline__ void build_axis(typename F::T* tab, const EvalRule& R, const IntegrandParams& prm,
                                            double c, double h, int j) {
+  const typename F::Ax ax = F::axis(prm, j);
 #pragma unroll
-  for (int code = 0; code < kCodes; ++code) {
-    double x = fma(h, code_offset(R, code), c);
-    tab[(code * N + j) * THREADS] = F::factor(ax, x);
-  }
+  for (int code = 0; code < kCodes; ++code)
+    tab[(code * N + j) * THREADS] = F::factor(ax, point_x(prm, j, c, h, code_offset(R, code)));
 }
 
 // k of a dyadic lower bound k 2^-level, from the IEEE fields (integer ops).
@@ -275,7 +282,7 @@ __device__ __forceinline__ void axis_entries(typename F::T* tab, const EvalRule&
     const typename F::Ax ax = F::axis(prm, j);
 #pragma unroll
     for (int code = 0; code < kCodes; ++code)
-      tab[(code * N + j) * THREADS] = F::factor(ax, fma(h, code_offset(R, code), lo + h));
+      tab[(code * N + j) * THREADS] = F::factor(ax, point_x(prm, j, lo + h, h, code_offset(R, code)));
   }
 }
 
@@ -524,8 +531,9 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
       const uchar2 lv2 = *reinterpret_cast<const uchar2*>(level + (size_t)j * cap + iL);
       loL[j] = lo2.x;
       loR[j] = lo2.y;
-      wL[j] = pow2_neg(lv2.x);
-      wR[j] = pow2_neg(lv2.y);
+      // widths on the integration bounds (they only break split-axis ties)
+      wL[j] = pow2_neg(lv2.x) * prm.len[j];
+      wR[j] = pow2_neg(lv2.y) * prm.len[j];
       lvLj[j] = lv2.x;
       lvL += lv2.x;
       lvR += lv2.y;
@@ -543,12 +551,12 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     double VL, EL, VR, ER;
     int KL, KR;
     rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
-    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL), wL, VL, EL, KL, nullptr);
+    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL) * prm.vol, wL, VL, EL, KL, nullptr);
     // patch the one axis where the right sibling differs
     if (diff_axis >= 0)
       axis_entries<F, N, THREADS>(tab, R, prm, fcache, A.fcache_levels, diff_lo, diff_lv, diff_axis);
     rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
-    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR), wR, VR, ER, KR, nullptr);
+    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR) * prm.vol, wR, VR, ER, KR, nullptr);
 
     if (it > 1) two_level(VL, VR, A.pool.Vp[p], EL, ER);
 
@@ -635,7 +643,7 @@ __global__ void __launch_bounds__(256) k_factor_cache(const EvalRule R, const Lo
     const int j = (int)(rest / count);
     const double lo = (double)k * w;
     cache[((size_t)j * kCacheSlots + (count - 1) + k) * kCodes + code] =
-        F::factor(F::axis(prm, j), fma(h, code_offset(R, code), lo + h));
+        F::factor(F::axis(prm, j), point_x(prm, j, lo + h, h, code_offset(R, code)));
   }
 }
 
@@ -670,7 +678,7 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule 
         if (side == 1) same = (lo[j] == A.lower[(size_t)j * m + i - 1]) && (w[j] == A.width[(size_t)j * m + i - 1]);
         if (!same) {
           const double h = 0.5 * w[j];
-          build_axis<F, N, THREADS>(tab, R, F::axis(prm, j), lo[j] + h, h, j);
+          build_axis<F, N, THREADS>(tab, R, prm, lo[j] + h, h, j);
         }
       }
       double S[kNumGen], D[N], V, E, nk[8];
@@ -724,8 +732,8 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_batch(const EvalRule R, co
       const double2 lo2 = *reinterpret_cast<const double2*>(lower + (size_t)j * slots + iL);
       const uchar2 lv2 = *reinterpret_cast<const uchar2*>(level + (size_t)j * slots + iL);
       loL[j] = lo2.x;
-      wL[j] = pow2_neg(lv2.x);
-      wR[j] = pow2_neg(lv2.y);
+      wL[j] = pow2_neg(lv2.x) * prm.len[j];
+      wR[j] = pow2_neg(lv2.y) * prm.len[j];
       lvLj[j] = lv2.x;
       lvL += lv2.x;
       lvR += lv2.y;
@@ -742,11 +750,11 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_batch(const EvalRule R, co
     double VL, EL, VR, ER;
     int KL, KR;
     rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
-    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL), wL, VL, EL, KL, nullptr);
+    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL) * prm.vol, wL, VL, EL, KL, nullptr);
     if (diff_axis >= 0)
       axis_entries<F, N, THREADS>(tab, R, prm, (const T*)nullptr, 0, diff_lo, diff_lv, diff_axis);
     rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
-    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR), wR, VR, ER, KR, nullptr);
+    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR) * prm.vol, wR, VR, ER, KR, nullptr);
     if (it > 1) two_level(VL, VR, G.Vp[p], EL, ER);
     *reinterpret_cast<double2*>(G.V + iL) = make_double2(VL, VR);
     *reinterpret_cast<double2*>(G.E + iL) = make_double2(EL, ER);
@@ -780,12 +788,12 @@ __global__ void __launch_bounds__(128) k_gradient(const EvalRule R, const GradAr
     int L = 0;
 #pragma unroll
     for (int j = 0; j < N; ++j) L += A.level[(size_t)j * A.m + r];
-    const double vol = pow2_neg(L);
+    const double vol = pow2_neg(L) * prm.vol;
     for (int e = lane; e < N * kCodes; e += 32) {
       const int j = e / kCodes, code = e - j * kCodes;
       const int lv = A.level[(size_t)j * A.m + r];
       const double h = 0.5 * pow2_neg(lv);
-      const double x = fma(h, code_offset(R, code), A.lower[(size_t)j * A.m + r] + h);
+      const double x = point_x(prm, j, A.lower[(size_t)j * A.m + r] + h, h, code_offset(R, code));
       const double ph = F::factor(F::axis(prm, j), x);
       double a0, a1;
       F::dlog(prm, j, x, ph, a0, a1);

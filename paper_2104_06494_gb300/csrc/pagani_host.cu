@@ -641,6 +641,8 @@ static int check_params(int fam, int n, const double* p) {
 static IntegrandParams to_params(int fam, int n, const double* p) {
   IntegrandParams q;
   std::memset(&q, 0, sizeof(q));
+  for (int j = 0; j < kMaxDim; ++j) q.len[j] = 1.0;  // the unit cube
+  q.vol = 1.0;
   if (fam == kFamOscillatory) {
     q.u = p[0];
     for (int j = 0; j < n; ++j) q.p0[j] = p[1 + j];
@@ -655,6 +657,17 @@ static IntegrandParams to_params(int fam, int n, const double* p) {
     }
   }
   return q;
+}
+
+// Threshold-Classify triggers of an options value: bit 0 the estimate's
+// digits unchanged, bit 1 memory about to be exhausted (Sec. 3.5.2).
+static int32_t trigger_mask(int32_t heuristic_filter) {
+  switch (heuristic_filter) {
+    case 0: return 0;
+    case 2: return 2;
+    case 3: return 1;
+    default: return 3;
+  }
 }
 
 static int default_init_div(int n) {
@@ -783,9 +796,9 @@ static int build_graph(int fam, int n, const EvalRule& rule, const Launch& L, Gr
   return 0;
 }
 
-static int integrate_locked(int n, int fam, const double* params, double epsrel, double epsabs,
-                            int64_t max_regions, const pagani_options& o, cudaStream_t st, pagani_result* out,
-                            pagani_trace_record* trace, int trace_cap) {
+static int integrate_locked(int n, int fam, const double* params, const double* lower, const double* upper,
+                            double epsrel, double epsabs, int64_t max_regions, const pagani_options& o,
+                            cudaStream_t st, pagani_result* out, pagani_trace_record* trace, int trace_cap) {
   std::memset(out, 0, sizeof(*out));
   if (n < PAGANI_MIN_DIM || n > PAGANI_MAX_DIM) return out->status = fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
   if (fam < 0 || fam >= kNumFamilies) return out->status = fail(PAGANI_ERR_INTEGRAND, "unknown integrand_id");
@@ -793,8 +806,21 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   if (!(epsrel > 0.0) || !(epsabs >= 0.0) || !std::isfinite(epsrel) || !std::isfinite(epsabs))
     return out->status = fail(PAGANI_ERR_TOLERANCE, "need epsrel > 0 and epsabs >= 0, finite");
   if (o.it_max < 1 || o.it_max > kTraceCap) return out->status = fail(PAGANI_ERR_ARGUMENT, "it_max out of range");
+  if (o.heuristic_filter < 0 || o.heuristic_filter > 3)
+    return out->status = fail(PAGANI_ERR_ARGUMENT, "heuristic_filter must be 0..3");
   int rc = check_params(fam, n, params);
   if (rc) return out->status = rc;
+  if ((lower == nullptr) != (upper == nullptr))
+    return out->status = fail(PAGANI_ERR_ARGUMENT, "give both bounds or neither");
+  double bound_vol = 1.0;
+  for (int j = 0; lower && j < n; ++j) {
+    const double len = upper[j] - lower[j];
+    if (!std::isfinite(lower[j]) || !std::isfinite(upper[j]) || !(len > 0.0) || !std::isfinite(len))
+      return out->status = fail(PAGANI_ERR_ARGUMENT, "bounds must be finite with upper > lower");
+    bound_vol *= len;
+  }
+  if (!(bound_vol > 0.0) || !std::isfinite(bound_vol))
+    return out->status = fail(PAGANI_ERR_ARGUMENT, "the volume of the bounds is not a normal number");
   const int d0 = o.init_div > 0 ? o.init_div : default_init_div(n);
   int log2d = 0;
   while ((1 << log2d) < d0) ++log2d;
@@ -832,7 +858,7 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   h.max_regions = max_regions;
   h.it_max = o.it_max;
   h.relerr_filter = o.relerr_filter ? 1 : 0;
-  h.heuristic_filter = o.heuristic_filter ? 1 : 0;
+  h.heuristic_filter = trigger_mask(o.heuristic_filter);
   h.trace_on = trace != nullptr ? 1 : 0;
   h.s = s0;
   h.it = 1;
@@ -840,6 +866,13 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   h.l0 = log2d;
   h.keep_leaves = o.keep_leaves ? 1 : 0;
   IntegrandParams prm = to_params(fam, n, params);
+  if (lower) {
+    for (int j = 0; j < n; ++j) {
+      prm.lo[j] = lower[j];
+      prm.len[j] = upper[j] - lower[j];
+    }
+    prm.vol = bound_vol;
+  }
   cudaError_t e;
 #define PG_CK(x)                                                                          \
   do {                                                                                    \
@@ -944,8 +977,9 @@ static int integrate_locked(int n, int fam, const double* params, double epsrel,
   out->iterations = h.it;
   out->n_regions = h.n_regions_total;
   out->n_active_last = h.s;
-  out->finished_volume = nval(h.fin_volume_acc);
-  out->active_volume = h.active_volume;
+  // the device tracks volumes of the unit cube; report them on the bounds
+  out->finished_volume = nval(h.fin_volume_acc) * bound_vol;
+  out->active_volume = h.active_volume * bound_vol;
   out->n_leaves = -1;
   if (o.keep_leaves && h.done) {
     if (h.leaf_overflow) {
@@ -1106,7 +1140,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   h.max_regions = max_regions;
   h.it_max = 100;
   h.relerr_filter = fam == kFamOscillatory ? 0 : 1;
-  h.heuristic_filter = 1;
+  h.heuristic_filter = trigger_mask(1);
   h.s = s0;
   h.it = 1;
   h.status = -100;
@@ -1427,6 +1461,7 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
   if (count <= 0 || !items || !res) return fail(PAGANI_ERR_ARGUMENT, "empty batch or null pointer");
   if (count > (1 << 24)) return fail(PAGANI_ERR_ARGUMENT, "batch too large");
   if (o.it_max < 1 || o.it_max > kTraceCap) return fail(PAGANI_ERR_ARGUMENT, "it_max out of range");
+  if (o.heuristic_filter < 0 || o.heuristic_filter > 3) return fail(PAGANI_ERR_ARGUMENT, "heuristic_filter must be 0..3");
   int64_t slot_cap = ((slot_cap_req + 1) / 2) * 2;
   // group the instances by (family, n)
   std::map<int, std::vector<int64_t>> by_group;
@@ -1527,7 +1562,7 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
       c.max_regions = slot_cap;
       c.it_max = o.it_max;
       c.relerr_filter = it.relerr_filter ? 1 : 0;
-      c.heuristic_filter = o.heuristic_filter ? 1 : 0;
+      c.heuristic_filter = trigger_mask(o.heuristic_filter);
       c.s = s0;
       c.it = 1;
       c.status = -100;
@@ -1704,20 +1739,28 @@ void pagani_default_options(pagani_options* o) {
   o->keep_leaves = 0;
 }
 
-int pagani_integrate_ex(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
-                        int64_t max_regions, const pagani_options* opt, void* cuda_stream, pagani_result* out,
-                        pagani_trace_record* trace, int trace_cap) {
+int pagani_integrate_box(int dim, int integrand_id, const double* params, const double* lower,
+                         const double* upper, double epsrel, double epsabs, int64_t max_regions,
+                         const pagani_options* opt, void* cuda_stream, pagani_result* out,
+                         pagani_trace_record* trace, int trace_cap) {
   if (!out) return fail(PAGANI_ERR_ARGUMENT, "out is NULL");
   pagani_options o;
   pagani_default_options(&o);
   if (opt) o = *opt;
   std::lock_guard<std::mutex> lk(g_mu);
   try {
-    return integrate_locked(dim, integrand_id, params, epsrel, epsabs, max_regions, o,
+    return integrate_locked(dim, integrand_id, params, lower, upper, epsrel, epsabs, max_regions, o,
                             (cudaStream_t)cuda_stream, out, trace, trace_cap);
   } catch (...) {
     return out->status = fail(PAGANI_ERR_CUDA, "internal error");
   }
+}
+
+int pagani_integrate_ex(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
+                        int64_t max_regions, const pagani_options* opt, void* cuda_stream, pagani_result* out,
+                        pagani_trace_record* trace, int trace_cap) {
+  return pagani_integrate_box(dim, integrand_id, params, nullptr, nullptr, epsrel, epsabs, max_regions, opt,
+                              cuda_stream, out, trace, trace_cap);
 }
 
 int pagani_integrate(int dim, int integrand_id, const double* params, double epsrel, double epsabs,

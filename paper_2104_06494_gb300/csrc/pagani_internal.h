@@ -75,6 +75,12 @@ struct IntegrandParams {
   double p0[kMaxDim];   // c (product peak), a (Gaussian, corner peak, C0, oscillatory, discontinuous)
   double p1[kMaxDim];   // w (product peak, Gaussian, C0, discontinuous)
   double u;             // oscillatory phase parameter; box-power exponent
+  // integration bounds [a, b] (Algorithm 2): regions live in the unit cube
+  // and a point x of it is evaluated at lo + len x; vol = prod len.  The
+  // unit cube (lo = 0, len = 1, vol = 1) maps exactly onto itself.
+  double lo[kMaxDim];
+  double len[kMaxDim];
+  double vol;
 };
 
 // Neumaier pair used for compensated sums.

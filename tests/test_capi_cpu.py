@@ -76,6 +76,16 @@ def test_host_argument_checks(lib):
         pg.pagani_integrate(3, 0, [0.0] * 6, 1e-3)       # product peak needs c != 0
     with pytest.raises(pg.PaganiError):
         pg.pagani_integrate(3, 0, [7.0] * 6, 1e-3, max_regions=100)  # below the initial split
+    with pytest.raises(pg.PaganiError, match="-8"):
+        pg.pagani_integrate_ex(3, 0, [7.0] * 6, 1e-3, heuristic_filter=4)  # trigger modes are 0..3
+    with pytest.raises(pg.PaganiError, match="-8"):
+        pg.pagani_integrate_ex(3, 0, [7.0] * 6, 1e-3, bounds=([0.0, 0.5, 0.0], [1.0, 0.5, 1.0]))  # empty box
+    with pytest.raises(pg.PaganiError, match="-8"):
+        pg.pagani_integrate_ex(3, 0, [7.0] * 6, 1e-3, bounds=([0.0, 0.0, -1e308], [1.0, 1.0, 1e308]))
+    with pytest.raises(pg.PaganiError, match="-2"):
+        pg.pagani_integrate(3, pg.BOX_POWER, [-1.0], 1e-3)                # box power needs q >= 0
+    with pytest.raises(pg.PaganiError, match="-2"):
+        pg.pagani_integrate(3, pg.DISCONTINUOUS, [1.0, 2.0, float("nan"), 0.5, 0.5, 0.5], 1e-3)
 
 
 @pytest.mark.skipif(has_gpu(), reason="checks the behaviour without a GPU")

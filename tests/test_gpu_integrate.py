@@ -41,6 +41,112 @@ def test_loop_matches_oracle(pg, family, n, tau, relerr):
     compare_runs(g, o)
 
 
+def _box(family, n, seed, params=None):
+    """A random box with negative and positive ends; the corner peak's stays
+    where 1 + a.x > 0, and with params given the Gaussian's holds its peak w
+    (a box far from a narrow peak leaves the first rule points in its tail,
+    where the error estimate is blind: at d = 8 such a box gave 1e-83 for
+    an integral of 5e-74, with an error estimate of 2e-85, on both sides)."""
+    rng = np.random.default_rng(seed)
+    if family == 1 and params is not None:
+        w = np.asarray(params[n:2 * n])
+        return w - rng.uniform(0.3, 0.7, n), w + rng.uniform(0.3, 0.7, n)
+    lo = rng.uniform(0.0, 0.5, n) if family == 3 else rng.uniform(-0.8, 0.6, n)
+    return lo, lo + rng.uniform(0.3, 1.4, n)
+
+
+@pytest.mark.parametrize("family,n,tau", [(0, 3, 1e-6), (1, 4, 1e-5), (2, 3, 1e-6), (3, 3, 1e-7), (4, 3, 1e-4),
+                                          (5, 3, 1e-3), (6, 3, 1e-9), (1, 6, 1e-4), (1, 8, 1e-2)])
+def test_general_bounds_match_oracle(pg, family, n, tau):
+    """Algorithm 2 over a box [a, b] with negative and positive ends: the GPU
+    maps unit-cube rule points onto the box, the oracle splits the box
+    itself; equal region sets and traces, estimates to 1e-12, the volume
+    of the box tiled, and the box's closed form inside the error estimate
+    (except for the C0 kink and the discontinuous jump, where the null rules
+    are not a bound)."""
+    params = draw_params(family, n, 1700 + 10 * family + n)
+    lo, hi = _box(family, n, 41 + 10 * family + n, params)
+    relerr = 0 if family == 2 else 1
+    o = oracle.integrate(family, n, params, tau, max_regions=2_000_000, relerr_filter=relerr, bounds=(lo, hi))
+    g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=2_000_000, relerr_filter=relerr,
+                               bounds=(lo, hi), trace=True)
+    compare_runs(g, o)
+    vol = float(np.prod(hi - lo))
+    assert abs(g.finished_volume + g.active_volume - vol) <= 1e-13 * vol
+    assert abs(g.finished_volume - o.finished_volume) <= 1e-13 * vol
+    ex = cf.closed_form_box(family, n, params, lo, hi)
+    if ex is not None and family not in (4, 5):
+        assert abs(g.estimate - ex) <= max(g.errorest, 1e-13 * abs(ex))
+
+
+def test_unit_bounds_are_the_unit_cube_bitwise(pg):
+    """The map lo + len x with lo = 0, len = 1 is exact, so integrating over
+    [0, 1]^n through the bounds entry gives the unit-cube run bit for bit."""
+    for family, n in ((1, 5), (2, 4), (6, 3)):
+        params = draw_params(family, n, 88 + family)
+        a = pg.pagani_integrate_ex(n, family, params, 1e-6, relerr_filter=0 if family == 2 else 1, trace=True)
+        b = pg.pagani_integrate_ex(n, family, params, 1e-6, relerr_filter=0 if family == 2 else 1, trace=True,
+                                   bounds=(np.zeros(n), np.ones(n)))
+        assert (a.estimate, a.errorest, a.status, a.n_regions) == (b.estimate, b.errorest, b.status, b.n_regions)
+        assert a.trace.tobytes() == b.trace.tobytes()
+
+
+def test_bounds_scale_the_measure(pg):
+    """Integrating f(x) over [a, b] equals vol * the integral of f(a + L t)
+    over the unit cube: for the Gaussian, the latter is itself a Gaussian with
+    a' = a L and w' = (w - a)/L.  The two runs see the same values up to
+    rounding, but the bounded run breaks split-axis ties by widths on the
+    box, so their region sets may differ; the estimates agree within the
+    two error estimates."""
+    n = 4
+    p = np.array(draw_params(1, n, 5151))
+    lo, hi = _box(1, n, 5, p)
+    L = hi - lo
+    a, w = p[:n], p[n:]
+    g = pg.pagani_integrate_ex(n, 1, p, 1e-7, bounds=(lo, hi))
+    u = pg.pagani_integrate_ex(n, 1, np.concatenate([a * L, (w - lo) / L]), 1e-7)
+    vol = float(np.prod(L))
+    assert g.status == u.status
+    assert abs(g.estimate - vol * u.estimate) <= g.errorest + vol * u.errorest
+
+
+def test_bounds_argument_errors(pg):
+    with pytest.raises(pg.PaganiError, match="-8"):
+        pg.pagani_integrate_ex(3, 1, draw_params(1, 3, 1), 1e-3, bounds=([0, 0, 0], [1, 0, 1]))
+    with pytest.raises(pg.PaganiError, match="-8"):
+        pg.pagani_integrate_ex(3, 1, draw_params(1, 3, 1), 1e-3, bounds=([0, 0, 0], [1, np.inf, 1]))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_filter_modes_match_oracle(pg, mode):
+    """The filtering ablation (Sec. 4.2): Threshold-Classify off (0), on with
+    both triggers of Sec. 3.5.2 (1), with the memory trigger only (2) or the
+    unchanged-digits trigger only (3), on the paper's f4 at d = 5 with a
+    10^6-region pool: modes 1 and 2 converge, 0 and 3 run out of memory at
+    iteration 10, on both sides alike."""
+    from paper_2104_06494_gb300.workloads import paper_integrands
+    w = paper_integrands()["f4_d5"]
+    o = oracle.integrate(w.family, w.dim, w.params, 1e-4, max_regions=1_000_000, heuristic_filter=mode)
+    g = pg.pagani_integrate_ex(w.dim, w.family, w.params, 1e-4, max_regions=1_000_000, heuristic_filter=mode,
+                               trace=True)
+    compare_runs(g, o)
+    assert g.status == (0 if mode in (1, 2) else 2)
+
+
+def test_filtering_ablation_f4_d8(pg):
+    """The paper's ablation case: 8-D f4 at three digits.  With the heuristic
+    filter the run converges inside a 2^27-region pool; without it the
+    active set outgrows the pool (memory exhausted, status 2) before the
+    error estimate reaches 1e-3."""
+    from paper_2104_06494_gb300.workloads import paper_integrands
+    w = paper_integrands()["f4_d8"]
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    on = pg.pagani_integrate_ex(w.dim, w.family, w.params, 1e-3, max_regions=1 << 27, heuristic_filter=1)
+    off = pg.pagani_integrate_ex(w.dim, w.family, w.params, 1e-3, max_regions=1 << 27, heuristic_filter=0)
+    assert on.status == 0 and abs(on.estimate - ex) <= on.errorest
+    assert off.status == 2 and off.errorest > 1e-3 * abs(off.estimate)
+
+
 @pytest.mark.parametrize("n,tau", [(2, 1e-4), (3, 1e-3)])
 def test_discontinuous_without_heuristic_filter(pg, n, tau):
     """The discontinuous family converges only with the heuristic filter off
