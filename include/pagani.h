@@ -103,7 +103,11 @@ typedef struct {
   int32_t it_max;           /* iteration limit (default 100)                                       */
   int32_t use_graph;        /* 1 (default): device-resident loop in one CUDA graph; 0: host-driven */
   int32_t keep_leaves;      /* 1: keep the converged leaf set for pagani_leaves / differentiation;
-                               0 (default)                                                         */
+                               0 (default); needs rule_degree 9                                   */
+  int32_t rule_degree;      /* cubature rule: 9 (default; 0 means the same) the degree-9 rule with
+                               four null rules (Sec. 2.1, 3.2); 7 the Genz-Malik degree-7 rule of
+                               Cuhre, 2^dim + 2 dim^2 + 2 dim + 1 points, error |R7 - R5| with its
+                               embedded degree-5 rule.  Other values: PAGANI_ERR_ARGUMENT          */
 } pagani_options;
 
 /* One record per iteration (Algorithm 2 scalars after that iteration). */
@@ -184,7 +188,8 @@ int pagani_integrate_noalloc(int dim, int integrand_id, const double* params, do
  * the group (timed on that batch's first iteration) and cached.
  * items: host array of count items; results: host array of count results (in
  * item order).  opt: NULL = defaults (heuristic_filter, it_max and
- * use_graph are used).  device_ms (may be NULL) receives the device time of
+ * use_graph are used; rule_degree must be 9 or 0, the degree-9 rule).
+ * device_ms (may be NULL) receives the device time of
  * the loop (CUDA events on the stream).  Returns 0 when the batch ran (each
  * item's status in its result), < 0 on an argument or CUDA error. */
 typedef struct {
@@ -226,6 +231,13 @@ int pagani_workspace_release(void);
 int pagani_evaluate(int dim, int integrand_id, const double* params, int64_t m, const double* lower,
                     const double* width, double* V, double* E, int32_t* K, double* diag, void* cuda_stream);
 
+/* As pagani_evaluate with the rule chosen by rule_degree (9 or 7, as in
+ * pagani_options).  With 7, E is |R7 - R5| and diag row 0 holds that
+ * difference (rows 1..3 and their floors are zero). */
+int pagani_evaluate_ex(int dim, int integrand_id, const double* params, int rule_degree, int64_t m,
+                       const double* lower, const double* width, double* V, double* E, int32_t* K, double* diag,
+                       void* cuda_stream);
+
 /* The converged leaf set of the last integration run with keep_leaves: the
  * boxes whose rule values make up the estimate v + v_f of Algorithm 2 (every
  * box classified finished, in the iteration it finished, and every box of
@@ -256,6 +268,13 @@ int pagani_gradient(int dim, int integrand_id, const double* params, int64_t m, 
  * counts[9] = orbit sizes.  Host computation only (no GPU needed).  Returns
  * the number of rule points N(dim), or < 0 on error. */
 int pagani_rule_tables(int dim, double* radius, double* weights, int64_t* counts);
+
+/* As pagani_rule_tables for rule_degree 9 or 7.  For 7 the Genz-Malik orbits
+ * sit on the slots of the same structure (centre; one axis at sqrt(9/70) in
+ * slot lp and at sqrt(9/10) in slot l2; pairs at sqrt(9/10) in slot l1l1;
+ * every axis at sqrt(9/19) in slot l0^n), column 1 holds w7 - w5 and
+ * columns 2..4 are zero. */
+int pagani_rule_tables_ex(int dim, int rule_degree, double* radius, double* weights, int64_t* counts);
 
 /* Measures this GPU's FP64 throughput with independent-chain
  * microbenchmarks (the roofline denominators of Evaluate).  Writes up to

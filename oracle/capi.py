@@ -15,6 +15,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import rule as _rule
+from . import rule_gm7 as _rule_gm7
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pagani_oracle.c")
@@ -38,7 +39,7 @@ class _Rule(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("G", ctypes.c_int),
                 ("gen", ctypes.POINTER(ctypes.c_double)), ("wts", ctypes.POINTER(ctypes.c_double)),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("q", ctypes.c_double),
-                ("count", ctypes.POINTER(ctypes.c_int64))]
+                ("count", ctypes.POINTER(ctypes.c_int64)), ("error_kind", ctypes.c_int)]
 
 
 class _Opt(ctypes.Structure):
@@ -74,20 +75,32 @@ def _load():
 _rule_cache: dict = {}
 
 
-def _rule_struct(n: int):
-    if n not in _rule_cache:
-        gen, wts = _rule.rule_tables(n)
+def _rule_struct(n: int, degree: int = 9):
+    """The rule as the C oracle reads it: degree 9 (the PAGANI rule, four
+    null rules) or 7 (the Genz-Malik rule, error |R7 - R5|)."""
+    key = (n, degree)
+    if key not in _rule_cache:
+        if degree == 9:
+            gen, wts = _rule.rule_tables(n)
+            a, b = _rule.fourth_difference_offsets()
+            q = float(_rule.LP / _rule.L2)
+            _, counts, _, _, _ = _rule.exact_rule(n)
+            kind = 0
+        elif degree == 7:
+            gen, wts = _rule_gm7.rule_tables(n)
+            a, b, q = _rule_gm7.fourth_difference_offsets()
+            _, counts, _, _, _ = _rule_gm7.exact_rule(n)
+            kind = 1
+        else:
+            raise ValueError("rule degree must be 9 or 7")
         g = np.ascontiguousarray(gen, dtype=np.float64)
         w = np.ascontiguousarray(wts, dtype=np.float64)
-        a, b = _rule.fourth_difference_offsets()
-        q = float(_rule.LP / _rule.L2)
-        _, counts, _, _, _ = _rule.exact_rule(n)
         c = np.ascontiguousarray(counts, dtype=np.int64)
         r = _Rule(n, g.shape[0], g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                   w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a, b, q,
-                  c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
-        _rule_cache[n] = (r, g, w, c)
-    return _rule_cache[n][0]
+                  c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), kind)
+        _rule_cache[key] = (r, g, w, c)
+    return _rule_cache[key][0]
 
 
 def _dp(x):
@@ -98,7 +111,7 @@ def default_init_div(n: int) -> int:
     return _load().oracle_default_init_div(n)
 
 
-def evaluate(family: int, n: int, params, lower, width, diag: bool = False):
+def evaluate(family: int, n: int, params, lower, width, diag: bool = False, degree: int = 9):
     """Evaluate regions (arrays m x n).  Returns V, E (null-rule error, before
     the two-level refinement) and K; with diag=True also the diagnostic rows
     [N_1..N_4, rounding scales of N_1..N_4, rounding scale of V, D_0..D_{n-1},
@@ -112,7 +125,7 @@ def evaluate(family: int, n: int, params, lower, width, diag: bool = False):
     E = np.zeros(m)
     K = np.zeros(m, dtype=np.int32)
     D = np.zeros((m, 13 + 2 * n)) if diag else None
-    lib.oracle_evaluate(ctypes.byref(_rule_struct(n)), ctypes.c_int(family), _dp(p), ctypes.c_int64(m),
+    lib.oracle_evaluate(ctypes.byref(_rule_struct(n, degree)), ctypes.c_int(family), _dp(p), ctypes.c_int64(m),
                         _dp(lo), _dp(wd), _dp(V), _dp(E), K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                         _dp(D) if diag else None)
     return (V, E, K, D) if diag else (V, E, K)
@@ -135,8 +148,9 @@ class OracleResult:
 
 def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20, max_regions: int = 10 ** 6,
               relerr_filter: int = 1, heuristic_filter: int = 1, init_div: int = 0, it_max: int = 100,
-              want_regions: bool = False, want_leaves: bool = False, bounds=None) -> OracleResult:
-    """bounds: None for the unit cube, else (a, b), each of length n."""
+              want_regions: bool = False, want_leaves: bool = False, bounds=None, degree: int = 9) -> OracleResult:
+    """bounds: None for the unit cube, else (a, b), each of length n; degree:
+    the rule (9, or 7 for the Genz-Malik variant)."""
     lib = _load()
     p = np.ascontiguousarray(params, dtype=np.float64)
     opt = _Opt(relerr_filter, heuristic_filter, init_div, it_max, None, None)
@@ -161,7 +175,7 @@ def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20,
         lcap = 8 * max_regions
         ll = np.zeros((lcap, n))
         lw = np.zeros((lcap, n))
-    lib.oracle_pagani(ctypes.byref(_rule_struct(n)), ctypes.c_int(family), _dp(p), ctypes.c_double(epsrel),
+    lib.oracle_pagani(ctypes.byref(_rule_struct(n, degree)), ctypes.c_int(family), _dp(p), ctypes.c_double(epsrel),
                       ctypes.c_double(epsabs), ctypes.c_int64(max_regions), ctypes.byref(opt), ctypes.byref(res),
                       trace.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(it_max),
                       _dp(fl) if want_regions else None, _dp(fw) if want_regions else None,

@@ -77,6 +77,9 @@ typedef struct {
   const double *wts;  /* G x 5: basic rule, then null rules u_1..u_4 */
   double a, b, q;     /* fourth-difference radii sqrt(lp), sqrt(l2); q = a^2/b^2 */
   const int64_t *count; /* G orbit sizes */
+  int error_kind;     /* 0: the four-null-rule error formula (degree-9 rule);
+                         1: |R7 - R5|, the Genz-Malik degree-7 rule's difference
+                         with its embedded degree-5 rule (null rule 1 = w7 - w5) */
 } oracle_rule;
 
 typedef struct {
@@ -262,7 +265,7 @@ static void evaluate_region(const oracle_rule *R, int fam, const double *p,
     Nused[k] = N[k] <= Nfloor[k] ? 0.0 : N[k];
   }
   *V = vol * basic;
-  *E = null_rule_error(Nused);
+  *E = R->error_kind == 1 ? Nused[0] : null_rule_error(Nused);
 
   /* split axis from fourth divided differences */
   double x[16], D[16], Dabs[16], Dused[16], f0, Dmax = 0.0;

@@ -55,7 +55,7 @@ class BatchResult(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("relerr_filter", ctypes.c_int32), ("heuristic_filter", ctypes.c_int32),
                 ("init_div", ctypes.c_int32), ("it_max", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("keep_leaves", ctypes.c_int32)]
+                ("keep_leaves", ctypes.c_int32), ("rule_degree", ctypes.c_int32)]
 
 
 TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.int32), ("search_ok", np.int32),
@@ -67,7 +67,8 @@ TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.i
 EXPORTED = ["pagani_default_options", "pagani_integrate", "pagani_integrate_ex", "pagani_workspace_reserve",
             "pagani_workspace_release", "pagani_evaluate", "pagani_rule_tables", "pagani_fp64_peak",
             "pagani_last_error", "pagani_version", "pagani_integrate_noalloc", "pagani_leaves", "pagani_gradient",
-            "pagani_integrate_batch", "pagani_integrate_box"]
+            "pagani_integrate_batch", "pagani_integrate_box", "pagani_evaluate_ex",
+            "pagani_rule_tables_ex"]
 
 _lib = None
 
@@ -107,6 +108,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.pagani_evaluate.restype = ctypes.c_int
+    lib.pagani_evaluate_ex.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_int, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.pagani_evaluate_ex.restype = ctypes.c_int
     lib.pagani_leaves.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int64),
                                   ctypes.c_void_p]
     lib.pagani_leaves.restype = ctypes.c_int
@@ -118,6 +123,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.pagani_integrate_batch.restype = ctypes.c_int
     lib.pagani_rule_tables.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64)]
     lib.pagani_rule_tables.restype = ctypes.c_int
+    lib.pagani_rule_tables_ex.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
+                                          P(ctypes.c_int64)]
+    lib.pagani_rule_tables_ex.restype = ctypes.c_int
     lib.pagani_fp64_peak.argtypes = [P(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]
     lib.pagani_fp64_peak.restype = ctypes.c_int
     lib.pagani_last_error.argtypes = []
@@ -188,13 +196,13 @@ def pagani_integrate_ex(dim: int, integrand_id: int, params, epsrel: float, epsa
                         max_regions: int = 10_000_000, relerr_filter: int = 1, heuristic_filter: int = 1,
                         init_div: int = 0, it_max: int = 100, use_graph: int = 1, stream: int | None = None,
                         trace: bool = False, raise_on_error: bool = True, keep_leaves: int = 0,
-                        bounds=None) -> Integration:
+                        bounds=None, rule_degree: int = 9) -> Integration:
     """C ABI pagani_integrate_ex, or pagani_integrate_box when bounds = (a, b)
     (each of length dim) is given; stream is a raw cudaStream_t (e.g.
     torch.cuda.current_stream().cuda_stream) or None for the library stream."""
     lib = load()
     p, pp = _params_array(params)
-    o = Options(relerr_filter, heuristic_filter, init_div, it_max, use_graph, keep_leaves)
+    o = Options(relerr_filter, heuristic_filter, init_div, it_max, use_graph, keep_leaves, rule_degree)
     r = Result()
     tr = np.zeros(it_max, dtype=TRACE_DTYPE) if trace else None
     tail = (ctypes.byref(o), ctypes.c_void_p(stream or 0), ctypes.byref(r),
@@ -241,11 +249,12 @@ def pagani_workspace_release() -> None:
     load().pagani_workspace_release()
 
 
-def pagani_evaluate(dim: int, integrand_id: int, params, lower, width, diag: bool = False, stream: int | None = None):
-    """Evaluate on caller boxes.  lower, width: CUDA tensors (float64) of
-    shape (dim, m) (SoA).  Returns CUDA tensors V, E (float64), K (int32)
-    and, with diag=True, the (8 + dim, m) diagnostics (N_1..N_4, their noise
-    floors, D_j)."""
+def pagani_evaluate(dim: int, integrand_id: int, params, lower, width, diag: bool = False, stream: int | None = None,
+                    rule_degree: int = 9):
+    """Evaluate on caller boxes (C ABI pagani_evaluate_ex).  lower, width:
+    CUDA tensors (float64) of shape (dim, m) (SoA).  Returns CUDA tensors V,
+    E (float64), K (int32) and, with diag=True, the (8 + dim, m) diagnostics
+    (N_1..N_4, their noise floors, D_j)."""
     import torch
 
     lib = load()
@@ -262,10 +271,10 @@ def pagani_evaluate(dim: int, integrand_id: int, params, lower, width, diag: boo
     p, pp = _params_array(params)
     if stream is None:
         stream = torch.cuda.current_stream(dev).cuda_stream
-    rc = lib.pagani_evaluate(dim, integrand_id, pp, m, ctypes.c_void_p(lower.data_ptr()),
-                             ctypes.c_void_p(width.data_ptr()), ctypes.c_void_p(V.data_ptr()),
-                             ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(K.data_ptr()),
-                             ctypes.c_void_p(D.data_ptr()) if diag else None, ctypes.c_void_p(stream))
+    rc = lib.pagani_evaluate_ex(dim, integrand_id, pp, rule_degree, m, ctypes.c_void_p(lower.data_ptr()),
+                                ctypes.c_void_p(width.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(K.data_ptr()),
+                                ctypes.c_void_p(D.data_ptr()) if diag else None, ctypes.c_void_p(stream))
     if rc < 0:
         raise PaganiError(f"pagani_evaluate failed ({rc}): {last_error()}")
     return (V, E, K, D) if diag else (V, E, K)
@@ -343,15 +352,16 @@ def pagani_integrate_batch(items, max_regions_per_item: int, heuristic_filter: i
     return out, ms.value
 
 
-def pagani_rule_tables(dim: int):
-    """(num_points, radius[5], weights[9, 5], counts[9]) as generated by the library (host code)."""
+def pagani_rule_tables(dim: int, rule_degree: int = 9):
+    """(num_points, radius[5], weights[9, 5], counts[9]) as generated by the
+    library (host code), for the degree-9 rule or the degree-7 variant."""
     lib = load()
     rad = np.zeros(5)
     w = np.zeros(45)
     cnt = np.zeros(9, dtype=np.int64)
-    npts = lib.pagani_rule_tables(dim, rad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                  w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                  cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    npts = lib.pagani_rule_tables_ex(dim, rule_degree, rad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
     if npts < 0:
         raise PaganiError(f"pagani_rule_tables failed ({npts}): {last_error()}")
     return npts, rad, w.reshape(9, 5), cnt

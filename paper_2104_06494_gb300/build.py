@@ -33,6 +33,18 @@ def _sources():
     return [os.path.join(CSRC, s) for s in CU_SOURCES + CPP_SOURCES]
 
 
+def _units():
+    """(source, extra flags, object name): every eval_*.cu is compiled twice,
+    the second time with -DPAGANI_GM7 for the degree-7 rule variant."""
+    units = []
+    for src in _sources():
+        base = os.path.basename(src)
+        units.append((src, [], base + ".o"))
+        if base.startswith("eval_"):
+            units.append((src, ["-DPAGANI_GM7"], base[:-3] + "_gm7.cu.o"))
+    return units
+
+
 def _headers():
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hs.append(os.path.join(HERE, "..", "include", "pagani.h"))
@@ -55,10 +67,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     env_flags = os.environ.get("PAGANI_EXTRA_NVCC_FLAGS", "").split()
     flags = NVCC_FLAGS + env_flags + (extra_flags or [])
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
+    def compile_one(unit) -> str:
+        src, defs, name = unit
+        obj = os.path.join(OUT, name)
         if src.endswith(".cu"):
-            cmd = [nvcc] + flags + ["-c", src, "-o", obj]
+            cmd = [nvcc] + flags + defs + ["-c", src, "-o", obj]
         else:
             cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", os.path.join(HERE, "..", "include"),
                    "-I", "/usr/local/cuda/include", "-c", src, "-o", obj]
@@ -69,8 +82,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             print(r.stdout + r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, _sources()))
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, _units()))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -3,9 +3,17 @@
 
 namespace pg {
 
+#ifdef PAGANI_GM7
+// compiled a second time with -DPAGANI_GM7: the Genz-Malik degree-7 variant
+const FamilyKernels& kernels_box_power_gm7() {
+  static const FamilyKernels k = make_family_kernels_gm7<Fixed<BoxPower>::template type, 64>();
+  return k;
+}
+#else
 const FamilyKernels& kernels_box_power() {
   static const FamilyKernels k = make_family_kernels<Fixed<BoxPower>::template type, 64>();
   return k;
 }
+#endif
 
 }  // namespace pg

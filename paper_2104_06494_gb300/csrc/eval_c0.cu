@@ -3,9 +3,17 @@
 
 namespace pg {
 
+#ifdef PAGANI_GM7
+// compiled a second time with -DPAGANI_GM7: the Genz-Malik degree-7 variant
+const FamilyKernels& kernels_c0_gm7() {
+  static const FamilyKernels k = make_family_kernels_gm7<Fixed<C0Fam>::template type, 128>();
+  return k;
+}
+#else
 const FamilyKernels& kernels_c0() {
   static const FamilyKernels k = make_family_kernels<Fixed<C0Fam>::template type, 128>();
   return k;
 }
+#endif
 
 }  // namespace pg

@@ -288,7 +288,10 @@ __device__ __forceinline__ void axis_entries(typename F::T* tab, const EvalRule&
 
 // The nine generator sums S[g] = sum over the orbit of g of f, and the
 // fourth differences D[j], for one region whose factor table is `tab`.
-template <class F, int N, int THREADS>
+// DEG 9: every orbit of the degree-9 rule.  DEG 7: the Genz-Malik rule's
+// orbits only (centre, one axis at the lp and l2 slots, pairs at l1, the
+// vertices); the other sums stay zero.
+template <class F, int N, int THREADS, int DEG = 9>
 __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab, typename F::T base, double q,
                                           double (&S)[kNumGen], double (&D)[N]) {
   typedef typename F::T T;
@@ -316,8 +319,10 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
     // formed individually; the l1 and l3 points go straight into their sums
     double p2 = F::last(Q, PG_TB(kR2P, j)), m2 = F::last(Q, PG_TB(kR2M, j));
     double pp = F::last(Q, PG_TB(kRpP, j)), mp = F::last(Q, PG_TB(kRpM, j));
-    S[kGenL1] = F::acc(F::acc(S[kGenL1], Q, PG_TB(kR1P, j)), Q, PG_TB(kR1M, j));
-    S[kGenL3] = F::acc(F::acc(S[kGenL3], Q, PG_TB(kR3P, j)), Q, PG_TB(kR3M, j));
+    if constexpr (DEG == 9) {
+      S[kGenL1] = F::acc(F::acc(S[kGenL1], Q, PG_TB(kR1P, j)), Q, PG_TB(kR1M, j));
+      S[kGenL3] = F::acc(F::acc(S[kGenL3], Q, PG_TB(kR3P, j)), Q, PG_TB(kR3M, j));
+    }
     const double s2 = p2 + m2, sp = pp + mp;
     S[kGenL2] += s2;
     S[kGenLp] += sp;
@@ -341,29 +346,32 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
       if (k > j + 1) PM = F::mul(PM, PG_TB(kC0, k - 1));
       T Q = (k == N - 1) ? PM : F::mul(PM, suf[k + 1]);
       T a1p = F::mul(Q, PG_TB(kR1P, j)), a1m = F::mul(Q, PG_TB(kR1M, j));
-      T a2p = F::mul(Q, PG_TB(kR2P, j)), a2m = F::mul(Q, PG_TB(kR2M, j));
       const T b1p = PG_TB(kR1P, k), b1m = PG_TB(kR1M, k);
-      const T b2p = PG_TB(kR2P, k), b2m = PG_TB(kR2M, k);
-      double s5 = S[kGenL1L1], s6 = S[kGenL1L2];
+      double s5 = S[kGenL1L1];
       s5 = F::acc(s5, a1p, b1p);
       s5 = F::acc(s5, a1p, b1m);
       s5 = F::acc(s5, a1m, b1p);
       s5 = F::acc(s5, a1m, b1m);
-      s6 = F::acc(s6, a1p, b2p);
-      s6 = F::acc(s6, a1p, b2m);
-      s6 = F::acc(s6, a1m, b2p);
-      s6 = F::acc(s6, a1m, b2m);
-      s6 = F::acc(s6, a2p, b1p);
-      s6 = F::acc(s6, a2p, b1m);
-      s6 = F::acc(s6, a2m, b1p);
-      s6 = F::acc(s6, a2m, b1m);
       S[kGenL1L1] = s5;
-      S[kGenL1L2] = s6;
+      if constexpr (DEG == 9) {
+        T a2p = F::mul(Q, PG_TB(kR2P, j)), a2m = F::mul(Q, PG_TB(kR2M, j));
+        const T b2p = PG_TB(kR2P, k), b2m = PG_TB(kR2M, k);
+        double s6 = S[kGenL1L2];
+        s6 = F::acc(s6, a1p, b2p);
+        s6 = F::acc(s6, a1p, b2m);
+        s6 = F::acc(s6, a1m, b2p);
+        s6 = F::acc(s6, a1m, b2m);
+        s6 = F::acc(s6, a2p, b1p);
+        s6 = F::acc(s6, a2p, b1m);
+        s6 = F::acc(s6, a2m, b1p);
+        s6 = F::acc(s6, a2m, b1m);
+        S[kGenL1L2] = s6;
+      }
     }
   }
 
   // axis triples j < k < l at l1: Q = pre[j] * mid(j,k) * mid(k,l) * suf[l+1]
-  if (N >= 3) {
+  if (N >= 3 && DEG == 9) {
 #pragma unroll
     for (int j = 0; j < N - 2; ++j) {
       T PM1 = pre[j];
@@ -434,16 +442,19 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
 // Rule, null rules, error and split axis of one region from its sums.
 // UNIT: the integrand is signed with |f| <= 1, so the magnitude of an orbit
 // sum is bounded by the orbit size; otherwise f > 0 and it is |S_g|.
-template <int N, bool UNIT>
+// DEG 7: one null rule, w7 - w5, whose value is the error |R7 - R5|.
+template <int N, bool UNIT, int DEG = 9>
 __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double (&S)[kNumGen], const double (&D)[N],
                                                 double vol, const double (&width)[N], double& V, double& E, int& K,
                                                 double* nk_out) {
+  constexpr int NK = DEG == 9 ? 4 : 1;  // null rules in use
   double b = 0.0, u[4] = {0.0, 0.0, 0.0, 0.0}, msum = 0.0;
 #pragma unroll
   for (int g = 0; g < kNumGen; ++g) {
+    if (DEG == 7 && !(g == kGenCentre || g == kGenL2 || g == kGenLp || g == kGenL1L1 || g == kGenL0All)) continue;
     b = fma(R.w[g][0], S[g], b);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) u[k] = fma(R.w[g][1 + k], S[g], u[k]);
+    for (int k = 0; k < NK; ++k) u[k] = fma(R.w[g][1 + k], S[g], u[k]);
     if (!UNIT) msum += fabs(S[g]);
   }
   V = vol * b;
@@ -451,9 +462,9 @@ __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double 
   // floor is noise * vol * sum_g |u_kg| M_g; max_g |u_kg| * sum_g M_g bounds
   // it from above, so the exact floor is formed only when the bound does not
   // already clear N_k
-  double nk[4], nu[4];
+  double nk[4] = {0.0, 0.0, 0.0, 0.0}, nu[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NK; ++k) {
     nk[k] = vol * fabs(u[k]);
     const double bound = UNIT ? R.floor_unit[k] : R.umax[k] * msum;
     double floor_k = 0.0;
@@ -470,7 +481,10 @@ __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double 
       nk_out[4 + k] = floor_k;
     }
   }
-  E = null_error(nu[0], nu[1], nu[2], nu[3]);
+  if (nk_out)
+#pragma unroll
+    for (int k = NK; k < 4; ++k) nk_out[k] = nk_out[4 + k] = 0.0;
+  E = DEG == 9 ? null_error(nu[0], nu[1], nu[2], nu[3]) : nu[0];
   // split axis: the largest fourth difference above its noise floor (floored
   // ones carry a negative sign), near-ties to the lowest axis; with every
   // difference at the floor, the widest axis
@@ -493,8 +507,9 @@ __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double 
 }
 
 // ------------------------------------------------------------- loop kernel
-// One thread per sibling pair (2p, 2p+1) of the current pool buffer.
-template <class F, int N, int THREADS>
+// One thread per sibling pair (2p, 2p+1) of the current pool buffer; DEG is
+// the rule (9, or 7 for the Genz-Malik variant).
+template <class F, int N, int THREADS, int DEG = 9>
 __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(const EvalRule R, const LoopArgs A) {
   typedef typename F::T T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -550,13 +565,13 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     double S[kNumGen], D[N];
     double VL, EL, VR, ER;
     int KL, KR;
-    rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
-    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL) * prm.vol, wL, VL, EL, KL, nullptr);
+    rule_sums<F, N, THREADS, DEG>(tab, base, R.q, S, D);
+    region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, pow2_neg(lvL) * prm.vol, wL, VL, EL, KL, nullptr);
     // patch the one axis where the right sibling differs
     if (diff_axis >= 0)
       axis_entries<F, N, THREADS>(tab, R, prm, fcache, A.fcache_levels, diff_lo, diff_lv, diff_axis);
-    rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
-    region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR) * prm.vol, wR, VR, ER, KR, nullptr);
+    rule_sums<F, N, THREADS, DEG>(tab, base, R.q, S, D);
+    region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, pow2_neg(lvR) * prm.vol, wR, VR, ER, KR, nullptr);
 
     if (it > 1) two_level(VL, VR, A.pool.Vp[p], EL, ER);
 
@@ -650,7 +665,7 @@ __global__ void __launch_bounds__(256) k_factor_cache(const EvalRule R, const Lo
 // --------------------------------------------------------- standalone kernel
 // Evaluates a caller-given list of boxes (lower, width SoA, n x m) with the
 // null-rule error (no two-level refinement); pairs (2i, 2i+1) share a thread.
-template <class F, int N, int THREADS, bool DIAG>
+template <class F, int N, int THREADS, bool DIAG, int DEG = 9>
 __global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule R, const StandaloneArgs A) {
   typedef typename F::T T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -683,8 +698,8 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule 
       }
       double S[kNumGen], D[N], V, E, nk[8];
       int K;
-      rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
-      region_epilogue<N, F::kUnitBounded>(R, S, D, vol, w, V, E, K, nk);
+      rule_sums<F, N, THREADS, DEG>(tab, base, R.q, S, D);
+      region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, vol, w, V, E, K, nk);
       A.V[i] = V;
       A.E[i] = E;
       A.K[i] = K;
@@ -853,9 +868,9 @@ __global__ void __launch_bounds__(128) k_gradient(const EvalRule R, const GradAr
 }
 
 // ---------------------------------------------------------------- launchers
-template <class F, int N, int THREADS>
+template <class F, int N, int THREADS, int DEG = 9>
 cudaError_t launch_loop(const EvalRule& R, const LoopArgs& A, int grid, int block, size_t smem, cudaStream_t st) {
-  k_evaluate_loop<F, N, THREADS><<<grid, block, smem, st>>>(R, A);
+  k_evaluate_loop<F, N, THREADS, DEG><<<grid, block, smem, st>>>(R, A);
   return cudaGetLastError();
 }
 template <class F, int N>
@@ -863,10 +878,10 @@ cudaError_t launch_fill(const EvalRule& R, const LoopArgs& A, int grid, int bloc
   k_factor_cache<F, N><<<grid, block, smem, st>>>(R, A);
   return cudaGetLastError();
 }
-template <class F, int N, int THREADS, bool DIAG>
+template <class F, int N, int THREADS, bool DIAG, int DEG = 9>
 cudaError_t launch_standalone(const EvalRule& R, const StandaloneArgs& A, int grid, int block, size_t smem,
                               cudaStream_t st) {
-  k_evaluate_standalone<F, N, THREADS, DIAG><<<grid, block, smem, st>>>(R, A);
+  k_evaluate_standalone<F, N, THREADS, DIAG, DEG><<<grid, block, smem, st>>>(R, A);
   return cudaGetLastError();
 }
 
@@ -911,6 +926,34 @@ FamilyKernels make_family_kernels() {
                        cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
                        (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
   cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, true>,       \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));
+  PG_SET(2) PG_SET(3) PG_SET(4) PG_SET(5) PG_SET(6) PG_SET(7) PG_SET(8)
+#undef PG_SET
+  return k;
+}
+
+// The Genz-Malik degree-7 variant: the loop, factor-cache fill and
+// standalone kernels (no batched form, no gradient).
+template <template <int> class FamOf, int THREADS>
+FamilyKernels make_family_kernels_gm7() {
+  FamilyKernels k = {};
+  k.threads = THREADS;
+#define PG_SET(NN)                                                                              \
+  k.loop[NN] = &launch_loop<FamOf<NN>, NN, THREADS, 7>;                                         \
+  k.fill[NN] = &launch_fill<FamOf<NN>, NN>;                                                     \
+  k.fill_fn[NN] = (const void*)&k_factor_cache<FamOf<NN>, NN>;                                  \
+  k.standalone[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, false, 7>;                      \
+  k.standalone_diag[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, true, 7>;                  \
+  k.loop_fn[NN] = (const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS, 7>;                     \
+  k.table_bytes_per_thread[NN] = (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN);           \
+  cudaFuncSetAttribute((const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS, 7>,                \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
+  cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, false, 7>,   \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
+  cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, true, 7>,    \
                        cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
                        (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));
   PG_SET(2) PG_SET(3) PG_SET(4) PG_SET(5) PG_SET(6) PG_SET(7) PG_SET(8)

@@ -451,7 +451,18 @@ constexpr int kMgmtThreads = 256;
 constexpr int kMgmtItems = 8;
 constexpr int kTraceCap = 1024;
 
-static const FamilyKernels& family_kernels(int fam) {
+static const FamilyKernels& family_kernels(int fam, int degree = 9) {
+  if (degree == 7) {
+    switch (fam) {
+      case kFamProductPeak: return kernels_product_peak_gm7();
+      case kFamGaussian: return kernels_gaussian_gm7();
+      case kFamOscillatory: return kernels_oscillatory_gm7();
+      case kFamCornerPeak: return kernels_corner_peak_gm7();
+      case kFamDiscontinuous: return kernels_discontinuous_gm7();
+      case kFamBoxPower: return kernels_box_power_gm7();
+      default: return kernels_c0_gm7();
+    }
+  }
   switch (fam) {
     case kFamProductPeak: return kernels_product_peak();
     case kFamGaussian: return kernels_gaussian();
@@ -462,6 +473,10 @@ static const FamilyKernels& family_kernels(int fam) {
     default: return kernels_c0();
   }
 }
+
+// The rule degree of an options value: 0 or 9 the degree-9 rule, 7 the
+// Genz-Malik variant, anything else -1.
+static int rule_degree(int32_t v) { return (v == 0 || v == 9) ? 9 : v == 7 ? 7 : -1; }
 
 static void release_graphs(Workspace& w) {
   for (auto& kv : w.graphs) {
@@ -590,13 +605,14 @@ static int ensure_leaf_log(int64_t cap, int n) {
   return 0;
 }
 
-static const RuleTable* get_rule(int n) {
-  auto it = g_rules.find(n);
+static const RuleTable* get_rule(int n, int degree = 9) {
+  const int key = n * 16 + degree;
+  auto it = g_rules.find(key);
   if (it != g_rules.end()) return &it->second;
   RuleTable t;
   double res = 0.0;
-  if (!build_rule(n, &t, &res) || !(res < 1e-14)) return nullptr;
-  return &(g_rules[n] = t);
+  if (!build_rule(n, degree, &t, &res) || !(res < 1e-14)) return nullptr;
+  return &(g_rules[key] = t);
 }
 
 static EvalRule to_eval_rule(const RuleTable& t) {
@@ -751,8 +767,8 @@ static cudaError_t add_while(cudaGraphNode_t* node, cudaGraph_t g, const cudaGra
 
 // The whole iteration loop of Algorithm 2 as one graph:
 //   WHILE(main) { evaluate -> WHILE(probe) { probe } -> count -> split }
-static int build_graph(int fam, int n, const EvalRule& rule, const Launch& L, GraphEntry* out) {
-  const FamilyKernels& fk = family_kernels(fam);
+static int build_graph(int fam, int n, int degree, const EvalRule& rule, const Launch& L, GraphEntry* out) {
+  const FamilyKernels& fk = family_kernels(fam, degree);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("cudaGraphCreate: ") + cudaGetErrorString(e));
@@ -808,6 +824,10 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
   if (o.it_max < 1 || o.it_max > kTraceCap) return out->status = fail(PAGANI_ERR_ARGUMENT, "it_max out of range");
   if (o.heuristic_filter < 0 || o.heuristic_filter > 3)
     return out->status = fail(PAGANI_ERR_ARGUMENT, "heuristic_filter must be 0..3");
+  const int deg = rule_degree(o.rule_degree);
+  if (deg < 0) return out->status = fail(PAGANI_ERR_ARGUMENT, "rule_degree must be 9 (or 0) or 7");
+  if (deg != 9 && o.keep_leaves)
+    return out->status = fail(PAGANI_ERR_ARGUMENT, "keep_leaves (differentiation) needs the degree-9 rule");
   int rc = check_params(fam, n, params);
   if (rc) return out->status = rc;
   if ((lower == nullptr) != (upper == nullptr))
@@ -831,7 +851,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
     if (s0 > ((int64_t)1 << 40)) return out->status = fail(PAGANI_ERR_ARGUMENT, "initial split too large");
   }
   if (s0 > max_regions) return out->status = fail(PAGANI_ERR_CAPACITY, "max_regions below the initial split");
-  const RuleTable* rt = get_rule(n);
+  const RuleTable* rt = get_rule(n, deg);
   if (!rt) return out->status = fail(PAGANI_ERR_CUDA, "rule construction failed");
   rc = ensure_workspace(max_regions > s0 ? max_regions : s0, n);
   if (rc) return out->status = rc;
@@ -842,7 +862,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
   }
   w.last_leaves = -1;
   if (!st) st = w.own_stream;
-  const FamilyKernels& fk = family_kernels(fam);
+  const FamilyKernels& fk = family_kernels(fam, deg);
   Launch L;
   rc = launch_config(fk, n, &L);
   if (rc) return out->status = rc;
@@ -892,11 +912,11 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
   int launches = 1, eval_launches = 0;  // the Uniform-Split kernel
   out->eval_ms = -1.0;
   if (o.use_graph) {
-    const int key = fam * 16 + n + (w.n << 8);
+    const int key = fam * 16 + n + (w.n << 8) + (deg << 16);
     auto it = w.graphs.find(key);
     if (it == w.graphs.end()) {
       GraphEntry ge;
-      rc = build_graph(fam, n, rule, L, &ge);
+      rc = build_graph(fam, n, deg, rule, L, &ge);
       if (rc) return out->status = rc;
       it = w.graphs.emplace(key, ge).first;
     }
@@ -1462,6 +1482,7 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
   if (count > (1 << 24)) return fail(PAGANI_ERR_ARGUMENT, "batch too large");
   if (o.it_max < 1 || o.it_max > kTraceCap) return fail(PAGANI_ERR_ARGUMENT, "it_max out of range");
   if (o.heuristic_filter < 0 || o.heuristic_filter > 3) return fail(PAGANI_ERR_ARGUMENT, "heuristic_filter must be 0..3");
+  if (rule_degree(o.rule_degree) != 9) return fail(PAGANI_ERR_ARGUMENT, "batches use the degree-9 rule");
   int64_t slot_cap = ((slot_cap_req + 1) / 2) * 2;
   // group the instances by (family, n)
   std::map<int, std::vector<int64_t>> by_group;
@@ -1737,6 +1758,7 @@ void pagani_default_options(pagani_options* o) {
   o->it_max = 100;
   o->use_graph = 1;
   o->keep_leaves = 0;
+  o->rule_degree = 9;
 }
 
 int pagani_integrate_box(int dim, int integrand_id, const double* params, const double* lower,
@@ -1817,7 +1839,15 @@ int pagani_workspace_release(void) {
 
 int pagani_evaluate(int dim, int integrand_id, const double* params, int64_t m, const double* lower,
                     const double* width, double* V, double* E, int32_t* K, double* diag, void* cuda_stream) {
+  return pagani_evaluate_ex(dim, integrand_id, params, 9, m, lower, width, V, E, K, diag, cuda_stream);
+}
+
+int pagani_evaluate_ex(int dim, int integrand_id, const double* params, int rule_degree_opt, int64_t m,
+                       const double* lower, const double* width, double* V, double* E, int32_t* K, double* diag,
+                       void* cuda_stream) {
   if (dim < PAGANI_MIN_DIM || dim > PAGANI_MAX_DIM) return fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
+  const int deg = rule_degree(rule_degree_opt);
+  if (deg < 0) return fail(PAGANI_ERR_ARGUMENT, "rule_degree must be 9 (or 0) or 7");
   if (integrand_id < 0 || integrand_id >= kNumFamilies) return fail(PAGANI_ERR_INTEGRAND, "unknown integrand_id");
   if (!params || m < 0) return fail(PAGANI_ERR_ARGUMENT, "bad params or m");
   if (m == 0) return 0;
@@ -1825,13 +1855,13 @@ int pagani_evaluate(int dim, int integrand_id, const double* params, int64_t m, 
   int rc = check_params(integrand_id, dim, params);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  const RuleTable* rt = get_rule(dim);
+  const RuleTable* rt = get_rule(dim, deg);
   if (!rt) return fail(PAGANI_ERR_CUDA, "rule construction failed");
   rc = ensure_workspace(4096, dim);
   if (rc) return rc;
   Workspace& w = g_ws;
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : w.own_stream;
-  const FamilyKernels& fk = family_kernels(integrand_id);
+  const FamilyKernels& fk = family_kernels(integrand_id, deg);
   IntegrandParams prm = to_params(integrand_id, dim, params);
   cudaError_t e = cudaMemcpyAsync(w.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
@@ -1924,10 +1954,16 @@ int pagani_gradient(int dim, int integrand_id, const double* params, int64_t m, 
 }
 
 int pagani_rule_tables(int dim, double* radius, double* weights, int64_t* counts) {
+  return pagani_rule_tables_ex(dim, 9, radius, weights, counts);
+}
+
+int pagani_rule_tables_ex(int dim, int rule_degree_opt, double* radius, double* weights, int64_t* counts) {
   if (dim < PAGANI_MIN_DIM || dim > PAGANI_MAX_DIM) return fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
+  const int deg = rule_degree(rule_degree_opt);
+  if (deg < 0) return fail(PAGANI_ERR_ARGUMENT, "rule_degree must be 9 (or 0) or 7");
   RuleTable t;
   double res = 0.0;
-  if (!build_rule(dim, &t, &res)) return fail(PAGANI_ERR_CUDA, "rule construction failed");
+  if (!build_rule(dim, deg, &t, &res)) return fail(PAGANI_ERR_CUDA, "rule construction failed");
   if (radius)
     for (int i = 0; i < 5; ++i) radius[i] = t.radius[i];
   if (weights)

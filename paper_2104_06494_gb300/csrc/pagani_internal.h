@@ -47,6 +47,7 @@ enum Code {
 
 struct RuleTable {
   int n;
+  int degree;              // 9: the PAGANI rule; 7: the Genz-Malik variant (error |R7 - R5| = null rule 1)
   int num_points;
   double radius[5];        // sqrt of l1, l2, l3, lp, l0 (on [-1, 1])
   double q;                // lp / l2 (fourth-difference weight)
@@ -54,7 +55,7 @@ struct RuleTable {
   int64_t count[kNumGen];  // orbit sizes
 };
 
-bool build_rule(int n, RuleTable* out, double* max_residual);
+bool build_rule(int n, int degree, RuleTable* out, double* max_residual);
 std::vector<uint64_t> point_codes(int n);
 int num_points(int n);
 int64_t orbit_count(int n, int g);
@@ -290,6 +291,14 @@ const FamilyKernels& kernels_corner_peak();
 const FamilyKernels& kernels_c0();
 const FamilyKernels& kernels_discontinuous();
 const FamilyKernels& kernels_box_power();
+// the Genz-Malik degree-7 variants (loop, cache fill, standalone)
+const FamilyKernels& kernels_product_peak_gm7();
+const FamilyKernels& kernels_gaussian_gm7();
+const FamilyKernels& kernels_oscillatory_gm7();
+const FamilyKernels& kernels_corner_peak_gm7();
+const FamilyKernels& kernels_c0_gm7();
+const FamilyKernels& kernels_discontinuous_gm7();
+const FamilyKernels& kernels_box_power_gm7();
 
 constexpr int kSplitThreads = 256;
 constexpr int kItemsPerThread = 8;

@@ -1,5 +1,5 @@
-// Degree-9 fully symmetric cubature rule with four null rules, generated on
-// the host in long double at library load.
+// Degree-9 fully symmetric cubature rule with four null rules (and the
+// Genz-Malik degree-7 variant), generated on the host in long double.
 //
 // The paper fixes the rule family (Sec. 2.1: the Genz-Malik rules used by
 // Cuhre, 2^n + Theta(n^3) points; Sec. 3.2: four extra rules whose
@@ -176,24 +176,20 @@ int num_points(int n) {
   return (int)t;
 }
 
-bool build_rule(int n, RuleTable* out, double* max_residual) {
-  if (n < 2 || n > kMaxDim) return false;
-  const Lambdas L = make_lambdas();
-  std::vector<int> gens;
-  for (int g = 0; g < kNumGen; ++g) if (orbit_count(n, g) > 0) gens.push_back(g);
+// Weights of the orbits `gens` solving the moment equations of degree
+// <= 2 half_degree + 1: least squares by Householder QR (no squaring of the
+// condition number), then one refinement step on the residual of the
+// original system.  Returns false if the system is rank deficient.
+static bool solve_weights(int n, const std::vector<int>& gens, int half_degree, const Lambdas& L, std::vector<ld>& w,
+                   ld* maxres_out) {
   const int G = (int)gens.size();
-
-  // basic rule: the degree-9 moment equations
-  std::vector<Part> rows = moment_set(n, 4);
+  std::vector<Part> rows = moment_set(n, half_degree);
   const int R = (int)rows.size();
   std::vector<ld> S(R * G), b(R);
   for (int r = 0; r < R; ++r) {
     for (int c = 0; c < G; ++c) S[r * G + c] = orbit_moment(n, gens[c], rows[r], L);
     b[r] = exact_moment(rows[r]);
   }
-  // least squares by Householder QR (no squaring of the condition number),
-  // then one refinement step on the residual of the original system
-  std::vector<ld> w;
   if (!lsq_qr(S, b, R, G, w)) return false;
   {
     std::vector<ld> res(R), dw;
@@ -211,6 +207,63 @@ bool build_rule(int n, RuleTable* out, double* max_residual) {
     for (int c = 0; c < G; ++c) s += S[r * G + c] * w[c];
     maxres = fmaxl(maxres, fabsl(s) / b[r]);
   }
+  if (maxres_out) *maxres_out = maxres;
+  return true;
+}
+
+// Genz-Malik degree-7 rule with its embedded degree-5 rule, placed on the
+// degree-9 generator slots that have its structure: centre; one axis at
+// sqrt(9/70) (slot lp, the small fourth-difference radius); one axis at
+// sqrt(9/10) (slot l2, the large one); two axes at sqrt(9/10) (slot l1l1,
+// so l1 = 9/10); every axis at sqrt(9/19) (slot l0).  Weights from the moment
+// equations of degree <= 7 (all five orbits) and <= 5 (the first four);
+// null rule 1 = w7 - w5, the rule's error |R7 - R5|; null rules 2..4 unused.
+static bool build_rule_gm7(int n, RuleTable* out, double* max_residual) {
+  Lambdas L;
+  L.l1 = L.l2 = L.l3 = 9.0L / 10.0L;
+  L.lp = 9.0L / 70.0L;
+  L.l0 = 9.0L / 19.0L;
+  const std::vector<int> g7 = {kGenCentre, kGenLp, kGenL2, kGenL1L1, kGenL0All};
+  const std::vector<int> g5 = {kGenCentre, kGenLp, kGenL2, kGenL1L1};
+  std::vector<ld> w7, w5;
+  ld r7 = 0.0L, r5 = 0.0L;
+  if (!solve_weights(n, g7, 3, L, w7, &r7) || !solve_weights(n, g5, 2, L, w5, &r5)) return false;
+  if (max_residual) *max_residual = (double)fmaxl(r7, r5);
+  w5.push_back(0.0L);
+  std::memset(out, 0, sizeof(*out));
+  out->n = n;
+  out->degree = 7;
+  out->radius[0] = (double)sqrtl(L.l1);
+  out->radius[1] = (double)sqrtl(L.l2);
+  out->radius[2] = (double)sqrtl(L.l3);
+  out->radius[3] = (double)sqrtl(L.lp);
+  out->radius[4] = (double)sqrtl(L.l0);
+  out->q = (double)(L.lp / L.l2);
+  int64_t pts = 0;
+  for (int c = 0; c < 5; ++c) {
+    const int g = g7[c];
+    out->count[g] = orbit_count(n, g);
+    pts += out->count[g];
+    out->w[g][0] = (double)w7[c];
+    out->w[g][1] = (double)(w7[c] - w5[c]);
+  }
+  out->num_points = (int)pts;
+  return true;
+}
+
+bool build_rule(int n, int degree, RuleTable* out, double* max_residual) {
+  if (n < 2 || n > kMaxDim) return false;
+  if (degree == 7) return build_rule_gm7(n, out, max_residual);
+  if (degree != 9) return false;
+  const Lambdas L = make_lambdas();
+  std::vector<int> gens;
+  for (int g = 0; g < kNumGen; ++g) if (orbit_count(n, g) > 0) gens.push_back(g);
+  const int G = (int)gens.size();
+
+  // basic rule: the degree-9 moment equations
+  std::vector<ld> w;
+  ld maxres = 0.0L;
+  if (!solve_weights(n, gens, 4, L, w, &maxres)) return false;
   if (max_residual) *max_residual = (double)maxres;
 
   // count-weighted inner product <a, c> = sum_g cnt_g a_g c_g
@@ -265,6 +318,7 @@ bool build_rule(int n, RuleTable* out, double* max_residual) {
 
   std::memset(out, 0, sizeof(*out));
   out->n = n;
+  out->degree = 9;
   out->radius[0] = (double)sqrtl(L.l1);
   out->radius[1] = (double)sqrtl(L.l2);
   out->radius[2] = (double)sqrtl(L.l3);

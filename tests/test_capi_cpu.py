@@ -65,6 +65,30 @@ def test_rule_tables_match_oracle(lib, n):
         assert cnt[7] == 0 and np.all(w[7] == 0)
 
 
+@pytest.mark.parametrize("n", range(2, 9))
+def test_gm7_rule_tables_match_oracle(lib, n):
+    """The library's degree-7 tables (host long double, QR on closed-form
+    orbit moments) against the oracle's exact rationals, slot by slot: the
+    Genz-Malik orbits sit on the centre, lp (sqrt(9/70)), l2 (sqrt(9/10)),
+    l1l1 (sqrt(9/10) pairs) and l0^n (sqrt(9/19)) slots; column 1 is w7 - w5."""
+    from oracle import rule_gm7
+    npts, rad, w, cnt = pg.pagani_rule_tables(n, rule_degree=7)
+    assert npts == rule_gm7.num_points(n) == 2 ** n + 2 * n * n + 2 * n + 1
+    gen, wts = rule_gm7.rule_tables(n)
+    _, counts, _, _, _ = rule_gm7.exact_rule(n)
+    slots = [0, 4, 2, 5, 8]
+    a, b, q = rule_gm7.fourth_difference_offsets()
+    assert abs(rad[3] - a) <= 1e-16 and abs(rad[1] - b) <= 2e-16 and abs(rad[0] - b) <= 2e-16
+    assert abs(rad[4] - gen[4][0]) <= 2e-16
+    for gi, g in enumerate(slots):
+        assert cnt[g] == counts[gi]
+        for k in (0, 1):
+            colscale = max(abs(r[k]) for r in wts)
+            assert abs(w[g, k] - wts[gi][k]) <= 1e-15 * colscale, (n, g, k, w[g, k], wts[gi][k])
+    others = [g for g in range(9) if g not in slots]
+    assert np.all(cnt[others] == 0) and np.all(w[others] == 0) and np.all(w[:, 2:] == 0)
+
+
 def test_host_argument_checks(lib):
     with pytest.raises(pg.PaganiError):
         pg.pagani_integrate(1, 0, [1.0, 0.5], 1e-3)
@@ -78,6 +102,12 @@ def test_host_argument_checks(lib):
         pg.pagani_integrate(3, 0, [7.0] * 6, 1e-3, max_regions=100)  # below the initial split
     with pytest.raises(pg.PaganiError, match="-8"):
         pg.pagani_integrate_ex(3, 0, [7.0] * 6, 1e-3, heuristic_filter=4)  # trigger modes are 0..3
+    with pytest.raises(pg.PaganiError, match="-8"):
+        pg.pagani_integrate_ex(3, 0, [7.0] * 6, 1e-3, rule_degree=8)       # rules are 9 and 7
+    with pytest.raises(pg.PaganiError, match="-8"):
+        pg.pagani_integrate_ex(3, 0, [7.0] * 6, 1e-3, rule_degree=7, keep_leaves=1)
+    with pytest.raises(pg.PaganiError):
+        pg.pagani_rule_tables(3, rule_degree=5)
     with pytest.raises(pg.PaganiError, match="-8"):
         pg.pagani_integrate_ex(3, 0, [7.0] * 6, 1e-3, bounds=([0.0, 0.5, 0.0], [1.0, 0.5, 1.0]))  # empty box
     with pytest.raises(pg.PaganiError, match="-8"):

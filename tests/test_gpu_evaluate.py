@@ -8,7 +8,7 @@ import pytest
 from oracle import capi as oracle
 from paper_2104_06494_gb300.workloads import draw_params, random_dyadic_regions, SplitMix64
 from tests.conftest import has_gpu
-from oracle import rule as orule
+from oracle import rule as orule, rule_gm7
 from tests.gpu_util import EPS, null_error, sibling_regions, sum_tolerance, value_condition
 
 pytestmark = pytest.mark.gpu
@@ -26,26 +26,27 @@ def torch_cuda():
     return torch
 
 
-def oracle_side(family, n, params, lo, wd):
-    Vo, Eo, Ko, Do = oracle.evaluate(family, n, params, lo, wd, diag=True)
+def oracle_side(family, n, params, lo, wd, degree=9):
+    Vo, Eo, Ko, Do = oracle.evaluate(family, n, params, lo, wd, diag=True, degree=degree)
     k_rel, k_abs = value_condition(family, n, params, lo, wd)
-    _, wts = orule.rule_tables(n)
-    _, counts, _, _, _ = orule.exact_rule(n)
+    rmod = orule if degree == 9 else rule_gm7
+    _, wts = rmod.rule_tables(n)
+    _, counts, _, _, _ = rmod.exact_rule(n)
     W = np.abs(np.array(wts)).T @ np.array(counts, dtype=np.float64)   # sum_g |w_gk| cnt_g, k = 0..4
     vol = np.prod(np.atleast_2d(wd), axis=1)
     return dict(V=Vo, E=Eo, K=Ko, N=Do[:, 0:4], Nabs=Do[:, 4:8], Vabs=Do[:, 8], Dj=Do[:, 9:9 + n],
                 Dabs=Do[:, 9 + n:9 + 2 * n], floor=Do[:, 9 + 2 * n:13 + 2 * n], k_rel=k_rel, k_abs=k_abs,
-                W=W, vol=vol, width=np.atleast_2d(wd))
+                W=W, vol=vol, width=np.atleast_2d(wd), degree=degree)
 
 
-def run_both(torch, family, n, params, lo, wd):
+def run_both(torch, family, n, params, lo, wd, degree=9):
     import paper_2104_06494_gb300 as pg
     lo_t = torch.tensor(lo.T.copy(), dtype=torch.float64, device="cuda")
     wd_t = torch.tensor(wd.T.copy(), dtype=torch.float64, device="cuda")
-    V, E, K, D = pg.pagani_evaluate(n, family, params, lo_t, wd_t, diag=True)
+    V, E, K, D = pg.pagani_evaluate(n, family, params, lo_t, wd_t, diag=True, rule_degree=degree)
     torch.cuda.synchronize()
     g = dict(V=V.cpu().numpy(), E=E.cpu().numpy(), K=K.cpu().numpy(), D=D.cpu().numpy())
-    return g, oracle_side(family, n, params, lo, wd)
+    return g, oracle_side(family, n, params, lo, wd, degree)
 
 
 def check_parity(g, o, n):
@@ -63,16 +64,25 @@ def check_parity(g, o, n):
     # the floors are the same rounding scale on both sides
     assert np.all(np.abs(Fg - o["floor"]) <= 1e-6 * o["floor"] + tolN)
     # the kernel's E follows the error formula applied to its own floored N_k
+    # (the degree-7 rule: E = |R7 - R5| = the floored N_1 itself)
     for i in range(m):
         nu = [0.0 if Ng[i, k] <= Fg[i, k] else Ng[i, k] for k in range(4)]
-        ref = null_error(*nu)
+        ref = null_error(*nu) if o["degree"] == 9 else nu[0]
         assert abs(g["E"][i] - ref) <= 1e-13 * abs(ref) + 1e-300, (i, g["E"][i], ref)
+    if o["degree"] == 7:
+        assert np.all(Ng[:, 1:] == 0) and np.all(Fg[:, 1:] == 0)
     # and equals the oracle's E within the perturbation bound of the formula:
     # with N_k known to relative delta, E is known to about 8 delta, except
     # next to the jump at r = 1 or a floor
     checked = 0
     for i in range(m):
         Nk = o["N"][i]
+        if o["degree"] == 7:
+            if Nk[0] <= 4 * o["floor"][i][0] + 4 * tolN[i][0]:
+                continue
+            checked += 1
+            assert abs(g["E"][i] - o["E"][i]) <= tolN[i][0] + 1e-12 * o["E"][i], (i, g["E"][i], o["E"][i])
+            continue
         if np.any(Nk <= 4 * o["floor"][i] + 4 * tolN[i]):
             continue
         delta = float(np.max(tolN[i] / Nk))
@@ -82,7 +92,7 @@ def check_parity(g, o, n):
         checked += 1
         assert abs(g["E"][i] - o["E"][i]) <= (8 * delta + 1e-12) * o["E"][i], (i, g["E"][i], o["E"][i], delta)
     Dg = g["D"][8:8 + n].T
-    q = 0.0625 / 0.16488242915640136
+    q = 0.0625 / 0.16488242915640136 if o["degree"] == 9 else 1 / 7
     tolD = 1e-12 * o["Dj"] + (2 * n + 16 + kr[:, None]) * EPS * o["Dabs"] + (4 + 4 * q) * ka[:, None] * EPS
     assert np.all(np.abs(Dg - o["Dj"]) <= tolD), np.max(np.abs(Dg - o["Dj"]) / tolD)
     # split axis: equal, or a valid choice under the rounding of D and of
@@ -156,3 +166,24 @@ def test_evaluate_large_list_sampled(torch_cuda, family, n):
     g = dict(V=V.cpu().numpy()[idx], E=E.cpu().numpy()[idx], K=K.cpu().numpy()[idx], D=D.cpu().numpy()[:, idx])
     lo_s, wd_s = lo.T.numpy()[idx], wd.T.numpy()[idx]
     check_parity(g, oracle_side(family, n, params, lo_s, wd_s), n)
+
+
+@pytest.mark.parametrize("family", FAMS)
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+def test_evaluate_gm7_random_boxes(torch_cuda, family, n):
+    """The Genz-Malik degree-7 variant: V, the difference |R7 - R5|, the
+    fourth differences at its radii and the split axis against the oracle."""
+    m = 301 if n < 7 else 97
+    params = draw_params(family, n, 5000 + 10 * family + n)
+    lo, wd = random_dyadic_regions(n, m, 97 + n, max_level=8)
+    g, o = run_both(torch_cuda, family, n, params, np.array(lo), np.array(wd), degree=7)
+    check_parity(g, o, n)
+
+
+@pytest.mark.parametrize("family", [1, 2])
+def test_evaluate_gm7_sibling_pairs(torch_cuda, family):
+    n = 6
+    params = draw_params(family, n, 5100 + family)
+    lo, wd = sibling_regions(n, 128, 11)
+    g, o = run_both(torch_cuda, family, n, params, lo, wd, degree=7)
+    check_parity(g, o, n)

@@ -117,6 +117,39 @@ def test_bounds_argument_errors(pg):
         pg.pagani_integrate_ex(3, 1, draw_params(1, 3, 1), 1e-3, bounds=([0, 0, 0], [1, np.inf, 1]))
 
 
+GM7_CASES = [(0, 3, 1e-6), (1, 4, 1e-5), (1, 6, 1e-4), (2, 3, 1e-7), (3, 5, 1e-6), (4, 3, 1e-4), (5, 3, 1e-3),
+             (6, 5, 1e-9)]
+
+
+@pytest.mark.parametrize("family,n,tau", GM7_CASES)
+def test_gm7_loop_matches_oracle(pg, family, n, tau):
+    """The whole loop with the Genz-Malik degree-7 rule (error |R7 - R5|):
+    equal region sets, traces and estimates, and the closed form inside the
+    error estimate where the oracle's is (all but the discontinuous case)."""
+    params = draw_params(family, n, 800 + 13 * family + n)
+    relerr = 0 if family == 2 else 1
+    o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, relerr_filter=relerr, degree=7)
+    g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=4_000_000, relerr_filter=relerr, trace=True,
+                               rule_degree=7)
+    compare_runs(g, o)
+    ex = cf.closed_form(family, n, params)
+    if ex is not None and family != 5:
+        assert abs(g.estimate - ex) <= g.errorest
+
+
+def test_gm7_uses_fewer_points_per_region(pg):
+    """Same integral, both rules: the degree-7 run evaluates
+    2^n + 2n^2 + 2n + 1 points per region (401 at n = 8, against 1105) and
+    both estimates hold the closed form within their error estimates."""
+    n = 8
+    params = draw_params(1, n, 8080)
+    ex = cf.closed_form(1, n, params)
+    r9 = pg.pagani_integrate_ex(n, 1, params, 1e-3, max_regions=1 << 24)
+    r7 = pg.pagani_integrate_ex(n, 1, params, 1e-3, max_regions=1 << 24, rule_degree=7)
+    for r in (r9, r7):
+        assert r.status in (0, 3) and abs(r.estimate - ex) <= r.errorest
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_filter_modes_match_oracle(pg, mode):
     """The filtering ablation (Sec. 4.2): Threshold-Classify off (0), on with

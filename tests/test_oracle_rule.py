@@ -125,3 +125,67 @@ def test_lambdas_match_construction():
     assert abs(lam["l1"] - 4 / (15 - 5 / 0.4707)) < 1e-15
     # every generator radius lies inside the reference cube
     assert all(0 < v < 1 for v in lam.values())
+
+
+# ------------------------------------------------ the degree-7 rule variant --
+from oracle import rule_gm7  # noqa: E402
+
+
+@pytest.mark.parametrize("n", range(2, 9))
+def test_gm7_point_count_and_closed_form_weights(n):
+    """2^n + 2n^2 + 2n + 1 points; the weights solved from the moment
+    equations equal Genz and Malik's closed forms in n (degree 7:
+    (12824 - 9120 n + 400 n^2)/19683, 980/6561, (1820 - 400 n)/19683,
+    200/19683, 6859/19683/2^n; embedded degree 5: (729 - 950 n + 50 n^2)/729,
+    245/486, (265 - 100 n)/1458, 25/729)."""
+    assert rule_gm7.num_points(n) == 2 ** n + 2 * n * n + 2 * n + 1
+    _, cnt, w7, w5, u = rule_gm7.exact_rule(n)
+    F = Fraction
+    assert w7 == [F(12824 - 9120 * n + 400 * n * n, 19683), F(980, 6561), F(1820 - 400 * n, 19683),
+                  F(200, 19683), F(6859, 19683 * 2 ** n)]
+    assert w5 == [F(729 - 950 * n + 50 * n * n, 729), F(245, 486), F(265 - 100 * n, 1458), F(25, 729), F(0)]
+    assert sum(c * x for c, x in zip(cnt, w7)) == 1 and sum(c * x for c, x in zip(cnt, w5)) == 1
+
+
+@pytest.mark.parametrize("n", range(2, 9))
+def test_gm7_exact_for_degree_le_7_and_error_vanishes_le_5(n):
+    rng = SplitMix64(177 + n)
+    lo = np.array([rng.uniform(0.0, 0.5) for _ in range(n)])
+    wd = np.array([rng.uniform(0.1, 0.5) for _ in range(n)])
+    for p in exponent_tuples(n, 7, rng, 80):
+        V, E, K, D = capi.evaluate(MONOMIAL, n, list(p), lo[None, :], wd[None, :], diag=True, degree=7)
+        ex = box_monomial_integral(p, lo, lo + wd)
+        assert abs(V[0] - ex) <= 1e-13 * abs(ex), (p, V[0], ex)
+        if sum(p) <= 5:
+            # R7 - R5 integrates degree <= 5 exactly to zero (rounding only)
+            assert D[0, 0] <= 64 * rule_gm7.num_points(n) * 2.0 ** -53 * D[0, 4] + 1e-300
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+def test_gm7_not_exact_for_degree_8_and_error_is_the_difference(n):
+    lo, wd = np.zeros(n), np.ones(n)
+    p = [8] + [0] * (n - 1)
+    V, E, K, D = capi.evaluate(MONOMIAL, n, p, lo[None, :], wd[None, :], diag=True, degree=7)
+    assert abs(V[0] - 1 / 9) > 1e-6
+    # E = |R7 - R5| for x_1^8 on [0, 1]^n, by hand: the l2 and l3 axis points
+    # carry the only non-zero values off the centre, x = (1 + g)/2
+    a, b = math.sqrt(9 / 70), math.sqrt(9 / 10)
+    _, _, w7, w5, _ = rule_gm7.exact_rule(n)
+    f = lambda g: ((1 + g) / 2) ** 8
+    sums = [f(0.0), f(a) + f(-a) + (n - 1) * 2 * f(0.0), f(b) + f(-b) + (n - 1) * 2 * f(0.0)]
+    pair = 2 * (n - 1) * (f(b) + f(-b)) + 4 * (n - 1) * (n - 2) // 2 * f(0.0)
+    vert = 2 ** (n - 1) * (f(math.sqrt(9 / 19)) + f(-math.sqrt(9 / 19)))
+    S = sums + [pair, vert]
+    r7 = sum(float(w) * s for w, s in zip(w7, S))
+    r5 = sum(float(w) * s for w, s in zip(w5, S))
+    assert abs(V[0] - r7) <= 1e-14
+    assert abs(E[0] - abs(r7 - r5)) <= 1e-14
+
+
+def test_gm7_split_axis_uses_its_radii():
+    # f = x_0^4 on [0,1]^2: D_0 = 2 a^2 h^4 |a^2 - b^2| with a^2 = 9/70,
+    # b^2 = 9/10, h = 1/2 (second differences 12 c^2 r^2 h^2 + 2 r^4 h^4)
+    V, E, K, D = capi.evaluate(MONOMIAL, 2, [4, 0], [[0.0, 0.0]], [[1.0, 1.0]], diag=True, degree=7)
+    a2, b2, h = 9 / 70, 9 / 10, 0.5
+    assert abs(D[0, 9] - 2 * a2 * h ** 4 * abs(a2 - b2)) < 1e-16
+    assert D[0, 10] == 0.0 and K[0] == 0
