@@ -343,7 +343,8 @@ def main():
     for w in ws:
         r = run(w, use_graph=0, trace=True)
         work = roofline.evaluate_work(w.family, w.dim, r.trace["s"])
-        roof_parts.append({"name": w.name, "eval_ms": r.eval_ms, "launches": r.eval_launches, **work})
+        roof_parts.append({"name": w.name, "eval_ms": r.eval_ms, "launches": r.eval_launches,
+                           "phase_ms": list(r.phase_ms), **work})
     fl = sum(p["flops"] for p in roof_parts)
     ins = sum(p["inst"] for p in roof_parts)
     ems = sum(p["eval_ms"] for p in roof_parts)
@@ -450,6 +451,14 @@ def main():
                              {k: v / nl for k, v in calls.items()},
                          "measured_rates_gps": {k: peaks[k] for k in ("exp_gps", "sincos_gps", "div_gps")},
                          "parts": [{k: p[k] for k in ("name", "eval_ms", "launches", "flops")} for p in roof_parts]},
+            # per-phase device time of the same host-driven pass (the
+            # performance breakdown of Sec. 4.2: evaluate / threshold search /
+            # post-processing / filter and split)
+            "breakdown": {p["name"]: {"evaluate_ms": p["eval_ms"], "cache_fill_ms": p["phase_ms"][0],
+                                      "threshold_probe_ms": p["phase_ms"][1], "sums_count_ms": p["phase_ms"][2],
+                                      "filter_split_ms": p["phase_ms"][3],
+                                      "evaluate_share": p["eval_ms"] / (p["eval_ms"] + sum(p["phase_ms"]))}
+                          for p in roof_parts},
             "clocks": clk,
             "gpu_launches": launches,
         }

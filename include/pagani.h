@@ -86,9 +86,17 @@ typedef struct {
   int64_t h2d_bytes;      /* host-to-device bytes copied by this call        */
   int64_t d2h_bytes;      /* device-to-host bytes copied by this call        */
   double active_volume;   /* volume of the regions of the last iteration; with
-                             finished_volume it sums to 1 (dyadic boxes)    */
+                             finished_volume it sums to the volume of the
+                             integration region (dyadic boxes)              */
   int64_t n_leaves;       /* with keep_leaves: boxes of the converged leaf set
                              (see pagani_leaves); -1 otherwise             */
+  double phase_ms[4];     /* host-driven loop only (use_graph = 0): summed device
+                             time, CUDA events on the launching stream, of the
+                             other phases of Algorithm 2 (the performance
+                             breakdown of Sec. 4.2): [0] factor-cache fill,
+                             [1] Threshold-Classify probes, [2] finished sums
+                             and survivor count, [3] filter and split; -1
+                             otherwise                                       */
 } pagani_result;
 
 typedef struct {

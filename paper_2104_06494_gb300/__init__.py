@@ -35,7 +35,8 @@ class Result(ctypes.Structure):
                 ("iterations", ctypes.c_int32), ("n_regions", ctypes.c_int64), ("n_active_last", ctypes.c_int64),
                 ("finished_volume", ctypes.c_double), ("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int32), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
-                ("active_volume", ctypes.c_double), ("n_leaves", ctypes.c_int64)]
+                ("active_volume", ctypes.c_double), ("n_leaves", ctypes.c_int64),
+                ("phase_ms", ctypes.c_double * 4)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -168,6 +169,7 @@ class Integration:
     trace: np.ndarray | None = None
     active_volume: float = 0.0
     n_leaves: int = -1
+    phase_ms: tuple = (-1.0, -1.0, -1.0, -1.0)   # fill, probe, count, split (host-driven loop)
 
     @property
     def status_name(self) -> str:
@@ -177,7 +179,7 @@ class Integration:
 def _integration(r: Result, trace=None) -> Integration:
     return Integration(r.estimate, r.errorest, r.status, r.iterations, r.n_regions, r.n_active_last,
                        r.finished_volume, r.eval_ms, r.eval_launches, r.kernel_launches, r.h2d_bytes, r.d2h_bytes,
-                       trace, r.active_volume, r.n_leaves)
+                       trace, r.active_volume, r.n_leaves, tuple(r.phase_ms))
 
 
 def pagani_integrate(dim: int, integrand_id: int, params, epsrel: float, epsabs: float = 1e-20,

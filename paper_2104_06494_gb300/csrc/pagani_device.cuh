@@ -161,6 +161,75 @@ __device__ __forceinline__ NSum nsum_block_combine(NSum a, NSum* sh) {
   return a;  // valid on thread 0
 }
 
+// K compensated sums reduced over the block at once.  A dependent FP64
+// operation takes about 64 cycles on this GPU, so the K shuffle trees run
+// interleaved, and the per-warp results are combined by a second shuffle tree
+// in warp 0 (log2 of the warp count levels) rather than by one thread in
+// sequence.  Fixed tree order: deterministic.  sh holds K * THREADS/32 sums;
+// the result is valid on thread 0.
+template <int THREADS, int K>
+__device__ __forceinline__ void nsum_block_reduce(NSum (&a)[K], NSum* sh) {
+  constexpr int NW = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    NSum b[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) b[k] = shfl_down_nsum(a[k], off);
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = ncomb(a[k], b[k]);
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * NW + warp] = a[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      a[k].s = lane < NW ? sh[k * NW + lane].s : 0.0;
+      a[k].c = lane < NW ? sh[k * NW + lane].c : 0.0;
+    }
+#pragma unroll
+    for (int off = NW / 2; off > 0; off >>= 1) {
+      NSum b[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) b[k] = shfl_down_nsum(a[k], off);
+#pragma unroll
+      for (int k = 0; k < K; ++k) a[k] = ncomb(a[k], b[k]);
+    }
+  }
+}
+
+// Exclusive scan of one 64-bit count per thread across the block (thread
+// order), by warp shuffles; *total receives the sum (all threads).
+template <int THREADS>
+__device__ __forceinline__ long long block_exclusive_scan(long long x, long long* sh, long long* total) {
+  constexpr int NW = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long inc = x;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    long long t = lane < NW ? sh[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < NW; off <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, t, off);
+      if (lane >= off) t += y;
+    }
+    if (lane < NW) sh[NW + lane] = t;  // inclusive warp offsets
+  }
+  __syncthreads();
+  *total = sh[2 * NW - 1];
+  return inc - x + (warp > 0 ? sh[NW + warp - 1] : 0);
+}
+
 __device__ __forceinline__ void set_cond(int use_graph, cudaGraphConditionalHandle h, unsigned int v) {
   if (use_graph) cudaGraphSetConditional(h, v);
 }

@@ -591,19 +591,26 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     if (!isfinite(VL) || !isfinite(VR) || !isfinite(EL) || !isfinite(ER)) nonfinite = 1;
   }
 
-  // block reduction of the partials (fixed tree order: deterministic)
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    sv = ncomb(sv, shfl_down_nsum(sv, off));
-    se = ncomb(se, shfl_down_nsum(se, off));
-    svol = ncomb(svol, shfl_down_nsum(svol, off));
-    emin = fmin(emin, __shfl_down_sync(0xffffffffu, emin, off));
-    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, off));
-    nrel += __shfl_down_sync(0xffffffffu, nrel, off);
-    nonfinite |= __shfl_down_sync(0xffffffffu, nonfinite, off);
-  }
+  // block reduction of the partials (fixed tree order: deterministic).  A
+  // block without pairs holds the identity: it skips the FP64 shuffles (each
+  // warp-wide FP64 instruction costs the SM's FP64 pipe 16 cycles), and the
+  // last block combines only the partials of blocks that had pairs, which
+  // leaves every sum bit for bit unchanged
+  const int64_t nparts_eval = (npairs + THREADS - 1) / THREADS < (int64_t)gridDim.x
+                                  ? (npairs + THREADS - 1) / THREADS
+                                  : (int64_t)gridDim.x;
   __shared__ EvalPartial wp[THREADS / 32];
-  {
+  if ((int64_t)blockIdx.x < nparts_eval) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sv = ncomb(sv, shfl_down_nsum(sv, off));
+      se = ncomb(se, shfl_down_nsum(se, off));
+      svol = ncomb(svol, shfl_down_nsum(svol, off));
+      emin = fmin(emin, __shfl_down_sync(0xffffffffu, emin, off));
+      emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, off));
+      nrel += __shfl_down_sync(0xffffffffu, nrel, off);
+      nonfinite |= __shfl_down_sync(0xffffffffu, nonfinite, off);
+    }
     EvalPartial mine;
     mine.v = sv;
     mine.e = se;
@@ -624,7 +631,7 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     }
   }
   if (!last_block_arrived(&c.ticket_eval)) return;
-  const EvalPartial tot = eval_reduce_partials<THREADS>(A.eval_part, gridDim.x, wp);
+  const EvalPartial tot = eval_reduce_partials<THREADS>(A.eval_part, (int)nparts_eval, wp);
   if (threadIdx.x == 0) {
     int search = finalize_iteration_head(c, nval(tot.v), nval(tot.e), tot.n_rel, tot.emin, tot.emax,
                                          tot.nonfinite, A.trace, A.trace_cap, nval(tot.vol));

@@ -116,23 +116,30 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   }
   __shared__ NSum shn[THREADS / 32];
   __shared__ long long shl[THREADS / 32];
-  NSum bs = block_nsum<THREADS>(sa, shn);
-  long long bn = block_sum_ll<THREADS>(na, shl);
-  if (threadIdx.x == 0) {
-    A.probe_part[blockIdx.x].ea = bs;
-    A.probe_part[blockIdx.x].n_active = bn;
+  // blocks without regions hold exact zeros and skip the FP64 shuffles; the
+  // last block reads only the partials that can be non-zero
+  const int64_t nblk = (s + THREADS - 1) / THREADS;
+  const int64_t nparts = nblk < (int64_t)gridDim.x ? nblk : (int64_t)gridDim.x;
+  if ((int64_t)blockIdx.x < nparts) {
+    NSum bs[1] = {sa};
+    nsum_block_reduce<THREADS, 1>(bs, shn);
+    long long bn = block_sum_ll<THREADS>(na, shl);
+    if (threadIdx.x == 0) {
+      A.probe_part[blockIdx.x].ea = bs[0];
+      A.probe_part[blockIdx.x].n_active = bn;
+    }
   }
   if (!last_block_arrived(&c.ticket_probe)) return;
-  NSum pa = {0.0, 0.0};
+  NSum pa[1] = {{0.0, 0.0}};
   long long pn = 0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS) {
-    pa = ncomb(pa, A.probe_part[b].ea);
+  for (int64_t b = threadIdx.x; b < nparts; b += THREADS) {
+    pa[0] = ncomb(pa[0], A.probe_part[b].ea);
     pn += A.probe_part[b].n_active;
   }
-  const NSum tot = nsum_block_combine<THREADS>(pa, shn);
+  nsum_block_reduce<THREADS, 1>(pa, shn);
   const long long n = block_sum_ll<THREADS>(pn, shl);
   if (threadIdx.x == 0) {
-    const int cont = threshold_step(c, n, nval(tot));
+    const int cont = threshold_step(c, n, nval(pa[0]));
     c.search_cont = cont;
     set_cond(A.use_graph, A.h_probe, (unsigned)cont);
     __threadfence();
@@ -159,20 +166,31 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   const double* __restrict__ V = A.pool.V;
   const double* __restrict__ E = A.pool.E;
   const int64_t ntiles = (s + TILE - 1) / TILE;
-  __shared__ long long shl[THREADS / 32];
-  __shared__ NSum shn[THREADS / 32];
+  __shared__ long long shl[2 * (THREADS / 32)];
+  __shared__ NSum shn[3 * (THREADS / 32)];
   // each thread sums its ITEMS regions of a tile plainly (relative error at
   // most (ITEMS - 1) u) and adds that partial into Neumaier accumulators, so
   // the sums stay compensated across all partials at a third of the FP64 work
-  NSum va = {0.0, 0.0}, ea = {0.0, 0.0}, fv = {0.0, 0.0};
+  NSum acc3[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};  // V.A, E.A, finished volume
+  NSum& va = acc3[0];
+  NSum& ea = acc3[1];
+  NSum& fv = acc3[2];
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     long long cnt = 0;
     double tv = 0.0, te = 0.0, tf = 0.0;
+    // every item's V and E are requested before the first is used
+    double vv[ITEMS], ee[ITEMS];
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
+      vv[r] = i < s ? V[i] : 0.0;
+      ee[r] = i < s ? E[i] : 0.0;
+    }
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
       if (i < s) {
-        const double v = V[i], e = E[i];
+        const double v = vv[r], e = ee[r];
         if (final_active(v, e, c)) {
           ++cnt;
           tv += v;
@@ -190,53 +208,43 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     const long long tc = block_sum_ll<THREADS>(cnt, shl);
     if (threadIdx.x == 0) A.pool.tile_count[tile] = tc;
   }
-  NSum bva = block_nsum<THREADS>(va, shn);
-  NSum bea = block_nsum<THREADS>(ea, shn);
-  NSum bfv = block_nsum<THREADS>(fv, shn);
-  if (threadIdx.x == 0) {
-    A.count_part[blockIdx.x].va = bva;
-    A.count_part[blockIdx.x].ea = bea;
-    A.count_part[blockIdx.x].finvol = bfv;
+  // a block without tiles holds exact zeros: it skips the FP64 shuffles (a
+  // warp-wide FP64 instruction costs the SM's FP64 pipe 16 cycles) and the
+  // last block reads only the partials of blocks that had tiles, which
+  // leaves every sum bit for bit unchanged
+  const int64_t nparts = ntiles < (int64_t)gridDim.x ? ntiles : (int64_t)gridDim.x;
+  if ((int64_t)blockIdx.x < nparts) {
+    nsum_block_reduce<THREADS, 3>(acc3, shn);
+    if (threadIdx.x == 0) {
+      A.count_part[blockIdx.x].va = va;
+      A.count_part[blockIdx.x].ea = ea;
+      A.count_part[blockIdx.x].finvol = fv;
+    }
   }
   if (!last_block_arrived(&c.ticket_count)) return;
 
-  // exclusive scan of the tile counts (each thread a contiguous chunk)
-  __shared__ long long chunk_sum[THREADS];
+  // exclusive scan of the tile counts: each thread a contiguous chunk, the
+  // chunk sums scanned by warp shuffles
   const int64_t per = (ntiles + THREADS - 1) / THREADS;
   const int64_t t0 = threadIdx.x * per, t1 = t0 + per < ntiles ? t0 + per : ntiles;
   long long acc = 0;
   for (int64_t t = t0; t < t1; ++t) acc += A.pool.tile_count[t];
-  chunk_sum[threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long run = 0;
-    for (int w = 0; w < THREADS; ++w) {
-      const long long x = chunk_sum[w];
-      chunk_sum[w] = run;
-      run += x;
-    }
-  }
-  __syncthreads();
-  long long run = chunk_sum[threadIdx.x];
+  long long n_surv = 0;
+  long long run = block_exclusive_scan<THREADS>(acc, shl, &n_surv);
   for (int64_t t = t0; t < t1; ++t) {
     const long long x = A.pool.tile_count[t];
     A.pool.tile_offset[t] = run;
     run += x;
   }
-  __shared__ long long total_surv;
-  if (threadIdx.x == THREADS - 1) total_surv = run;  // end of the last chunk
-  NSum pva = {0.0, 0.0}, pea = {0.0, 0.0}, pfv = {0.0, 0.0};
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS) {
-    pva = ncomb(pva, A.count_part[b].va);
-    pea = ncomb(pea, A.count_part[b].ea);
-    pfv = ncomb(pfv, A.count_part[b].finvol);
+  NSum p3[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+  for (int64_t b = threadIdx.x; b < nparts; b += THREADS) {
+    p3[0] = ncomb(p3[0], A.count_part[b].va);
+    p3[1] = ncomb(p3[1], A.count_part[b].ea);
+    p3[2] = ncomb(p3[2], A.count_part[b].finvol);
   }
-  const NSum tva = nsum_block_combine<THREADS>(pva, shn);
-  const NSum tea = nsum_block_combine<THREADS>(pea, shn);
-  const NSum tfv = nsum_block_combine<THREADS>(pfv, shn);
-  __syncthreads();
+  nsum_block_reduce<THREADS, 3>(p3, shn);
   if (threadIdx.x != 0) return;
-  const long long n_surv = total_surv;
+  const NSum tva = p3[0], tea = p3[1], tfv = p3[2];
   c.n_surv = n_surv;
   const bool tr_ok = c.trace_on && c.it - 1 < A.trace_cap;
   TraceRec* tr = tr_ok ? &A.trace[c.it - 1] : nullptr;
@@ -320,20 +328,35 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
   __shared__ int shr[THREADS / 32];
   int bad = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    long long base = A.pool.tile_offset[tile];
+    const long long tile_base = A.pool.tile_offset[tile];
+    // phase 1: every item's classification and rank (V and E of all items
+    // requested before the first is used); phase 2: the copies, whose loads
+    // then overlap across items instead of following one barrier each
+    double vv[ITEMS];
+    bool actv[ITEMS];
+    long long qv[ITEMS];
+#pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-      bool act = false;
-      double v = 0.0;
-      if (i < s) {
-        v = A.pool.V[i];
-        act = final_active(v, A.pool.E[i], c);
-      }
+      vv[r] = i < s ? A.pool.V[i] : 0.0;
+      actv[r] = i < s ? final_active(vv[r], A.pool.E[i], c) : false;
+    }
+    long long base = tile_base;
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
       int total;
-      const int rank = block_rank<THREADS>(act, shr, &total);
+      const int rank = block_rank<THREADS>(actv[r], shr, &total);
+      qv[r] = base + rank;
+      base += total;
+    }
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
+      const bool act = actv[r];
+      const double v = vv[r];
       if (logl && !act && i < s) {
         // finished box: its rank among the finished ones is i - (survivors before i)
-        const int64_t pos = c.leaf_count + i - (base + rank);
+        const int64_t pos = c.leaf_count + i - qv[r];
         if (pos < A.leaves.cap) {
           for (int j = 0; j < n; ++j) {
             A.leaves.lower[(size_t)j * A.leaves.cap + pos] = lo_s[(size_t)j * cap + i];
@@ -344,7 +367,7 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
         }
       }
       if (act) {
-        const int64_t q = base + rank;
+        const int64_t q = qv[r];
         const int k = A.pool.K[i];
         A.pool.Vp[q] = v;
         for (int j = 0; j < n; ++j) {
@@ -361,7 +384,6 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
           *reinterpret_cast<uchar2*>(lv_d + (size_t)j * cap + 2 * q) = ol;
         }
       }
-      base += total;
     }
   }
   if (bad & 1) atomicExch(&c.watchdog, 1);
@@ -911,6 +933,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
   int64_t h2d = sizeof(Ctrl) + sizeof(prm), d2h = 0;
   int launches = 1, eval_launches = 0;  // the Uniform-Split kernel
   out->eval_ms = -1.0;
+  for (int i = 0; i < 4; ++i) out->phase_ms[i] = -1.0;
   if (o.use_graph) {
     const int key = fam * 16 + n + (w.n << 8) + (deg << 16);
     auto it = w.graphs.find(key);
@@ -927,49 +950,61 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
   } else {
     // host-driven loop: the same kernels, one launch each, with CUDA events
     // around every Evaluate launch on the launching stream
+    // host-driven loop: the same kernels, one launch each, with CUDA events
+    // around every launch on the launching stream (the per-phase breakdown)
     const LoopArgs args = loop_args(0, 0, 0);
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    PG_CK(cudaEventCreate(&ev0));
-    PG_CK(cudaEventCreate(&ev1));
-    double eval_ms = 0.0;
-    for (int guard = 0; guard < o.it_max + 2; ++guard) {
-      PG_CK(fk.fill[n](rule, args, L.mgmt_grid, 256, 0, st));
-      ++launches;
-      PG_CK(cudaEventRecord(ev0, st));
-      PG_CK(fk.loop[n](rule, args, L.eval_grid, L.eval_block, L.eval_smem, st));
-      PG_CK(cudaEventRecord(ev1, st));
-      ++launches;
-      PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-      PG_CK(cudaStreamSynchronize(st));
-      d2h += sizeof(Ctrl);
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int i = 0; i < 6; ++i) PG_CK(cudaEventCreate(&ev[i]));
+    double eval_ms = 0.0, phase[4] = {0.0, 0.0, 0.0, 0.0};
+    auto elapsed = [&](cudaEvent_t a, cudaEvent_t b) {
       float ms = 0.f;
-      PG_CK(cudaEventElapsedTime(&ms, ev0, ev1));
-      eval_ms += ms;
-      ++eval_launches;
-      if (h.search) {
-        for (int probe = 0; probe < 128; ++probe) {
-          k_probe<kMgmtThreads><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
-          PG_CK(cudaGetLastError());
-          ++launches;
-          PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-          PG_CK(cudaStreamSynchronize(st));
-          d2h += sizeof(Ctrl);
-          if (!h.search_cont) break;
-        }
-      }
-      k_count<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
-      PG_CK(cudaGetLastError());
-      k_split<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
-      PG_CK(cudaGetLastError());
+      return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? (double)ms : 0.0;
+    };
+    for (int guard = 0; guard < o.it_max + 2; ++guard) {
+      PG_CK(cudaEventRecord(ev[0], st));
+      PG_CK(fk.fill[n](rule, args, L.mgmt_grid, 256, 0, st));
+      PG_CK(cudaEventRecord(ev[1], st));
+      PG_CK(fk.loop[n](rule, args, L.eval_grid, L.eval_block, L.eval_smem, st));
+      PG_CK(cudaEventRecord(ev[2], st));
       launches += 2;
       PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       PG_CK(cudaStreamSynchronize(st));
       d2h += sizeof(Ctrl);
+      phase[0] += elapsed(ev[0], ev[1]);
+      eval_ms += elapsed(ev[1], ev[2]);
+      ++eval_launches;
+      if (h.search) {
+        for (int probe = 0; probe < 128; ++probe) {
+          PG_CK(cudaEventRecord(ev[0], st));
+          k_probe<kMgmtThreads><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
+          PG_CK(cudaGetLastError());
+          PG_CK(cudaEventRecord(ev[1], st));
+          ++launches;
+          PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+          PG_CK(cudaStreamSynchronize(st));
+          d2h += sizeof(Ctrl);
+          phase[1] += elapsed(ev[0], ev[1]);
+          if (!h.search_cont) break;
+        }
+      }
+      PG_CK(cudaEventRecord(ev[3], st));
+      k_count<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
+      PG_CK(cudaGetLastError());
+      PG_CK(cudaEventRecord(ev[4], st));
+      k_split<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
+      PG_CK(cudaGetLastError());
+      PG_CK(cudaEventRecord(ev[5], st));
+      launches += 2;
+      PG_CK(cudaMemcpyAsync(&h, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      PG_CK(cudaStreamSynchronize(st));
+      d2h += sizeof(Ctrl);
+      phase[2] += elapsed(ev[3], ev[4]);
+      phase[3] += elapsed(ev[4], ev[5]);
       if (h.done) break;
     }
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
     out->eval_ms = eval_ms;
+    for (int i = 0; i < 4; ++i) out->phase_ms[i] = phase[i];
   }
   if (trace && trace_cap > 0) {
     const int nrec = std::min(std::min(h.it, trace_cap), w.trace_cap);
@@ -1081,6 +1116,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
                                     int64_t max_regions, cudaStream_t st, pagani_result* out) {
   std::memset(out, 0, sizeof(*out));
   out->eval_ms = -1.0;
+  for (int k = 0; k < 4; ++k) out->phase_ms[k] = -1.0;
   if (n < PAGANI_MIN_DIM || n > PAGANI_MAX_DIM) return out->status = fail(PAGANI_ERR_DIM, "dim must be in [2, 8]");
   if (fam < 0 || fam >= kNumFamilies) return out->status = fail(PAGANI_ERR_INTEGRAND, "unknown integrand_id");
   if (!params) return out->status = fail(PAGANI_ERR_ARGUMENT, "params is NULL");
