@@ -506,6 +506,154 @@ __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double 
   K = k;
 }
 
+// ------------------------------------------------- cooperative evaluation
+// Table entry (code, axis j) of the box [lo, lo + 2^-lv): the same
+// expression as axis_entries (cache when the level is cached, else the
+// factor), so both give the same bits.
+template <class F>
+__device__ __forceinline__ typename F::T entry_value(const EvalRule& R, const IntegrandParams& prm,
+                                                     const typename F::T* __restrict__ cache, int cache_levels,
+                                                     double lo, int lv, int j, int code) {
+  if (cache != nullptr && lv <= cache_levels)
+    return cache[((size_t)j * kCacheSlots + ((1 << lv) - 1) + dyadic_index(lo, lv)) * kCodes + code];
+  const double h = 0.5 * pow2_neg(lv);
+  return F::factor(F::axis(prm, j), point_x(prm, j, lo + h, h, code_offset(R, code)));
+}
+
+// One warp per sibling pair, 16 lanes per region: the lanes build the
+// region's factor table together, take its rule points from the packed code
+// list (each point the product of its n table entries), reduce the nine
+// generator sums by butterfly, and compute one fourth difference each; then
+// every lane runs the same epilogue as the thread-per-pair form and lane 0
+// applies the two-level estimate and writes the pair.  Used while few pairs
+// exist: a thread-per-pair pass over them would run a handful of warps
+// through long dependent FP64 chains (about 64 cycles each) and a large
+// instruction stream.  The per-thread partial sums it leaves (lane 0 of each
+// warp) feed the block reduction of the loop kernel.
+template <class F, int N, int THREADS, int DEG>
+__device__ __forceinline__ void coop_pairs(const EvalRule& R, const LoopArgs& A, const IntegrandParams& prm,
+                                           const double* __restrict__ lower, const uint8_t* __restrict__ level,
+                                           int64_t cap, int64_t npairs, int it, int relerr, double tau_rel,
+                                           typename F::T* smem_warp, NSum& sv, NSum& se, NSum& svol, double& emin,
+                                           double& emax, long long& nrel, int& nonfinite) {
+  typedef typename F::T T;
+  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const int64_t warp0 = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (THREADS / 32);
+  T* tab = smem_warp + half * (kCodes * N);  // [code][axis] of this half's region
+  const T base = F::base(prm);
+  const T* __restrict__ fcache = static_cast<const T*>(A.fcache);
+  const uint64_t* __restrict__ codes = A.codes;
+  for (int64_t p = warp0; p < npairs; p += nwarps) {
+    const int64_t i = 2 * p + half;
+    double lo_mine = 0.0;
+    int lv_mine = 0;
+    if (hl < N) {
+      lo_mine = lower[(size_t)hl * cap + i];
+      lv_mine = level[(size_t)hl * cap + i];
+    }
+    double lo[N];
+    int lv[N], lvsum = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      lo[j] = __shfl_sync(0xffffffffu, lo_mine, half * 16 + j);
+      lv[j] = __shfl_sync(0xffffffffu, lv_mine, half * 16 + j);
+      lvsum += lv[j];
+    }
+    for (int e = hl; e < kCodes * N; e += 16) {
+      const int code = e / N, j = e - code * N;
+      double loj = lo[0];
+      int lvj = lv[0];
+#pragma unroll
+      for (int m = 1; m < N; ++m)
+        if (j == m) {
+          loj = lo[m];
+          lvj = lv[m];
+        }
+      tab[code * N + j] = entry_value<F>(R, prm, fcache, A.fcache_levels, loj, lvj, j, code);
+    }
+    __syncwarp();
+
+    // generator sums, lanes strided over each orbit's points
+    double S[kNumGen];
+#pragma unroll
+    for (int g = 0; g < kNumGen; ++g) {
+      S[g] = 0.0;
+      if (DEG == 7 && !(g == kGenCentre || g == kGenL2 || g == kGenLp || g == kGenL1L1 || g == kGenL0All)) continue;
+      double acc = 0.0;
+      for (int q = A.gen_off[g] + hl; q < A.gen_off[g + 1]; q += 16) {
+        const uint64_t w = codes[q];
+        T f = base;
+#pragma unroll
+        for (int j = 0; j < N; ++j) f = F::mul(f, tab[(int)((w >> (4 * j)) & 15) * N + j]);
+        acc += F::val(f);
+      }
+      S[g] = acc;
+    }
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1)
+#pragma unroll
+      for (int g = 0; g < kNumGen; ++g) S[g] += __shfl_xor_sync(0xffffffffu, S[g], off);
+
+    // fourth difference of axis hl (the same formula and noise floor as
+    // rule_sums), gathered to every lane of the half
+    double Dj;
+    {
+      const int jd = hl < N ? hl : 0;
+      T c0 = base, p2 = base, m2 = base, pp = base, mp = base;
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        const T t0 = tab[kC0 * N + m];
+        c0 = F::mul(c0, t0);
+        p2 = F::mul(p2, m == jd ? tab[kR2P * N + m] : t0);
+        m2 = F::mul(m2, m == jd ? tab[kR2M * N + m] : t0);
+        pp = F::mul(pp, m == jd ? tab[kRpP * N + m] : t0);
+        mp = F::mul(mp, m == jd ? tab[kRpM * N + m] : t0);
+      }
+      const double q = R.q;
+      const double f0 = F::val(c0), vp2 = F::val(p2), vm2 = F::val(m2), vpp = F::val(pp), vmp = F::val(mp);
+      const double s2 = vp2 + vm2, sp = vpp + vmp;
+      const double dj = fabs((sp - 2.0 * f0) - q * (s2 - 2.0 * f0));
+      const double mj = F::kUnitBounded
+                            ? (fabs(vpp) + fabs(vmp)) + q * (fabs(vp2) + fabs(vm2)) + (2.0 + 2.0 * q) * fabs(f0)
+                            : fma(2.0 + 2.0 * q, fabs(f0), fma(q, fabs(s2), fabs(sp)));
+      Dj = fma(-kDiffNoise, mj, dj) > 0.0 ? dj : -dj;
+    }
+    double D[N], width[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      D[j] = __shfl_sync(0xffffffffu, Dj, half * 16 + j);
+      width[j] = pow2_neg(lv[j]) * prm.len[j];
+    }
+    double V, E;
+    int K;
+    region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, pow2_neg(lvsum) * prm.vol, width, V, E, K, nullptr);
+    const double VR = __shfl_sync(0xffffffffu, V, 16);
+    double ER = __shfl_sync(0xffffffffu, E, 16);
+    const int KR = __shfl_sync(0xffffffffu, K, 16);
+    const int lvR = __shfl_sync(0xffffffffu, lvsum, 16);
+    if (lane == 0) {
+      const double VL = V;
+      double EL = E;
+      if (it > 1) two_level(VL, VR, A.pool.Vp[p], EL, ER);
+      *reinterpret_cast<double2*>(A.pool.V + 2 * p) = make_double2(VL, VR);
+      *reinterpret_cast<double2*>(A.pool.E + 2 * p) = make_double2(EL, ER);
+      *reinterpret_cast<uchar2*>(A.pool.K + 2 * p) = make_uchar2((unsigned char)K, (unsigned char)KR);
+      nadd(sv, VL);
+      nadd(sv, VR);
+      nadd(se, EL);
+      nadd(se, ER);
+      nadd(svol, pow2_neg(lvsum));
+      nadd(svol, pow2_neg(lvR));
+      emin = fmin(emin, fmin(EL, ER));
+      emax = fmax(emax, fmax(EL, ER));
+      nrel += relerr_active(VL, EL, tau_rel, relerr) + relerr_active(VR, ER, tau_rel, relerr);
+      if (!isfinite(VL) || !isfinite(VR) || !isfinite(EL) || !isfinite(ER)) nonfinite = 1;
+    }
+    __syncwarp();  // the table is rewritten for the next pair
+  }
+}
+
 // ------------------------------------------------------------- loop kernel
 // One thread per sibling pair (2p, 2p+1) of the current pool buffer; DEG is
 // the rule (9, or 7 for the Genz-Malik variant).
@@ -534,6 +682,16 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
   int nonfinite = 0;
 
   const int64_t npairs = s >> 1;
+  const int64_t nwarps = (int64_t)gridDim.x * (THREADS / 32);
+  const bool coop = A.codes != nullptr && npairs <= kCoopPasses * nwarps;
+  if (coop) {
+    // (parameters read through global memory: the cooperative table build
+    // indexes them with a runtime axis, which must not move the kernel's
+    // register copy to local memory)
+    coop_pairs<F, N, THREADS, DEG>(R, A, *A.prm, lower, level, cap, npairs, it, relerr, tau_rel,
+                                   reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * 32 * kCodes * N, sv, se,
+                                   svol, emin, emax, nrel, nonfinite);
+  } else
   for (int64_t p = (int64_t)blockIdx.x * THREADS + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * THREADS) {
     const int64_t iL = 2 * p;
     double loL[N], loR[N], wL[N], wR[N];
@@ -596,8 +754,10 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
   // warp-wide FP64 instruction costs the SM's FP64 pipe 16 cycles), and the
   // last block combines only the partials of blocks that had pairs, which
   // leaves every sum bit for bit unchanged
-  const int64_t nparts_eval = (npairs + THREADS - 1) / THREADS < (int64_t)gridDim.x
-                                  ? (npairs + THREADS - 1) / THREADS
+  // (cooperative: pair p on warp p mod nwarps, THREADS/32 warps a block)
+  const int64_t per_block = coop ? THREADS / 32 : THREADS;
+  const int64_t nparts_eval = (npairs + per_block - 1) / per_block < (int64_t)gridDim.x
+                                  ? (npairs + per_block - 1) / per_block
                                   : (int64_t)gridDim.x;
   __shared__ EvalPartial wp[THREADS / 32];
   if ((int64_t)blockIdx.x < nparts_eval) {

@@ -740,10 +740,13 @@ static int launch_config(const FamilyKernels& fk, int n, Launch* L) {
   return 0;
 }
 
-static LoopArgs loop_args(int use_graph, cudaGraphConditionalHandle hm, cudaGraphConditionalHandle hp) {
+static LoopArgs loop_args(int n, int use_graph, cudaGraphConditionalHandle hm, cudaGraphConditionalHandle hp) {
   Workspace& w = g_ws;
   LoopArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.codes = w.codes[n];
+  a.gen_off[0] = 0;
+  for (int g = 0; g < kNumGen; ++g) a.gen_off[g + 1] = a.gen_off[g] + (int)orbit_count(n, g);
   a.pool = w.pool;
   a.ctrl = w.ctrl;
   a.prm = w.prm;
@@ -812,7 +815,7 @@ static int build_graph(int fam, int n, int degree, const EvalRule& rule, const L
   PG_CK(cudaGraphConditionalHandleCreate(&hm, g, 1, cudaGraphCondAssignDefault));
   PG_CK(add_while(&wmain, g, nullptr, 0, hm, &body));
   PG_CK(cudaGraphConditionalHandleCreate(&hp, body, 0, 0));
-  args = loop_args(1, hm, hp);
+  args = loop_args(n, 1, hm, hp);
   eargs[0] = &r;
   eargs[1] = &args;
   margs[0] = &args;
@@ -952,7 +955,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
     // around every Evaluate launch on the launching stream
     // host-driven loop: the same kernels, one launch each, with CUDA events
     // around every launch on the launching stream (the per-phase breakdown)
-    const LoopArgs args = loop_args(0, 0, 0);
+    const LoopArgs args = loop_args(n, 0, 0, 0);
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     for (int i = 0; i < 6; ++i) PG_CK(cudaEventCreate(&ev[i]));
     double eval_ms = 0.0, phase[4] = {0.0, 0.0, 0.0, 0.0};
