@@ -801,30 +801,29 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
 }
 
 // ------------------------------------------------------- factor-cache fill
-// Fills level L = l0 + it - 1 of the per-axis factor cache (the deepest level
-// a box can have reached by iteration it), if it is cached.  One thread per
-// (axis, interval, code).
+// Fills every cached level (0 .. fcache_levels) of the per-axis factor cache
+// in one launch before the loop: n (2^(levels+1) - 1) 11 factors, one thread
+// per (axis, interval, code), with the expression axis_entries uses.
 template <class F, int N>
 __global__ void __launch_bounds__(256) k_factor_cache(const EvalRule R, const LoopArgs A) {
   typedef typename F::T T;
-  const Ctrl& c = *A.ctrl;
-  if (c.done || A.fcache == nullptr) return;
-  const int L = c.l0 + c.it - 1;
-  if (L > A.fcache_levels) return;
+  if (A.fcache == nullptr) return;
   T* cache = static_cast<T*>(A.fcache);
   const IntegrandParams prm = *A.prm;
-  const long long count = 1LL << L;
-  const long long total = (long long)N * count * kCodes;
-  const double w = pow2_neg(L);
-  const double h = 0.5 * w;
+  const long long slots = (2LL << A.fcache_levels) - 1;
+  const long long total = (long long)N * slots * kCodes;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int code = (int)(idx % kCodes);
     const long long rest = idx / kCodes;
-    const long long k = rest % count;
-    const int j = (int)(rest / count);
+    const long long slot = rest % slots;
+    const int j = (int)(rest / slots);
+    const int L = 63 - __clzll(slot + 1);       // slot = 2^L - 1 + k
+    const long long k = slot + 1 - (1LL << L);
+    const double w = pow2_neg(L);
+    const double h = 0.5 * w;
     const double lo = (double)k * w;
-    cache[((size_t)j * kCacheSlots + (count - 1) + k) * kCodes + code] =
+    cache[((size_t)j * kCacheSlots + slot) * kCodes + code] =
         F::factor(F::axis(prm, j), point_x(prm, j, lo + h, h, code_offset(R, code)));
   }
 }

@@ -235,7 +235,8 @@ def pair_table_work(family: int, n: int) -> Counter:
 
 def cache_fill_work(family: int, n: int, level: int) -> Counter:
     """FP64 work of filling one level of the per-axis factor cache: n 2^level
-    intervals, each with the 11 entries (and set-up) of one table axis."""
+    intervals, each with the 11 entries (and set-up) of one table axis.  The
+    fill kernel writes levels 0..11 once per integration."""
     one_axis = Counter(pair_table_work(family, 1))
     one_axis.subtract(pair_table_work(family, 0))
     return Counter({k: v * n * (1 << level) for k, v in one_axis.items() if v})
