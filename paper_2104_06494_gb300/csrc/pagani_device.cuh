@@ -161,44 +161,36 @@ __device__ __forceinline__ NSum nsum_block_combine(NSum a, NSum* sh) {
   return a;  // valid on thread 0
 }
 
-// K compensated sums reduced over the block at once.  A dependent FP64
-// operation takes about 64 cycles on this GPU, so the K shuffle trees run
-// interleaved, and the per-warp results are combined by a second shuffle tree
-// in warp 0 (log2 of the warp count levels) rather than by one thread in
-// sequence.  Fixed tree order: deterministic.  sh holds K * THREADS/32 sums;
-// the result is valid on thread 0.
+// K compensated sums reduced over the block through shared memory: a
+// warp-wide FP64 instruction occupies its scheduler's FP64 unit about 64
+// cycles on this GPU, so the reduction keeps the number of them small
+// instead of running every warp through a shuffle tree.  The K x THREADS partials are staged in sh; K*32
+// threads fold chunks of THREADS/32 consecutive partials in index order, and
+// warp k reduces sum k's 32 chunk results by shuffles.  Fixed order:
+// deterministic.  sh holds K * THREADS + K sums; the results are valid on
+// thread 0 (in a).  Needs K <= THREADS / 32.
 template <int THREADS, int K>
-__device__ __forceinline__ void nsum_block_reduce(NSum (&a)[K], NSum* sh) {
-  constexpr int NW = THREADS / 32;
+__device__ __forceinline__ void nsum_block_reduce_staged(NSum (&a)[K], NSum* sh) {
+  constexpr int C = THREADS / 32;  // partials per chunk: 32 chunks per sum
+  static_assert(K <= THREADS / 32, "one warp per sum");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    NSum b[K];
+  for (int k = 0; k < K; ++k) sh[k * THREADS + threadIdx.x] = a[k];
+  __syncthreads();
+  if (warp < K) {
+    const NSum* src = sh + warp * THREADS + lane * C;
+    NSum r = src[0];
 #pragma unroll
-    for (int k = 0; k < K; ++k) b[k] = shfl_down_nsum(a[k], off);
+    for (int t = 1; t < C; ++t) r = ncomb(r, src[t]);
 #pragma unroll
-    for (int k = 0; k < K; ++k) a[k] = ncomb(a[k], b[k]);
+    for (int off = 16; off > 0; off >>= 1) r = ncomb(r, shfl_down_nsum(r, off));
+    if (lane == 0) sh[K * THREADS + warp] = r;
   }
   __syncthreads();
-  if (lane == 0)
+  if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < K; ++k) sh[k * NW + warp] = a[k];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      a[k].s = lane < NW ? sh[k * NW + lane].s : 0.0;
-      a[k].c = lane < NW ? sh[k * NW + lane].c : 0.0;
-    }
-#pragma unroll
-    for (int off = NW / 2; off > 0; off >>= 1) {
-      NSum b[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) b[k] = shfl_down_nsum(a[k], off);
-#pragma unroll
-      for (int k = 0; k < K; ++k) a[k] = ncomb(a[k], b[k]);
-    }
-  }
+    for (int k = 0; k < K; ++k) a[k] = sh[K * THREADS + k];
 }
 
 // Exclusive scan of one 64-bit count per thread across the block (thread

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
       nadd(sa, e);
     }
   }
-  __shared__ NSum shn[THREADS / 32];
+  __shared__ NSum shn[THREADS + 1];
   __shared__ long long shl[THREADS / 32];
   // blocks without regions hold exact zeros and skip the FP64 shuffles; the
   // last block reads only the partials that can be non-zero
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   const int64_t nparts = nblk < (int64_t)gridDim.x ? nblk : (int64_t)gridDim.x;
   if ((int64_t)blockIdx.x < nparts) {
     NSum bs[1] = {sa};
-    nsum_block_reduce<THREADS, 1>(bs, shn);
+    nsum_block_reduce_staged<THREADS, 1>(bs, shn);
     long long bn = block_sum_ll<THREADS>(na, shl);
     if (threadIdx.x == 0) {
       A.probe_part[blockIdx.x].ea = bs[0];
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
     pa[0] = ncomb(pa[0], A.probe_part[b].ea);
     pn += A.probe_part[b].n_active;
   }
-  nsum_block_reduce<THREADS, 1>(pa, shn);
+  nsum_block_reduce_staged<THREADS, 1>(pa, shn);
   const long long n = block_sum_ll<THREADS>(pn, shl);
   if (threadIdx.x == 0) {
     const int cont = threshold_step(c, n, nval(pa[0]));
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   const double* __restrict__ E = A.pool.E;
   const int64_t ntiles = (s + TILE - 1) / TILE;
   __shared__ long long shl[2 * (THREADS / 32)];
-  __shared__ NSum shn[3 * (THREADS / 32)];
+  __shared__ NSum shn[3 * THREADS + 3];
   // each thread sums its ITEMS regions of a tile plainly (relative error at
   // most (ITEMS - 1) u) and adds that partial into Neumaier accumulators, so
   // the sums stay compensated across all partials at a third of the FP64 work
@@ -191,7 +191,9 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
       if (i < s) {
         const double v = vv[r], e = ee[r];
-        if (final_active(v, e, c)) {
+        const bool act = final_active(v, e, c);
+        A.pool.act[i] = act ? 1 : 0;  // the split reads it back
+        if (act) {
           ++cnt;
           tv += v;
           te += e;
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   // leaves every sum bit for bit unchanged
   const int64_t nparts = ntiles < (int64_t)gridDim.x ? ntiles : (int64_t)gridDim.x;
   if ((int64_t)blockIdx.x < nparts) {
-    nsum_block_reduce<THREADS, 3>(acc3, shn);
+    nsum_block_reduce_staged<THREADS, 3>(acc3, shn);
     if (threadIdx.x == 0) {
       A.count_part[blockIdx.x].va = va;
       A.count_part[blockIdx.x].ea = ea;
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     p3[1] = ncomb(p3[1], A.count_part[b].ea);
     p3[2] = ncomb(p3[2], A.count_part[b].finvol);
   }
-  nsum_block_reduce<THREADS, 3>(p3, shn);
+  nsum_block_reduce_staged<THREADS, 3>(p3, shn);
   if (threadIdx.x != 0) return;
   const NSum tva = p3[0], tea = p3[1], tfv = p3[2];
   c.n_surv = n_surv;
@@ -329,17 +331,15 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
   int bad = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long tile_base = A.pool.tile_offset[tile];
-    // phase 1: every item's classification and rank (V and E of all items
-    // requested before the first is used); phase 2: the copies, whose loads
-    // then overlap across items instead of following one barrier each
-    double vv[ITEMS];
+    // phase 1: every item's classification (stored by the count kernel) and
+    // rank; phase 2: the copies, whose loads then overlap across items
+    // instead of following one barrier each
     bool actv[ITEMS];
     long long qv[ITEMS];
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-      vv[r] = i < s ? A.pool.V[i] : 0.0;
-      actv[r] = i < s ? final_active(vv[r], A.pool.E[i], c) : false;
+      actv[r] = i < s && A.pool.act[i] != 0;  // classified by the count kernel
     }
     long long base = tile_base;
 #pragma unroll
@@ -353,7 +353,6 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
       const bool act = actv[r];
-      const double v = vv[r];
       if (logl && !act && i < s) {
         // finished box: its rank among the finished ones is i - (survivors before i)
         const int64_t pos = c.leaf_count + i - qv[r];
@@ -369,7 +368,7 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
       if (act) {
         const int64_t q = qv[r];
         const int k = A.pool.K[i];
-        A.pool.Vp[q] = v;
+        A.pool.Vp[q] = A.pool.V[i];
         for (int j = 0; j < n; ++j) {
           const double lo = lo_s[(size_t)j * cap + i];
           const int lv = lv_s[(size_t)j * cap + i];
@@ -569,6 +568,7 @@ static int ensure_workspace(int64_t want_cap, int n) {
   PG_ALLOC(w.pool.V, cap);
   PG_ALLOC(w.pool.E, cap);
   PG_ALLOC(w.pool.K, cap);
+  PG_ALLOC(w.pool.act, cap);
   PG_ALLOC(w.pool.Vp, cap / 2 + 1);
   PG_ALLOC(w.pool.tile_count, ntiles);
   PG_ALLOC(w.pool.tile_offset, ntiles);
@@ -1080,7 +1080,7 @@ static void* g_noalloc_base[64] = {nullptr};
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NoallocLayout {
-  size_t ctrl, prm, eval_part, probe_part, count_part, lower, level, V, E, K, Vp, tile_count, tile_offset, total;
+  size_t ctrl, prm, eval_part, probe_part, count_part, lower, level, V, E, K, act, Vp, tile_count, tile_offset, total;
 };
 
 static NoallocLayout noalloc_layout(int64_t cap, int n, int max_grid) {
@@ -1102,6 +1102,7 @@ static NoallocLayout noalloc_layout(int64_t cap, int n, int max_grid) {
   L.V = take(sizeof(double) * (size_t)cap);
   L.E = take(sizeof(double) * (size_t)cap);
   L.K = take((size_t)cap);
+  L.act = take((size_t)cap);
   L.Vp = take(sizeof(double) * (size_t)(cap / 2 + 1));
   L.tile_count = take(sizeof(long long) * (size_t)ntiles);
   L.tile_offset = take(sizeof(long long) * (size_t)ntiles);
@@ -1111,7 +1112,7 @@ static NoallocLayout noalloc_layout(int64_t cap, int n, int max_grid) {
 
 // Largest region capacity (a multiple of 4096) whose layout fits the array.
 static int64_t noalloc_capacity(int n, int max_grid) {
-  int64_t lo = 0, hi = (int64_t)(kNoallocBytes / (size_t)(18 * n + 25)) + 4096;
+  int64_t lo = 0, hi = (int64_t)(kNoallocBytes / (size_t)(18 * n + 26)) + 4096;
   while (hi - lo > 4096) {
     const int64_t mid = ((lo + hi) / 2 / 4096) * 4096;
     if (mid <= lo) break;
@@ -1181,6 +1182,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   a.pool.V = reinterpret_cast<double*>(base + L.V);
   a.pool.E = reinterpret_cast<double*>(base + L.E);
   a.pool.K = base + L.K;
+  a.pool.act = base + L.act;
   a.pool.Vp = reinterpret_cast<double*>(base + L.Vp);
   a.pool.tile_count = reinterpret_cast<long long*>(base + L.tile_count);
   a.pool.tile_offset = reinterpret_cast<long long*>(base + L.tile_offset);

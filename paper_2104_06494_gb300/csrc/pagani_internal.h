@@ -173,6 +173,7 @@ struct Pool {
   double* V;            // cap
   double* E;            // cap
   uint8_t* K;           // cap
+  uint8_t* act;         // cap: final classification of the iteration (1 = survivor)
   double* Vp;           // cap / 2 + 1
   long long* tile_count;   // n_tiles + 1
   long long* tile_offset;  // n_tiles + 1
