@@ -142,24 +142,6 @@ __device__ __forceinline__ EvalPartial eval_block_combine(EvalPartial acc, EvalP
     for (int w = 1; w < THREADS / 32; ++w) acc = eval_combine(acc, sh[w]);
   return acc;  // valid on thread 0
 }
-template <int THREADS>
-__device__ __forceinline__ EvalPartial eval_reduce_partials(const EvalPartial* parts, int n, EvalPartial* sh) {
-  EvalPartial acc = eval_identity();
-  for (int b = threadIdx.x; b < n; b += THREADS) acc = eval_combine(acc, parts[b]);
-  return eval_block_combine<THREADS>(acc, sh);
-}
-
-template <int THREADS>
-__device__ __forceinline__ NSum nsum_block_combine(NSum a, NSum* sh) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) a = ncomb(a, shfl_down_nsum(a, off));
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int w = 1; w < THREADS / 32; ++w) a = ncomb(a, sh[w]);
-  return a;  // valid on thread 0
-}
 
 // K compensated sums reduced over the block through shared memory: a
 // warp-wide FP64 instruction occupies its scheduler's FP64 unit about 64
@@ -168,29 +150,79 @@ __device__ __forceinline__ NSum nsum_block_combine(NSum a, NSum* sh) {
 // threads fold chunks of THREADS/32 consecutive partials in index order, and
 // warp k reduces sum k's 32 chunk results by shuffles.  Fixed order:
 // deterministic.  sh holds K * THREADS + K sums; the results are valid on
-// thread 0 (in a).  Needs K <= THREADS / 32.
+// thread 0 (in a).  With fewer warps than sums, a warp takes several.
 template <int THREADS, int K>
 __device__ __forceinline__ void nsum_block_reduce_staged(NSum (&a)[K], NSum* sh) {
   constexpr int C = THREADS / 32;  // partials per chunk: 32 chunks per sum
-  static_assert(K <= THREADS / 32, "one warp per sum");
+  constexpr int NW = THREADS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) sh[k * THREADS + threadIdx.x] = a[k];
   __syncthreads();
-  if (warp < K) {
-    const NSum* src = sh + warp * THREADS + lane * C;
+  for (int k = warp; k < K; k += NW) {
+    const NSum* src = sh + k * THREADS + lane * C;
     NSum r = src[0];
 #pragma unroll
     for (int t = 1; t < C; ++t) r = ncomb(r, src[t]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) r = ncomb(r, shfl_down_nsum(r, off));
-    if (lane == 0) sh[K * THREADS + warp] = r;
+    if (lane == 0) sh[K * THREADS + k] = r;
   }
   __syncthreads();
   if (threadIdx.x == 0)
 #pragma unroll
     for (int k = 0; k < K; ++k) a[k] = sh[K * THREADS + k];
+}
+
+// An EvalPartial reduced over the block: the three compensated sums staged
+// as above; emin / emax as the bit patterns of non-negative doubles (their
+// integer order is the numeric one; the -inf of an empty partial is a
+// negative integer), so no FP64 instruction is spent on them.  smem holds
+// 3 * THREADS + 3 sums plus 4 * THREADS/32 64-bit words.  Valid on thread 0.
+template <int THREADS>
+__device__ __forceinline__ EvalPartial eval_block_finish(EvalPartial p, void* smem) {
+  constexpr int NW = THREADS / 32;
+  NSum* shn = static_cast<NSum*>(smem);
+  long long* shl = reinterpret_cast<long long*>(shn + 3 * THREADS + 3);
+  NSum a3[3] = {p.v, p.e, p.vol};
+  long long imin = __double_as_longlong(p.emin), imax = __double_as_longlong(p.emax), nrel = p.n_rel;
+  int nf = p.nonfinite;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long a = __shfl_down_sync(0xffffffffu, imin, off), b = __shfl_down_sync(0xffffffffu, imax, off);
+    imin = a < imin ? a : imin;
+    imax = b > imax ? b : imax;
+    nrel += __shfl_down_sync(0xffffffffu, nrel, off);
+    nf |= __shfl_down_sync(0xffffffffu, nf, off);
+  }
+  nsum_block_reduce_staged<THREADS, 3>(a3, shn);  // begins and ends with a barrier
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    shl[warp] = imin;
+    shl[NW + warp] = imax;
+    shl[2 * NW + warp] = nrel;
+    shl[3 * NW + warp] = nf;
+  }
+  __syncthreads();
+  EvalPartial out = p;
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < NW; ++w) {
+      imin = shl[w] < imin ? shl[w] : imin;
+      imax = shl[NW + w] > imax ? shl[NW + w] : imax;
+      nrel += shl[2 * NW + w];
+      nf |= (int)shl[3 * NW + w];
+    }
+    out.v = a3[0];
+    out.e = a3[1];
+    out.vol = a3[2];
+    out.emin = __longlong_as_double(imin);
+    out.emax = __longlong_as_double(imax);
+    out.n_rel = nrel;
+    out.nonfinite = nf;
+    out.pad = 0;
+  }
+  return out;
 }
 
 // Exclusive scan of one 64-bit count per thread across the block (thread

@@ -749,9 +749,9 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     if (!isfinite(VL) || !isfinite(VR) || !isfinite(EL) || !isfinite(ER)) nonfinite = 1;
   }
 
-  // block reduction of the partials (fixed tree order: deterministic).  A
-  // block without pairs holds the identity: it skips the FP64 shuffles (each
-  // warp-wide FP64 instruction costs the SM's FP64 pipe 16 cycles), and the
+  // block reduction of the partials (fixed order: deterministic).  A block
+  // without pairs holds the identity and skips it (a warp-wide FP64
+  // instruction occupies its scheduler's FP64 unit about 64 cycles), and the
   // last block combines only the partials of blocks that had pairs, which
   // leaves every sum bit for bit unchanged
   // (cooperative: pair p on warp p mod nwarps, THREADS/32 warps a block)
@@ -759,18 +759,7 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
   const int64_t nparts_eval = (npairs + per_block - 1) / per_block < (int64_t)gridDim.x
                                   ? (npairs + per_block - 1) / per_block
                                   : (int64_t)gridDim.x;
-  __shared__ EvalPartial wp[THREADS / 32];
   if ((int64_t)blockIdx.x < nparts_eval) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      sv = ncomb(sv, shfl_down_nsum(sv, off));
-      se = ncomb(se, shfl_down_nsum(se, off));
-      svol = ncomb(svol, shfl_down_nsum(svol, off));
-      emin = fmin(emin, __shfl_down_sync(0xffffffffu, emin, off));
-      emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, off));
-      nrel += __shfl_down_sync(0xffffffffu, nrel, off);
-      nonfinite |= __shfl_down_sync(0xffffffffu, nonfinite, off);
-    }
     EvalPartial mine;
     mine.v = sv;
     mine.e = se;
@@ -780,18 +769,15 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     mine.n_rel = nrel;
     mine.nonfinite = nonfinite;
     mine.pad = 0;
-    // (the shuffles above already combined each warp; combine the warps)
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5] = mine;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      EvalPartial bp = wp[0];
-      for (int w = 1; w < THREADS / 32; ++w) bp = eval_combine(bp, wp[w]);
-      A.eval_part[blockIdx.x] = bp;
-    }
+    // (the factor tables in shared memory are done with: the reduction
+    // stages its partials there)
+    const EvalPartial bp = eval_block_finish<THREADS>(mine, smem_raw);
+    if (threadIdx.x == 0) A.eval_part[blockIdx.x] = bp;
   }
   if (!last_block_arrived(&c.ticket_eval)) return;
-  const EvalPartial tot = eval_reduce_partials<THREADS>(A.eval_part, (int)nparts_eval, wp);
+  EvalPartial acc = eval_identity();
+  for (int64_t b = threadIdx.x; b < nparts_eval; b += THREADS) acc = eval_combine(acc, A.eval_part[b]);
+  const EvalPartial tot = eval_block_finish<THREADS>(acc, smem_raw);
   if (threadIdx.x == 0) {
     int search = finalize_iteration_head(c, nval(tot.v), nval(tot.e), tot.n_rel, tot.emin, tot.emax,
                                          tot.nonfinite, A.trace, A.trace_cap, nval(tot.vol));

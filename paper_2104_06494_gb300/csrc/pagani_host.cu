@@ -42,22 +42,6 @@ __device__ __forceinline__ long long block_sum_ll(long long x, long long* sh) {
   return t;  // valid on thread 0
 }
 
-template <int THREADS>
-__device__ __forceinline__ NSum block_nsum(NSum a, NSum* sh) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) a = ncomb(a, shfl_down_nsum(a, off));
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[warp] = a;
-  __syncthreads();
-  NSum t = {0.0, 0.0};
-  if (threadIdx.x == 0) {
-    t = sh[0];
-    for (int w = 1; w < THREADS / 32; ++w) t = ncomb(t, sh[w]);
-  }
-  return t;  // valid on thread 0
-}
-
 // Exclusive scan of one flag per thread across the block, in thread order.
 // Returns this thread's rank among the set flags; *total = number set.
 template <int THREADS>
@@ -1311,7 +1295,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_uniform(const BatchArgs
 // Sums, Rel-Err-Classify, termination and the Threshold-Classify trigger of
 // every instance (Algorithm 2), one block per instance.
 __global__ void __launch_bounds__(kBatchThreads) k_batch_reduce(const BatchArgs A) {
-  __shared__ EvalPartial sh[kBatchThreads / 32];
+  // staging area of eval_block_finish: 3 * threads + 3 sums and 4 words a warp
+  __shared__ __align__(16) unsigned char sh[(3 * kBatchThreads + 3) * sizeof(NSum) + 4 * (kBatchThreads / 32) * 8];
   for (int b = blockIdx.x; b < A.n_inst; b += gridDim.x) {
     BatchInst& I = A.inst[b];
     Ctrl& c = I.c;
@@ -1334,7 +1319,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_reduce(const BatchArgs 
       for (int j = 0; j < I.n; ++j) L += G->level[((size_t)buf * I.n + j) * slots + base + i];
       nadd(acc.vol, pow2_neg(L));
     }
-    const EvalPartial tot = eval_block_combine<kBatchThreads>(acc, sh);
+    const EvalPartial tot = eval_block_finish<kBatchThreads>(acc, sh);
     if (threadIdx.x == 0) {
       const int search = finalize_iteration_head(c, nval(tot.v), nval(tot.e), tot.n_rel, tot.emin, tot.emax,
                                                  tot.nonfinite, nullptr, 0, nval(tot.vol));
@@ -1353,7 +1338,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_reduce(const BatchArgs 
 
 // One threshold-search probe for every instance still searching (Algorithm 3).
 __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A) {
-  __shared__ NSum shn[kBatchThreads / 32];
+  __shared__ NSum shn[kBatchThreads + 1];
   __shared__ long long shl[kBatchThreads / 32];
   for (int b = blockIdx.x; b < A.n_inst; b += gridDim.x) {
     BatchInst& I = A.inst[b];
@@ -1373,7 +1358,9 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A
         nadd(sa, e);
       }
     }
-    const NSum tot = nsum_block_combine<kBatchThreads>(sa, shn);
+    NSum tot1[1] = {sa};
+    nsum_block_reduce_staged<kBatchThreads, 1>(tot1, shn);
+    const NSum tot = tot1[0];
     const long long n = block_sum_ll<kBatchThreads>(na, shl);
     if (threadIdx.x == 0) {
       const int cont = threshold_step(c, n, nval(tot));
@@ -1394,7 +1381,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A
 // v_f, e_f, the memory and reachability checks, then Filter + parent update
 // + Split inside the instance's slot (Algorithm 2), one block per instance.
 __global__ void __launch_bounds__(kBatchThreads) k_batch_split(const BatchArgs A) {
-  __shared__ NSum shn[kBatchThreads / 32];
+  __shared__ NSum shn[2 * kBatchThreads + 2];
   __shared__ long long shl[kBatchThreads / 32];
   __shared__ int shr[kBatchThreads / 32];
   __shared__ int go_on;
@@ -1419,8 +1406,9 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_split(const BatchArgs A
         nadd(ea, e);
       }
     }
-    const NSum tva = nsum_block_combine<kBatchThreads>(va, shn);
-    const NSum tea = nsum_block_combine<kBatchThreads>(ea, shn);
+    NSum t2[2] = {va, ea};
+    nsum_block_reduce_staged<kBatchThreads, 2>(t2, shn);
+    const NSum tva = t2[0], tea = t2[1];
     const long long n_surv = block_sum_ll<kBatchThreads>(cnt, shl);
     if (threadIdx.x == 0) {
       c.n_surv = n_surv;
