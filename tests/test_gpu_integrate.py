@@ -210,6 +210,28 @@ def test_config_product_peak_d3_full_size(pg):
     assert abs(g.estimate - ex) <= g.errorest and g.status == 0
 
 
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_zero_and_constant_integrands(pg, n):
+    """Degenerate integrands: f = 0 converges in one pass with estimate and
+    error exactly 0; f = 1 returns the volume with zero error, to the
+    rounding of the double weights' sum (the oracle, summing exact-rounded
+    weights per orbit, gets 1 exactly; the kernel's order is 1 ulp off at
+    n = 8)."""
+    g = pg.pagani_integrate_ex(n, 5, [1.0] * n + [0.0] * n, 1e-6)
+    assert (g.status, g.iterations, g.estimate, g.errorest) == (0, 1, 0.0, 0.0)
+    g = pg.pagani_integrate_ex(n, 6, [0.0], 1e-12)
+    assert (g.status, g.iterations, g.errorest) == (0, 1, 0.0)
+    assert abs(g.estimate - 1.0) <= 4 * 2.0 ** -53
+
+
+@pytest.mark.parametrize("init_div", [2, 8])
+def test_non_default_uniform_split_matches_oracle(pg, init_div):
+    params = [10.0, 12.0, 14.0, 0.3, 0.5, 0.7]
+    o = oracle.integrate(1, 3, params, 1e-6, init_div=init_div)
+    g = pg.pagani_integrate_ex(3, 1, params, 1e-6, init_div=init_div, trace=True)
+    compare_runs(g, o)
+
+
 def test_graph_and_host_loop_identical(pg):
     params = draw_params(1, 4, 42)
     a = pg.pagani_integrate_ex(4, 1, params, 1e-6, use_graph=1, trace=True)

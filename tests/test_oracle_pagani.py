@@ -206,3 +206,25 @@ def test_error_vanishes_for_exactly_integrated_polynomials(p):
     assert E[0] == 0.0
     n = 2
     assert D[0, 0] <= D[0, 9 + 2 * n] and D[0, 1] <= D[0, 10 + 2 * n]
+
+
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_identically_zero_integrand(n):
+    """f = 0 on the whole cube (discontinuous family with every w_j = 0): one
+    pass, estimate and error exactly 0, converged through the absolute
+    tolerance (0/0 is not a relative-error pass)."""
+    o = capi.integrate(5, n, [1.0] * n + [0.0] * n, 1e-6)
+    assert (o.status, o.iterations, o.estimate, o.errorest) == (0, 1, 0.0, 0.0)
+
+
+@pytest.mark.parametrize("n", [3, 8])
+def test_constant_integrand_is_exact(n):
+    """(sum x^2)^0 = 1: the rule integrates constants exactly, every null rule
+    annihilates them, so the first pass returns the volume with zero error,
+    on the unit cube and on a general box."""
+    o = capi.integrate(6, n, [0.0], 1e-12)
+    assert (o.status, o.iterations, o.estimate, o.errorest) == (0, 1, 1.0, 0.0)
+    lo = [-1.0, 0.0, 2.0] + [0.0] * (n - 3)
+    hi = [1.0, 3.0, 2.5] + [1.0] * (n - 3)
+    o = capi.integrate(6, n, [0.0], 1e-12, bounds=(lo, hi))
+    assert o.status == 0 and abs(o.estimate - 3.0) <= 4e-16 * 3.0 and o.errorest == 0.0
