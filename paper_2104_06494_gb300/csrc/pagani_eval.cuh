@@ -878,12 +878,23 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_batch(const EvalRule R, co
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
   const int64_t slots = (int64_t)G.count * G.slot_cap;
-  const int64_t npairs = slots >> 1;
-  for (int64_t p = (int64_t)blockIdx.x * THREADS + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * THREADS) {
-    const int64_t iL = 2 * p;
-    const int li = (int)(iL / G.slot_cap);
+  // live pairs only: thread t's pair belongs to the instance whose prefix
+  // range holds it (binary search over the group's instances)
+  const long long* __restrict__ pre = A.pair_prefix;
+  const long long first = pre[G.first];
+  const long long npairs = pre[G.first + G.count] - first;
+  for (long long t = (long long)blockIdx.x * THREADS + threadIdx.x; t < npairs; t += (long long)gridDim.x * THREADS) {
+    const long long key = first + t;
+    int lo_i = 0, hi_i = G.count - 1;  // last instance with pre[G.first + li] <= key
+    while (lo_i < hi_i) {
+      const int mid = (lo_i + hi_i + 1) >> 1;
+      if (pre[G.first + mid] <= key) lo_i = mid;
+      else hi_i = mid - 1;
+    }
+    const int li = lo_i;
     const Ctrl& c = A.inst[G.first + li].c;
-    if (c.done || iL - (int64_t)li * G.slot_cap >= c.s) continue;
+    const int64_t p = (int64_t)li * (G.slot_cap >> 1) + (key - pre[G.first + li]);  // group pair index
+    const int64_t iL = 2 * p;
     const int it = c.it;
     const int buf = (it - 1) & 1;
     const double* __restrict__ lower = G.lower + (size_t)buf * N * slots;

@@ -1480,6 +1480,23 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_split(const BatchArgs A
     __syncthreads();
   }
   if (!last_block_arrived(&A.tickets[2])) return;
+  // live pairs of every instance for the next Evaluate (chunks per thread,
+  // chunk sums scanned by warp shuffles)
+  {
+    __shared__ long long shl[2 * (kBatchThreads / 32)];
+    const int nI = A.n_inst;
+    const int per = (nI + kBatchThreads - 1) / kBatchThreads;
+    const int i0 = threadIdx.x * per, i1 = i0 + per < nI ? i0 + per : nI;
+    long long acc = 0;
+    for (int i = i0; i < i1; ++i) acc += A.inst[i].c.done ? 0 : A.inst[i].c.s / 2;
+    long long total = 0;
+    long long run = block_exclusive_scan<kBatchThreads>(acc, shl, &total);
+    for (int i = i0; i < i1; ++i) {
+      A.pair_prefix[i] = run;
+      run += A.inst[i].c.done ? 0 : A.inst[i].c.s / 2;
+    }
+    if (threadIdx.x == 0) A.pair_prefix[nI] = total;
+  }
   if (threadIdx.x == 0) {
     const int any = atomicExch(&A.flags[1], 0);
     A.flags[3] = any;
@@ -1552,7 +1569,7 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
     for (int64_t i : kv.second) order.push_back(i);
     groups.push_back(g);
   }
-  bytes += align(sizeof(BatchGroup) * groups.size());
+  bytes += align(sizeof(BatchGroup) * groups.size()) + align(sizeof(long long) * (count + 1));
   BatchWorkspace& bw = g_bws;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1580,6 +1597,7 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
   a.prm = prm_d;
   a.tickets = reinterpret_cast<unsigned int*>(take(256));
   a.flags = reinterpret_cast<int32_t*>(take(256));
+  a.pair_prefix = reinterpret_cast<long long*>(take(sizeof(long long) * (count + 1)));
   take(512);
   for (auto& g : groups) {
     const size_t slots = (size_t)g.count * slot_cap;
@@ -1631,6 +1649,10 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
     e = (x);                                                                                \
     if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e)); \
   } while (0)
+  // live pairs of the first iteration: every instance's s0 / 2
+  std::vector<long long> prefix(count + 1, 0);
+  for (int64_t i = 0; i < count; ++i) prefix[i + 1] = prefix[i] + hi[i].c.s / 2;
+  PG_CK(cudaMemcpyAsync(a.pair_prefix, prefix.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st));
   PG_CK(cudaMemcpyAsync(a.inst, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st));
   PG_CK(cudaMemcpyAsync(prm_d, hp.data(), sizeof(IntegrandParams) * count, cudaMemcpyHostToDevice, st));
   PG_CK(cudaMemcpyAsync(groups_d, groups.data(), sizeof(BatchGroup) * groups.size(), cudaMemcpyHostToDevice, st));

@@ -271,6 +271,9 @@ struct BatchArgs {
   int n_inst;
   unsigned int* tickets;        // [0] reduce, [1] probe, [2] split
   int32_t* flags;               // [0] any searching, [1] any running
+  // exclusive prefix over the instances (group order) of their live pairs
+  // (s / 2, or 0 once done); [n_inst] is the total.  Evaluate visits only these.
+  long long* pair_prefix;
   int use_graph;
   cudaGraphConditionalHandle h_main, h_probe;
 };
