@@ -205,6 +205,42 @@ def differentiation_report(pg, torch, flush, reps: int = 3):
             "backward_evals_per_s": r.n_leaves * npoints(n) / (bwd_ms * 1e-3)}
 
 
+def hbm_peak_gbs():
+    """The measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json,
+    written by the driver), else the profiling recipe's fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def management_bandwidth(part, hbm_peak):
+    """Achieved HBM bandwidth of the region-management kernels over one
+    host-driven integration: algorithmic bytes from the per-iteration trace
+    (s regions, n_surv survivors, n axes) over the phase's CUDA-event time.
+      count: V and E read, the classification byte written, the n level
+             bytes of every finished region read: 17 s + n (s - n_surv)
+      split: the classification byte read; per survivor K and V read, its
+             bounds and levels (9n) read, V_p and both halves (2 * 9n)
+             written: s + n_surv (17 + 27 n)"""
+    import numpy as np
+    tr, n = part["trace"], part["dim"]
+    s = tr["s"].astype(float)
+    surv = tr["n_survivors"].astype(float)
+    count_b = float(np.sum(17 * s + n * (s - surv)))
+    # the last iteration is split only when the loop goes on (not here: it ended)
+    split_b = float(np.sum((s + surv * (17 + 27 * n))[:-1]))
+    out = {}
+    for key, b, ms in (("sums_count", count_b, part["phase_ms"][2]), ("filter_split", split_b, part["phase_ms"][3])):
+        gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out[f"{key}_gbs"] = gbs
+        out[f"{key}_hbm_frac"] = gbs / hbm_peak if gbs is not None and hbm_peak else None
+    out["hbm_peak_gbs"] = hbm_peak
+    return out
+
+
 def filtering_report(pg, torch, flush, max_regions: int = 1 << 27):
     """The filtering ablation of Sec. 4.2 on the paper's own case, f4 in 8-D
     at three digits: Threshold-Classify with both triggers (the default), the
@@ -340,11 +376,12 @@ def main():
     # roofline of Evaluate: the same kernels, host-driven, CUDA events around
     # every Evaluate launch on the launching stream
     roof_parts = []
+    hbm_peak, hbm_peak_source = hbm_peak_gbs()
     for w in ws:
         r = run(w, use_graph=0, trace=True)
         work = roofline.evaluate_work(w.family, w.dim, r.trace["s"])
         roof_parts.append({"name": w.name, "eval_ms": r.eval_ms, "launches": r.eval_launches,
-                           "phase_ms": list(r.phase_ms), **work})
+                           "phase_ms": list(r.phase_ms), "dim": w.dim, "trace": r.trace, **work})
     fl = sum(p["flops"] for p in roof_parts)
     ins = sum(p["inst"] for p in roof_parts)
     ems = sum(p["eval_ms"] for p in roof_parts)
@@ -457,7 +494,8 @@ def main():
             "breakdown": {p["name"]: {"evaluate_ms": p["eval_ms"], "cache_fill_ms": p["phase_ms"][0],
                                       "threshold_probe_ms": p["phase_ms"][1], "sums_count_ms": p["phase_ms"][2],
                                       "filter_split_ms": p["phase_ms"][3],
-                                      "evaluate_share": p["eval_ms"] / (p["eval_ms"] + sum(p["phase_ms"]))}
+                                      "evaluate_share": p["eval_ms"] / (p["eval_ms"] + sum(p["phase_ms"])),
+                                      **management_bandwidth(p, hbm_peak), "hbm_peak_source": hbm_peak_source}
                           for p in roof_parts},
             "clocks": clk,
             "gpu_launches": launches,
