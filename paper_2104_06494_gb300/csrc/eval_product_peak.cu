@@ -1,5 +1,5 @@
 // Evaluate kernels of the product peak family, dimensions 2..8.
-#include "pagani_eval.cuh"
+#include "pagani_kernels.cuh"
 
 namespace pg {
 

@@ -940,96 +940,6 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_batch(const EvalRule R, co
   }
 }
 
-// ------------------------------------------------------------ gradient kernel
-// d/dtheta of the rule estimate summed over a fixed list of boxes (the leaf
-// set of an integration): vol * sum_points w_g f(x) d log phi_j(x_j)/d theta_j
-// for theta = (p0_j, p1_j) of every axis, and the estimate itself.  One warp
-// per box, lanes over the rule points (packed code table); per-axis factor and
-// log-derivative tables in shared memory per warp.  Each lane sums one box's
-// points plainly and adds that into Neumaier accumulators; the last block
-// combines the per-block partials.
-template <class F, int N>
-__global__ void __launch_bounds__(128) k_gradient(const EvalRule R, const GradArgs A) {
-  constexpr int K = 2 * N + 1;
-  __shared__ double tabs[4][3][N][kCodes];
-  __shared__ NSum red[4][K];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const IntegrandParams prm = *A.prm;
-  double (*phi)[kCodes] = tabs[wib][0];
-  double (*d0)[kCodes] = tabs[wib][1];
-  double (*d1)[kCodes] = tabs[wib][2];
-  NSum acc[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) acc[k].s = acc[k].c = 0.0;
-  const int64_t warps = (int64_t)gridDim.x * 4;
-  for (int64_t r = (int64_t)blockIdx.x * 4 + wib; r < A.m; r += warps) {
-    int L = 0;
-#pragma unroll
-    for (int j = 0; j < N; ++j) L += A.level[(size_t)j * A.m + r];
-    const double vol = pow2_neg(L) * prm.vol;
-    for (int e = lane; e < N * kCodes; e += 32) {
-      const int j = e / kCodes, code = e - j * kCodes;
-      const int lv = A.level[(size_t)j * A.m + r];
-      const double h = 0.5 * pow2_neg(lv);
-      const double x = point_x(prm, j, A.lower[(size_t)j * A.m + r] + h, h, code_offset(R, code));
-      const double ph = F::factor(F::axis(prm, j), x);
-      double a0, a1;
-      F::dlog(prm, j, x, ph, a0, a1);
-      phi[j][code] = ph;
-      d0[j][code] = a0;
-      d1[j][code] = a1;
-    }
-    __syncwarp();
-    double loc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) loc[k] = 0.0;
-    for (int p = lane; p < A.npts; p += 32) {
-      const uint64_t w = A.codes[p];
-      double f = 1.0;
-#pragma unroll
-      for (int j = 0; j < N; ++j) f *= phi[j][(w >> (4 * j)) & 15];
-      const double wf = vol * R.w[(int)(w >> 32)][0] * f;
-      loc[0] += wf;
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        const int code = (int)((w >> (4 * j)) & 15);
-        loc[1 + j] = fma(wf, d0[j][code], loc[1 + j]);
-        loc[1 + N + j] = fma(wf, d1[j][code], loc[1 + N + j]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) nadd(acc[k], loc[k]);
-    __syncwarp();
-  }
-  // warp, then block reduction (fixed order)
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc[k] = ncomb(acc[k], shfl_down_nsum(acc[k], off));
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < K; ++k) red[wib][k] = acc[k];
-  __syncthreads();
-  if (threadIdx.x < K) {
-    NSum t = red[0][threadIdx.x];
-    for (int wq = 1; wq < 4; ++wq) t = ncomb(t, red[wq][threadIdx.x]);
-    A.part[((size_t)blockIdx.x * K + threadIdx.x) * 2] = t.s;
-    A.part[((size_t)blockIdx.x * K + threadIdx.x) * 2 + 1] = t.c;
-  }
-  if (!last_block_arrived(A.ticket)) return;
-  if (threadIdx.x < K) {
-    NSum t = {0.0, 0.0};
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-      NSum q;
-      q.s = A.part[((size_t)b * K + threadIdx.x) * 2];
-      q.c = A.part[((size_t)b * K + threadIdx.x) * 2 + 1];
-      t = ncomb(t, q);
-    }
-    A.out[threadIdx.x] = nval(t);
-  }
-}
-
 // ---------------------------------------------------------------- launchers
 template <class F, int N, int THREADS, int DEG = 9>
 cudaError_t launch_loop(const EvalRule& R, const LoopArgs& A, int grid, int block, size_t smem, cudaStream_t st) {
@@ -1048,86 +958,10 @@ cudaError_t launch_standalone(const EvalRule& R, const StandaloneArgs& A, int gr
   return cudaGetLastError();
 }
 
-template <class F, int N>
-cudaError_t launch_grad(const EvalRule& R, const GradArgs& A, int grid, cudaStream_t st) {
-  if constexpr (F::kHasGrad) {
-    k_gradient<F, N><<<grid, 128, 0, st>>>(R, A);
-    return cudaGetLastError();
-  } else {
-    return cudaErrorNotSupported;
-  }
-}
-
 template <class F, int N, int THREADS>
 cudaError_t launch_batch_eval(const EvalRule& R, const BatchArgs& A, const BatchGroup& G, int grid, cudaStream_t st) {
   k_evaluate_batch<F, N, THREADS><<<grid, THREADS, sizeof(typename F::T) * kCodes * N * THREADS, st>>>(R, A, G);
   return cudaGetLastError();
 }
-
-template <template <int> class FamOf, int THREADS>
-FamilyKernels make_family_kernels() {
-  FamilyKernels k = {};
-  k.threads = THREADS;
-#define PG_SET(NN)                                                                              \
-  k.loop[NN] = &launch_loop<FamOf<NN>, NN, THREADS>;                                            \
-  k.fill[NN] = &launch_fill<FamOf<NN>, NN>;                                                     \
-  k.grad[NN] = &launch_grad<FamOf<NN>, NN>;                                                     \
-  k.batch_eval[NN] = &launch_batch_eval<FamOf<NN>, NN, THREADS>;                                \
-  k.batch_eval_fn[NN] = (const void*)&k_evaluate_batch<FamOf<NN>, NN, THREADS>;                 \
-  cudaFuncSetAttribute((const void*)&k_evaluate_batch<FamOf<NN>, NN, THREADS>,                  \
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
-                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
-  k.fill_fn[NN] = (const void*)&k_factor_cache<FamOf<NN>, NN>;                                  \
-  k.standalone[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, false>;                         \
-  k.standalone_diag[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, true>;                     \
-  k.loop_fn[NN] = (const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS>;                        \
-  k.table_bytes_per_thread[NN] = (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN);           \
-  cudaFuncSetAttribute((const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS>,                   \
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
-                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
-  cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, false>,      \
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
-                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
-  cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, true>,       \
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
-                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));
-  PG_SET(2) PG_SET(3) PG_SET(4) PG_SET(5) PG_SET(6) PG_SET(7) PG_SET(8)
-#undef PG_SET
-  return k;
-}
-
-// The Genz-Malik degree-7 variant: the loop, factor-cache fill and
-// standalone kernels (no batched form, no gradient).
-template <template <int> class FamOf, int THREADS>
-FamilyKernels make_family_kernels_gm7() {
-  FamilyKernels k = {};
-  k.threads = THREADS;
-#define PG_SET(NN)                                                                              \
-  k.loop[NN] = &launch_loop<FamOf<NN>, NN, THREADS, 7>;                                         \
-  k.fill[NN] = &launch_fill<FamOf<NN>, NN>;                                                     \
-  k.fill_fn[NN] = (const void*)&k_factor_cache<FamOf<NN>, NN>;                                  \
-  k.standalone[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, false, 7>;                      \
-  k.standalone_diag[NN] = &launch_standalone<FamOf<NN>, NN, THREADS, true, 7>;                  \
-  k.loop_fn[NN] = (const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS, 7>;                     \
-  k.table_bytes_per_thread[NN] = (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN);           \
-  cudaFuncSetAttribute((const void*)&k_evaluate_loop<FamOf<NN>, NN, THREADS, 7>,                \
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
-                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
-  cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, false, 7>,   \
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
-                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));          \
-  cudaFuncSetAttribute((const void*)&k_evaluate_standalone<FamOf<NN>, NN, THREADS, true, 7>,    \
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
-                       (int)(sizeof(typename FamOf<NN>::T) * kCodes * NN * THREADS));
-  PG_SET(2) PG_SET(3) PG_SET(4) PG_SET(5) PG_SET(6) PG_SET(7) PG_SET(8)
-#undef PG_SET
-  return k;
-}
-
-template <class F>
-struct Fixed {
-  template <int N>
-  using type = F;
-};
 
 }  // namespace pg

@@ -1,0 +1,253 @@
+// Differentiation of the rule estimate over a frozen box list: the backward
+// pass of the converged integral (the paper defines no derivative).
+#pragma once
+#include "pagani_eval.cuh"
+
+namespace pg {
+
+// -------------------------------------------------- gradient, thread per box
+// d/dtheta of the basic-rule estimate summed over a fixed list of boxes (the
+// leaf set of an integration), and the estimate itself, for theta = (p0_j,
+// p1_j) of every axis.  One thread per box.
+//
+// For a product integrand f = prod_j phi_j(x_j), the box's basic-rule value
+// V = sum_g w_g sum_{x in orbit g} f(x) is multilinear in the per-axis factor
+// values t_j(c) = phi_j(x at code c): every rule point takes exactly one
+// factor from each axis.  Summed over the +/- signs of an orbit, the factors
+// of one non-centre radius enter only as s_j(r) = t_j(r+) + t_j(r-), so
+//   V = w_0 P + sum_j Q_j (w_1 s_j(1) + w_2 s_j(2) + w_3 s_j(3))
+//     + sum_{j<k} Q_jk (w_5 s_j(1) s_k(1) + w_6 (s_j(1) s_k(2) + s_j(2) s_k(1)))
+//     + sum_{j<k<l} w_7 Q_jkl s_j(1) s_k(1) s_l(1) + w_8 prod_j s_j(0),
+// with P the product of the centre factors and Q_... the same product
+// without the named axes (the lambda_p orbit has zero basic weight).  Then
+// H_j(r) = dV/ds_j(r) is a sum of leave-one-out products, and by the chain
+// rule, with dt_j(c)/dtheta = t_j(c) dlog phi_j(x_c)/dtheta,
+//   dV/dtheta_j = sum_{c != C0} dlog_j(c) t_j(c) H_j(r(c)) + dlog_j(C0) G_j(C0),
+// where G_j(C0) = V - sum_r s_j(r) H_j(r) is the part of V whose points sit
+// at the centre on axis j (V is linear in axis j's factors, one per point).
+// The orbit's 2, 4 or 8 sign combinations, and the 2^n vertices, are never
+// formed one by one.  Per thread in shared memory: the 9 factor values used
+// per axis (C0, r1+-, r2+-, r3+-, r0+-), read from the factor cache where
+// the box's level on that axis is cached, and the 2n + 1 running sums.
+template <int N, int GT>
+struct GradSmem {
+  static constexpr int kTab = 9;         // factor values per axis
+  static constexpr int kSums = 2 * N + 1;  // V, d/dp0_j, d/dp1_j
+  static constexpr size_t bytes = ((size_t)kSums * sizeof(NSum) + (size_t)kTab * N * sizeof(double)) * GT;
+};
+
+__device__ __forceinline__ int grad_code(int slot) {  // compact table slot -> Code
+  return slot < 7 ? slot : slot + 2;                  // 0..6 as is, 7, 8 -> kR0P, kR0M
+}
+
+template <class F, int N, int GT>
+__global__ void __launch_bounds__(GT) k_gradient_box(const EvalRule R, const GradArgs A) {
+  extern __shared__ __align__(16) unsigned char gsmem[];
+  constexpr int K = GradSmem<N, GT>::kSums;
+  NSum* acc = reinterpret_cast<NSum*>(gsmem);                               // [k][thread]
+  double* tab = reinterpret_cast<double*>(acc + K * GT) + threadIdx.x;      // [slot][j], stride GT
+#define PG_T(slot, j) tab[((slot) * N + (j)) * GT]
+  const IntegrandParams& prm = *A.prm;
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k * GT + threadIdx.x] = NSum{0.0, 0.0};
+  const double w0 = R.w[kGenCentre][0], w1 = R.w[kGenL1][0], w2 = R.w[kGenL2][0], w3 = R.w[kGenL3][0];
+  const double w5 = R.w[kGenL1L1][0], w6 = R.w[kGenL1L2][0], w7 = R.w[kGenL1L1L1][0], w8 = R.w[kGenL0All][0];
+  for (int64_t r = (int64_t)blockIdx.x * GT + threadIdx.x; r < A.m; r += (int64_t)gridDim.x * GT) {
+    int L = 0;
+    double s1[N], s2[N], s3[N], s0[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const double lo = A.lower[(size_t)j * A.m + r];
+      const int lv = A.level[(size_t)j * A.m + r];
+      L += lv;
+      if (A.fcache != nullptr && lv <= A.fcache_levels) {  // same expression, same bits
+        const double* src = A.fcache + ((size_t)j * kCacheSlots + ((1 << lv) - 1) + dyadic_index(lo, lv)) * kCodes;
+#pragma unroll
+        for (int slot = 0; slot < GradSmem<N, GT>::kTab; ++slot) PG_T(slot, j) = src[grad_code(slot)];
+      } else {
+        const double h = 0.5 * pow2_neg(lv);
+        const typename F::Ax ax = F::axis(prm, j);
+#pragma unroll
+        for (int slot = 0; slot < GradSmem<N, GT>::kTab; ++slot)
+          PG_T(slot, j) = F::factor(ax, point_x(prm, j, lo + h, h, code_offset(R, grad_code(slot))));
+      }
+      s1[j] = PG_T(1, j) + PG_T(2, j);
+      s2[j] = PG_T(3, j) + PG_T(4, j);
+      s3[j] = PG_T(5, j) + PG_T(6, j);
+      s0[j] = PG_T(7, j) + PG_T(8, j);
+    }
+    // prefix / suffix products of the centre factors
+    double pre[N + 1], suf[N + 1];
+    pre[0] = 1.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) pre[j + 1] = pre[j] * PG_T(0, j);
+    suf[N] = 1.0;
+#pragma unroll
+    for (int j = N - 1; j >= 0; --j) suf[j] = PG_T(0, j) * suf[j + 1];
+    double H1[N], H2[N], H3[N], H0[N];
+    double V = w0 * pre[N];
+    // one-axis orbits
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const double Q = pre[j] * suf[j + 1];
+      H1[j] = w1 * Q;
+      H2[j] = w2 * Q;
+      H3[j] = w3 * Q;
+      V = fma(H1[j], s1[j], V);
+      V = fma(H2[j], s2[j], V);
+      V = fma(H3[j], s3[j], V);
+    }
+    // axis pairs j < k: (r1, r1) and both orders of (r1, r2)
+#pragma unroll
+    for (int j = 0; j < N - 1; ++j) {
+      double PM = pre[j];
+#pragma unroll
+      for (int k = j + 1; k < N; ++k) {
+        if (k > j + 1) PM = PM * PG_T(0, k - 1);
+        const double Q = PM * suf[k + 1];
+        const double q5 = w5 * Q, q6 = w6 * Q;
+        const double a = fma(q5, s1[k], q6 * s2[k]);  // dV/ds_j(1)
+        const double b = q6 * s1[k];                  // dV/ds_j(2)
+        H1[j] += a;
+        H2[j] += b;
+        H1[k] += fma(q5, s1[j], q6 * s2[j]);
+        H2[k] = fma(q6, s1[j], H2[k]);
+        V = fma(a, s1[j], V);
+        V = fma(b, s2[j], V);
+      }
+    }
+    // axis triples at r1
+    if constexpr (N >= 3) {
+#pragma unroll
+      for (int j = 0; j < N - 2; ++j) {
+        double PM1 = pre[j];
+#pragma unroll
+        for (int k = j + 1; k < N - 1; ++k) {
+          if (k > j + 1) PM1 = PM1 * PG_T(0, k - 1);
+          double PM2 = PM1;
+#pragma unroll
+          for (int l = k + 1; l < N; ++l) {
+            if (l > k + 1) PM2 = PM2 * PG_T(0, l - 1);
+            const double Q = w7 * (PM2 * suf[l + 1]);
+            const double qj = Q * s1[j];
+            const double qjk = qj * s1[k];  // dV/ds_l(1)
+            H1[l] += qjk;
+            H1[k] = fma(qj, s1[l], H1[k]);
+            H1[j] = fma(Q * s1[k], s1[l], H1[j]);
+            V = fma(qjk, s1[l], V);
+          }
+        }
+      }
+    }
+    // every axis at r0: w_8 prod_j s_j(0), and its leave-one-out products
+    {
+      double run = w8;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        H0[j] = run;
+        run *= s0[j];
+      }
+      V += run;
+      double sr = 1.0;
+#pragma unroll
+      for (int j = N - 1; j >= 0; --j) {
+        H0[j] *= sr;
+        sr *= s0[j];
+      }
+    }
+    // per axis: the chain rule through the nine factor values
+    const double vol = pow2_neg(L) * prm.vol;
+    {
+      NSum t = acc[threadIdx.x];
+      nadd(t, vol * V);
+      acc[threadIdx.x] = t;
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const double lo = A.lower[(size_t)j * A.m + r];
+      const double h = 0.5 * pow2_neg(A.level[(size_t)j * A.m + r]);
+      const double Hs[4] = {H1[j], H2[j], H3[j], H0[j]};  // radius of slots 2i+1, 2i+2
+      double g0 = 0.0, g1 = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        double e0 = 0.0, e1 = 0.0;
+#pragma unroll
+        for (int sg = 0; sg < 2; ++sg) {
+          const int slot = 2 * i + 1 + sg;
+          const double tc = PG_T(slot, j);
+          const double x = point_x(prm, j, lo + h, h, code_offset(R, grad_code(slot)));
+          double d0, d1;
+          F::dlog(prm, j, x, tc, d0, d1);
+          e0 = fma(d0, tc, e0);
+          e1 = fma(d1, tc, e1);
+        }
+        g0 = fma(e0, Hs[i], g0);
+        g1 = fma(e1, Hs[i], g1);
+      }
+      {
+        const double gc = V - fma(s1[j], H1[j], fma(s2[j], H2[j], fma(s3[j], H3[j], s0[j] * H0[j])));
+        const double x = point_x(prm, j, lo + h, h, 0.0);
+        double d0, d1;
+        F::dlog(prm, j, x, PG_T(0, j), d0, d1);
+        g0 = fma(d0, gc, g0);
+        g1 = fma(d1, gc, g1);
+      }
+      NSum t0 = acc[(1 + j) * GT + threadIdx.x], t1 = acc[(1 + N + j) * GT + threadIdx.x];
+      nadd(t0, vol * g0);
+      nadd(t1, vol * g1);
+      acc[(1 + j) * GT + threadIdx.x] = t0;
+      acc[(1 + N + j) * GT + threadIdx.x] = t1;
+    }
+  }
+#undef PG_T
+  // block, then grid reduction (fixed order)
+  __syncthreads();
+  NSum* red = acc;
+  if (threadIdx.x < K) {
+    NSum t = red[threadIdx.x * GT];
+    for (int q = 1; q < GT; ++q) t = ncomb(t, red[threadIdx.x * GT + q]);
+    A.part[((size_t)blockIdx.x * K + threadIdx.x) * 2] = t.s;
+    A.part[((size_t)blockIdx.x * K + threadIdx.x) * 2 + 1] = t.c;
+  }
+  if (!last_block_arrived(A.ticket)) return;
+  // K sums over the blocks: threads split the blocks of each sum, then fold
+  __syncthreads();
+  constexpr int PER = GT / K > 0 ? GT / K : 1;
+  if (threadIdx.x < K * PER) {
+    const int k = threadIdx.x / PER, part = threadIdx.x % PER;
+    NSum t = {0.0, 0.0};
+    for (unsigned b = part; b < gridDim.x; b += PER) {
+      NSum q;
+      q.s = A.part[((size_t)b * K + k) * 2];
+      q.c = A.part[((size_t)b * K + k) * 2 + 1];
+      t = ncomb(t, q);
+    }
+    red[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    NSum t = red[threadIdx.x * PER];
+    for (int q = 1; q < PER; ++q) t = ncomb(t, red[threadIdx.x * PER + q]);
+    A.out[threadIdx.x] = nval(t);
+  }
+}
+
+// ---------------------------------------------------------------- launcher
+template <class F, int N>
+cudaError_t launch_grad(const EvalRule& R, const GradArgs& A, int grid, cudaStream_t st) {
+  if constexpr (F::kHasGrad) {
+    const size_t smem = GradSmem<N, kGradThreads>::bytes;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute((const void*)&k_gradient_box<F, N, kGradThreads>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    k_gradient_box<F, N, kGradThreads><<<grid, kGradThreads, smem, st>>>(R, A);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace pg

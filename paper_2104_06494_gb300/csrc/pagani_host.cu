@@ -1991,19 +1991,29 @@ int pagani_gradient(int dim, int integrand_id, const double* params, int64_t m, 
   IntegrandParams prm = to_params(integrand_id, dim, params);
   cudaError_t e = cudaMemcpyAsync(w.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
+  // the factor cache, filled for these parameters (the gradient reads the
+  // factor values of cached levels from it, as Evaluate does)
+  const EvalRule rule = to_eval_rule(*rt);
+  {
+    LoopArgs la = loop_args(dim, 0, 0, 0);
+    int fill_grid = w.sms * 2;
+    if (fill_grid > w.max_grid) fill_grid = w.max_grid;
+    e = family_kernels(integrand_id).fill[dim](rule, la, fill_grid, 256, 0, st);
+    if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("factor cache: ") + cudaGetErrorString(e));
+  }
   GradArgs a;
   a.lower = lower;
   a.level = level;
   a.m = m;
-  a.codes = w.codes[dim];
-  a.npts = w.ncodes[dim];
   a.prm = w.prm;
+  a.fcache = static_cast<const double*>(w.fcache);
+  a.fcache_levels = kCacheLevels;
   a.part = w.grad_part;
   a.ticket = w.grad_ticket;
   a.out = w.grad_out;
-  int64_t grid = (m + 3) / 4;
+  int64_t grid = (m + kGradThreads - 1) / kGradThreads;
   if (grid > w.max_grid) grid = w.max_grid;
-  e = family_kernels(integrand_id).grad[dim](to_eval_rule(*rt), a, (int)grid, st);
+  e = family_kernels(integrand_id).grad[dim](rule, a, (int)grid, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, w.grad_out, sizeof(double) * K, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, std::string("gradient: ") + cudaGetErrorString(e));

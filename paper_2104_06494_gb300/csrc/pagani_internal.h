@@ -222,14 +222,15 @@ struct GradArgs {
   const double* lower;     // [n][m]
   const uint8_t* level;    // [n][m]
   int64_t m;
-  const uint64_t* codes;   // packed rule points
-  int npts;
   const IntegrandParams* prm;
+  const double* fcache;    // per-axis factor cache filled for prm (levels <= fcache_levels), or null
+  int fcache_levels;
   double* part;            // per block: 2n + 1 Neumaier pairs (value, gradient)
   unsigned int* ticket;
   double* out;             // 2n + 1 totals (value first)
 };
 typedef cudaError_t (*GradLauncher)(const EvalRule&, const GradArgs&, int grid, cudaStream_t);
+constexpr int kGradThreads = 64;  // gradient kernel: one thread per box
 
 // Arguments of the standalone evaluate entry point.
 struct StandaloneArgs {
