@@ -26,32 +26,103 @@ namespace pg {
 // where G_j(C0) = V - sum_r s_j(r) H_j(r) is the part of V whose points sit
 // at the centre on axis j (V is linear in axis j's factors, one per point).
 // The orbit's 2, 4 or 8 sign combinations, and the 2^n vertices, are never
-// formed one by one.  Per thread in shared memory: the 9 factor values used
-// per axis (C0, r1+-, r2+-, r3+-, r0+-), read from the factor cache where
-// the box's level on that axis is cached, and the 2n + 1 running sums.
+// formed one by one.
+//
+// The chain-rule factors depend only on the axis interval, like the factor
+// values: per interval, dlog_j(C0) and, per radius r, sum over its two signs
+// of t_j(c) dlog_j(c) (kGradTerms values).  They are tabulated for every
+// cached interval ahead of the gradient kernel and computed in place for
+// deeper levels, by the same function.  Per thread in shared memory: the 9
+// factor values used per axis (C0, r1+-, r2+-, r3+-, r0+-), read from the
+// factor cache where the box's level on that axis is cached, and the 2n + 1
+// sums: plain over up to kGradChunk boxes, then added into Neumaier pairs.
+constexpr int kGradChunk = 8;
+
 template <int N, int GT>
 struct GradSmem {
-  static constexpr int kTab = 9;         // factor values per axis
+  static constexpr int kTab = 9;           // factor values per axis
   static constexpr int kSums = 2 * N + 1;  // V, d/dp0_j, d/dp1_j
-  static constexpr size_t bytes = ((size_t)kSums * sizeof(NSum) + (size_t)kTab * N * sizeof(double)) * GT;
+  static constexpr size_t bytes =
+      ((size_t)kSums * (sizeof(NSum) + sizeof(double)) + (size_t)kTab * N * sizeof(double)) * GT;
 };
 
 __device__ __forceinline__ int grad_code(int slot) {  // compact table slot -> Code
   return slot < 7 ? slot : slot + 2;                  // 0..6 as is, 7, 8 -> kR0P, kR0M
 }
 
+// The chain-rule terms of axis j for the box [lo, lo + 2h) from its nine
+// factor values t[slot * TS]: o[0], o[1] = dlog phi_j / d(p0_j, p1_j) at the
+// centre; o[2 + 2i], o[3 + 2i] = the sum over the two signs of radius i (r1,
+// r2, r3, r0) of t dlog phi_j / d(p0_j, p1_j).
+template <class F, int TS>
+__device__ __forceinline__ void grad_axis_terms(const EvalRule& R, const IntegrandParams& prm, int j, double lo,
+                                                double h, const double* t, double* o) {
+  {
+    double d0, d1;
+    F::dlog(prm, j, point_x(prm, j, lo + h, h, 0.0), t[0], d0, d1);
+    o[0] = d0;
+    o[1] = d1;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    double e0 = 0.0, e1 = 0.0;
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      const int slot = 2 * i + 1 + sg;
+      const double tc = t[slot * TS];
+      double d0, d1;
+      F::dlog(prm, j, point_x(prm, j, lo + h, h, code_offset(R, grad_code(slot))), tc, d0, d1);
+      e0 = fma(d0, tc, e0);
+      e1 = fma(d1, tc, e1);
+    }
+    o[2 + 2 * i] = e0;
+    o[3 + 2 * i] = e1;
+  }
+}
+
+// Tabulates the chain-rule terms of every cached interval (levels <= L),
+// slot 2^l - 1 + k for [k 2^-l, (k+1) 2^-l), as the factor cache does.
+template <class F, int N>
+__global__ void __launch_bounds__(256) k_grad_terms(const EvalRule R, const GradArgs A) {
+  const IntegrandParams& prm = *A.prm;
+  const long long slots = (2LL << A.fcache_levels) - 1;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)N * slots;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long slot = idx % slots;
+    const int j = (int)(idx / slots);
+    const int L = 63 - __clzll(slot + 1);  // slot = 2^L - 1 + k
+    const long long k = slot + 1 - (1LL << L);
+    const double h = 0.5 * pow2_neg(L);
+    const double lo = (double)k * pow2_neg(L);
+    const typename F::Ax ax = F::axis(prm, j);
+    double t[9], o[kGradTerms];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) t[q] = F::factor(ax, point_x(prm, j, lo + h, h, code_offset(R, grad_code(q))));
+    grad_axis_terms<F, 1>(R, prm, j, lo, h, t, o);
+    double* dst = A.terms + ((size_t)j * kCacheSlots + slot) * kGradTerms;
+#pragma unroll
+    for (int q = 0; q < kGradTerms; ++q) dst[q] = o[q];
+  }
+}
+
 template <class F, int N, int GT>
 __global__ void __launch_bounds__(GT) k_gradient_box(const EvalRule R, const GradArgs A) {
   extern __shared__ __align__(16) unsigned char gsmem[];
   constexpr int K = GradSmem<N, GT>::kSums;
-  NSum* acc = reinterpret_cast<NSum*>(gsmem);                               // [k][thread]
-  double* tab = reinterpret_cast<double*>(acc + K * GT) + threadIdx.x;      // [slot][j], stride GT
+  NSum* acc = reinterpret_cast<NSum*>(gsmem);                           // [k][thread]
+  double* part = reinterpret_cast<double*>(acc + K * GT) + threadIdx.x;  // [k], stride GT: plain chunk sums
+  double* tab = part + K * GT;                                          // [slot][j], stride GT
 #define PG_T(slot, j) tab[((slot) * N + (j)) * GT]
   const IntegrandParams& prm = *A.prm;
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k * GT + threadIdx.x] = NSum{0.0, 0.0};
+  for (int k = 0; k < K; ++k) {
+    acc[k * GT + threadIdx.x] = NSum{0.0, 0.0};
+    part[k * GT] = 0.0;
+  }
   const double w0 = R.w[kGenCentre][0], w1 = R.w[kGenL1][0], w2 = R.w[kGenL2][0], w3 = R.w[kGenL3][0];
   const double w5 = R.w[kGenL1L1][0], w6 = R.w[kGenL1L2][0], w7 = R.w[kGenL1L1L1][0], w8 = R.w[kGenL0All][0];
+  const bool cached = A.fcache != nullptr && A.terms != nullptr;
+  int chunk = 0;
   for (int64_t r = (int64_t)blockIdx.x * GT + threadIdx.x; r < A.m; r += (int64_t)gridDim.x * GT) {
     int L = 0;
     double s1[N], s2[N], s3[N], s0[N];
@@ -60,7 +131,7 @@ __global__ void __launch_bounds__(GT) k_gradient_box(const EvalRule R, const Gra
       const double lo = A.lower[(size_t)j * A.m + r];
       const int lv = A.level[(size_t)j * A.m + r];
       L += lv;
-      if (A.fcache != nullptr && lv <= A.fcache_levels) {  // same expression, same bits
+      if (cached && lv <= A.fcache_levels) {  // same expression, same bits
         const double* src = A.fcache + ((size_t)j * kCacheSlots + ((1 << lv) - 1) + dyadic_index(lo, lv)) * kCodes;
 #pragma unroll
         for (int slot = 0; slot < GradSmem<N, GT>::kTab; ++slot) PG_T(slot, j) = src[grad_code(slot)];
@@ -155,49 +226,52 @@ __global__ void __launch_bounds__(GT) k_gradient_box(const EvalRule R, const Gra
         sr *= s0[j];
       }
     }
-    // per axis: the chain rule through the nine factor values
+    // per axis: the chain rule through the tabulated terms
     const double vol = pow2_neg(L) * prm.vol;
-    {
-      NSum t = acc[threadIdx.x];
-      nadd(t, vol * V);
-      acc[threadIdx.x] = t;
-    }
+    part[0] = fma(vol, V, part[0]);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       const double lo = A.lower[(size_t)j * A.m + r];
-      const double h = 0.5 * pow2_neg(A.level[(size_t)j * A.m + r]);
-      const double Hs[4] = {H1[j], H2[j], H3[j], H0[j]};  // radius of slots 2i+1, 2i+2
-      double g0 = 0.0, g1 = 0.0;
+      const int lv = A.level[(size_t)j * A.m + r];
+      double o[kGradTerms];
+      if (cached && lv <= A.fcache_levels) {
+        const double* src =
+            A.terms + ((size_t)j * kCacheSlots + ((1 << lv) - 1) + dyadic_index(lo, lv)) * kGradTerms;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        double e0 = 0.0, e1 = 0.0;
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-          const int slot = 2 * i + 1 + sg;
-          const double tc = PG_T(slot, j);
-          const double x = point_x(prm, j, lo + h, h, code_offset(R, grad_code(slot)));
-          double d0, d1;
-          F::dlog(prm, j, x, tc, d0, d1);
-          e0 = fma(d0, tc, e0);
-          e1 = fma(d1, tc, e1);
-        }
-        g0 = fma(e0, Hs[i], g0);
-        g1 = fma(e1, Hs[i], g1);
+        for (int q = 0; q < kGradTerms; ++q) o[q] = src[q];
+      } else {
+        grad_axis_terms<F, N * GT>(R, prm, j, lo, 0.5 * pow2_neg(lv), &PG_T(0, j), o);
       }
-      {
-        const double gc = V - fma(s1[j], H1[j], fma(s2[j], H2[j], fma(s3[j], H3[j], s0[j] * H0[j])));
-        const double x = point_x(prm, j, lo + h, h, 0.0);
-        double d0, d1;
-        F::dlog(prm, j, x, PG_T(0, j), d0, d1);
-        g0 = fma(d0, gc, g0);
-        g1 = fma(d1, gc, g1);
-      }
-      NSum t0 = acc[(1 + j) * GT + threadIdx.x], t1 = acc[(1 + N + j) * GT + threadIdx.x];
-      nadd(t0, vol * g0);
-      nadd(t1, vol * g1);
-      acc[(1 + j) * GT + threadIdx.x] = t0;
-      acc[(1 + N + j) * GT + threadIdx.x] = t1;
+      // the part of V at the centre on axis j
+      const double gc = V - fma(s1[j], H1[j], fma(s2[j], H2[j], fma(s3[j], H3[j], s0[j] * H0[j])));
+      double g0 = o[0] * gc, g1 = o[1] * gc;
+      g0 = fma(o[2], H1[j], g0);
+      g1 = fma(o[3], H1[j], g1);
+      g0 = fma(o[4], H2[j], g0);
+      g1 = fma(o[5], H2[j], g1);
+      g0 = fma(o[6], H3[j], g0);
+      g1 = fma(o[7], H3[j], g1);
+      g0 = fma(o[8], H0[j], g0);
+      g1 = fma(o[9], H0[j], g1);
+      part[(1 + j) * GT] = fma(vol, g0, part[(1 + j) * GT]);
+      part[(1 + N + j) * GT] = fma(vol, g1, part[(1 + N + j) * GT]);
     }
+    if (++chunk == kGradChunk) {  // plain over the chunk, compensated across chunks
+      chunk = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        NSum t = acc[k * GT + threadIdx.x];
+        nadd(t, part[k * GT]);
+        acc[k * GT + threadIdx.x] = t;
+        part[k * GT] = 0.0;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    NSum t = acc[k * GT + threadIdx.x];
+    nadd(t, part[k * GT]);
+    acc[k * GT + threadIdx.x] = t;
   }
 #undef PG_T
   // block, then grid reduction (fixed order)
@@ -242,6 +316,12 @@ cudaError_t launch_grad(const EvalRule& R, const GradArgs& A, int grid, cudaStre
       cudaFuncSetAttribute((const void*)&k_gradient_box<F, N, kGradThreads>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr = true;
+    }
+    if (A.terms != nullptr && A.fcache != nullptr) {
+      const long long entries = (long long)N * ((2LL << A.fcache_levels) - 1);
+      k_grad_terms<F, N><<<(int)((entries + 255) / 256), 256, 0, st>>>(R, A);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
     }
     k_gradient_box<F, N, kGradThreads><<<grid, kGradThreads, smem, st>>>(R, A);
     return cudaGetLastError();

@@ -439,6 +439,7 @@ struct Workspace {
   int64_t last_leaves = -1;   // leaf count of the last integration that kept them
   uint64_t* codes[kMaxDim + 1] = {nullptr};
   int ncodes[kMaxDim + 1] = {0};
+  double* grad_terms = nullptr;  // per-axis chain-rule terms of the cached intervals
   double* grad_part = nullptr;
   unsigned int* grad_ticket = nullptr;
   double* grad_out = nullptr;
@@ -567,6 +568,7 @@ static int ensure_workspace(int64_t want_cap, int n) {
     PG_ALLOC(fc, (size_t)kMaxDim * kCacheSlots * kCodes);
     w.fcache = fc;
   }
+  PG_ALLOC(w.grad_terms, (size_t)kMaxDim * kCacheSlots * kGradTerms);
   PG_ALLOC(w.grad_part, (size_t)w.max_grid * (2 * kMaxDim + 1) * 2);
   PG_ALLOC(w.grad_ticket, 1);
   PG_ALLOC(w.grad_out, 2 * kMaxDim + 1);
@@ -1992,7 +1994,8 @@ int pagani_gradient(int dim, int integrand_id, const double* params, int64_t m, 
   cudaError_t e = cudaMemcpyAsync(w.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return fail(PAGANI_ERR_CUDA, cudaGetErrorString(e));
   // the factor cache, filled for these parameters (the gradient reads the
-  // factor values of cached levels from it, as Evaluate does)
+  // factor values of cached levels from it, as Evaluate does); the launcher
+  // then fills the chain-rule terms of the same intervals
   const EvalRule rule = to_eval_rule(*rt);
   {
     LoopArgs la = loop_args(dim, 0, 0, 0);
@@ -2008,6 +2011,7 @@ int pagani_gradient(int dim, int integrand_id, const double* params, int64_t m, 
   a.prm = w.prm;
   a.fcache = static_cast<const double*>(w.fcache);
   a.fcache_levels = kCacheLevels;
+  a.terms = w.grad_terms;
   a.part = w.grad_part;
   a.ticket = w.grad_ticket;
   a.out = w.grad_out;

@@ -225,12 +225,14 @@ struct GradArgs {
   const IntegrandParams* prm;
   const double* fcache;    // per-axis factor cache filled for prm (levels <= fcache_levels), or null
   int fcache_levels;
+  double* terms;           // [n][kCacheSlots][kGradTerms] chain-rule terms, filled by the launcher
   double* part;            // per block: 2n + 1 Neumaier pairs (value, gradient)
   unsigned int* ticket;
   double* out;             // 2n + 1 totals (value first)
 };
 typedef cudaError_t (*GradLauncher)(const EvalRule&, const GradArgs&, int grid, cudaStream_t);
 constexpr int kGradThreads = 64;  // gradient kernel: one thread per box
+constexpr int kGradTerms = 10;    // chain-rule terms per axis interval (centre + 4 radii, 2 parameters)
 
 // Arguments of the standalone evaluate entry point.
 struct StandaloneArgs {
