@@ -170,21 +170,35 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
       vv[r] = i < s ? V[i] : 0.0;
       ee[r] = i < s ? E[i] : 0.0;
     }
+    // classification of every item, then the levels of the finished ones
+    // (all loads issued before the first store), then the stores and sums
+    bool actv[ITEMS];
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
+      actv[r] = i < s && final_active(vv[r], ee[r], c);
+    }
+    int Lr[ITEMS];
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) Lr[r] = 0;
+    for (int j = 0; j < n; ++j) {
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r) {
+        const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
+        if (i < s && !actv[r]) Lr[r] += level[(size_t)j * cap + i];
+      }
+    }
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
       if (i < s) {
-        const double v = vv[r], e = ee[r];
-        const bool act = final_active(v, e, c);
-        A.pool.act[i] = act ? 1 : 0;  // the split reads it back
-        if (act) {
+        A.pool.act[i] = actv[r] ? 1 : 0;  // the split reads it back
+        if (actv[r]) {
           ++cnt;
-          tv += v;
-          te += e;
+          tv += vv[r];
+          te += ee[r];
         } else {
-          int L = 0;
-          for (int j = 0; j < n; ++j) L += level[(size_t)j * cap + i];
-          tf += pow2_neg(L);
+          tf += pow2_neg(Lr[r]);
         }
       }
     }
@@ -333,39 +347,60 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
       qv[r] = base + rank;
       base += total;
     }
+    if (logl) {
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r) {
+        const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
+        if (!actv[r] && i < s) {
+          // finished box: its rank among the finished ones is i - (survivors before i)
+          const int64_t pos = c.leaf_count + i - qv[r];
+          if (pos < A.leaves.cap) {
+            for (int j = 0; j < n; ++j) {
+              A.leaves.lower[(size_t)j * A.leaves.cap + pos] = lo_s[(size_t)j * cap + i];
+              A.leaves.level[(size_t)j * A.leaves.cap + pos] = lv_s[(size_t)j * cap + i];
+            }
+          } else {
+            bad |= 2;
+          }
+        }
+      }
+    }
+    // the survivors' copies: every item's loads are issued before any store
+    // (per axis), so a thread waits on one L2 round trip per axis instead of
+    // one per item and axis
+    int kv[ITEMS];
+    double vv[ITEMS];
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-      const bool act = actv[r];
-      if (logl && !act && i < s) {
-        // finished box: its rank among the finished ones is i - (survivors before i)
-        const int64_t pos = c.leaf_count + i - qv[r];
-        if (pos < A.leaves.cap) {
-          for (int j = 0; j < n; ++j) {
-            A.leaves.lower[(size_t)j * A.leaves.cap + pos] = lo_s[(size_t)j * cap + i];
-            A.leaves.level[(size_t)j * A.leaves.cap + pos] = lv_s[(size_t)j * cap + i];
-          }
-        } else {
-          bad |= 2;
-        }
+      kv[r] = actv[r] ? A.pool.K[i] : -1;
+      vv[r] = actv[r] ? A.pool.V[i] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r)
+      if (actv[r]) A.pool.Vp[qv[r]] = vv[r];
+    for (int j = 0; j < n; ++j) {
+      double lo[ITEMS];
+      int lv[ITEMS];
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r) {
+        const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
+        lo[r] = actv[r] ? lo_s[(size_t)j * cap + i] : 0.0;
+        lv[r] = actv[r] ? lv_s[(size_t)j * cap + i] : 0;
       }
-      if (act) {
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r) {
+        if (!actv[r]) continue;
         const int64_t q = qv[r];
-        const int k = A.pool.K[i];
-        A.pool.Vp[q] = A.pool.V[i];
-        for (int j = 0; j < n; ++j) {
-          const double lo = lo_s[(size_t)j * cap + i];
-          const int lv = lv_s[(size_t)j * cap + i];
-          double2 out = make_double2(lo, lo);
-          uchar2 ol = make_uchar2((unsigned char)lv, (unsigned char)lv);
-          if (j == k) {
-            if (lv >= 62) bad = 1;
-            out.y = lo + pow2_neg(lv + 1);
-            ol = make_uchar2((unsigned char)(lv + 1), (unsigned char)(lv + 1));
-          }
-          *reinterpret_cast<double2*>(lo_d + (size_t)j * cap + 2 * q) = out;
-          *reinterpret_cast<uchar2*>(lv_d + (size_t)j * cap + 2 * q) = ol;
+        double2 out = make_double2(lo[r], lo[r]);
+        uchar2 ol = make_uchar2((unsigned char)lv[r], (unsigned char)lv[r]);
+        if (j == kv[r]) {
+          if (lv[r] >= 62) bad = 1;
+          out.y = lo[r] + pow2_neg(lv[r] + 1);
+          ol = make_uchar2((unsigned char)(lv[r] + 1), (unsigned char)(lv[r] + 1));
         }
+        *reinterpret_cast<double2*>(lo_d + (size_t)j * cap + 2 * q) = out;
+        *reinterpret_cast<uchar2*>(lv_d + (size_t)j * cap + 2 * q) = ol;
       }
     }
   }
@@ -881,9 +916,6 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
   if (rc) return out->status = rc;
   const EvalRule rule = to_eval_rule(*rt);
 
-  // pool arrays are laid out for w.n axes; the kernels index with pool.n
-  Pool pool = w.pool;
-  (void)pool;
   Ctrl h;
   std::memset(&h, 0, sizeof(h));
   h.tau_rel = epsrel;
