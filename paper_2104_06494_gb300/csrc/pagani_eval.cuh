@@ -684,6 +684,7 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
   const int64_t npairs = s >> 1;
   const int64_t nwarps = (int64_t)gridDim.x * (THREADS / 32);
   const bool coop = A.codes != nullptr && npairs <= kCoopPasses * nwarps;
+  const bool per_region = !coop && s <= (int64_t)kRegionPasses * gridDim.x * THREADS;
   if (coop) {
     // (parameters read through global memory: the cooperative table build
     // indexes them with a runtime axis, which must not move the kernel's
@@ -691,6 +692,51 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     coop_pairs<F, N, THREADS, DEG>(R, A, *A.prm, lower, level, cap, npairs, it, relerr, tau_rel,
                                    reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * 32 * kCodes * N, sv, se,
                                    svol, emin, emax, nrel, nonfinite);
+  } else if (per_region) {
+    // one thread per region; a warp covers 32 consecutive regions (16
+    // sibling pairs) and stays converged for the sibling exchange
+    const int lane = threadIdx.x & 31;
+    for (int64_t r0 = (int64_t)blockIdx.x * THREADS + (threadIdx.x - lane); r0 < s;
+         r0 += (int64_t)gridDim.x * THREADS) {
+      const int64_t i = r0 + lane;
+      const bool live = i < s;  // s is even: siblings are live together
+      double V = 0.0, E = 0.0;
+      int K = 0, lvsum = 0;
+      if (live) {
+        double wd[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const double lo = lower[(size_t)j * cap + i];
+          const int lv = level[(size_t)j * cap + i];
+          wd[j] = pow2_neg(lv) * prm.len[j];
+          lvsum += lv;
+          axis_entries<F, N, THREADS>(tab, R, prm, fcache, A.fcache_levels, lo, lv, j);
+        }
+        double S[kNumGen], D[N];
+        rule_sums<F, N, THREADS, DEG>(tab, base, R.q, S, D);
+        region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, pow2_neg(lvsum) * prm.vol, wd, V, E, K, nullptr);
+      }
+      const double Vo = __shfl_xor_sync(0xffffffffu, V, 1);
+      const double Eo = __shfl_xor_sync(0xffffffffu, E, 1);
+      if (live) {
+        // both siblings form the same two-level estimate; each keeps its own
+        const bool left = (lane & 1) == 0;
+        const double VL = left ? V : Vo, VR = left ? Vo : V;
+        double EL = left ? E : Eo, ER = left ? Eo : E;
+        if (it > 1) two_level(VL, VR, A.pool.Vp[i >> 1], EL, ER);
+        const double Em = left ? EL : ER;
+        A.pool.V[i] = V;
+        A.pool.E[i] = Em;
+        A.pool.K[i] = (unsigned char)K;
+        nadd(sv, V);
+        nadd(se, Em);
+        nadd(svol, pow2_neg(lvsum));
+        emin = fmin(emin, Em);
+        emax = fmax(emax, Em);
+        nrel += relerr_active(V, Em, tau_rel, relerr);
+        if (!isfinite(V) || !isfinite(Em)) nonfinite = 1;
+      }
+    }
   } else
   for (int64_t p = (int64_t)blockIdx.x * THREADS + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * THREADS) {
     const int64_t iL = 2 * p;
@@ -754,10 +800,12 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
   // instruction occupies its scheduler's FP64 unit about 64 cycles), and the
   // last block combines only the partials of blocks that had pairs, which
   // leaves every sum bit for bit unchanged
-  // (cooperative: pair p on warp p mod nwarps, THREADS/32 warps a block)
+  // (cooperative: pair p on warp p mod nwarps, THREADS/32 warps a block;
+  // per region: region i on thread i mod (grid threads))
+  const int64_t units = per_region ? s : npairs;
   const int64_t per_block = coop ? THREADS / 32 : THREADS;
-  const int64_t nparts_eval = (npairs + per_block - 1) / per_block < (int64_t)gridDim.x
-                                  ? (npairs + per_block - 1) / per_block
+  const int64_t nparts_eval = (units + per_block - 1) / per_block < (int64_t)gridDim.x
+                                  ? (units + per_block - 1) / per_block
                                   : (int64_t)gridDim.x;
   if ((int64_t)blockIdx.x < nparts_eval) {
     EvalPartial mine;

@@ -210,12 +210,17 @@ struct LoopArgs {
   int gen_off[kNumGen + 1];
 };
 
-// Evaluate switches to one warp per sibling pair while the pairs fit in this
-// many passes of all the launch's warps (few regions: the thread-per-pair
-// form would leave most of the GPU idle).  Measured on the 5-D Gaussian
-// (1216 warps): 59 and 62 us against 96 us at 512 and 1024 pairs, 89 against
-// 96 at 2048, 129 against 96 at 4096.
-constexpr int kCoopPasses = 2;
+// Evaluate's three forms, by the number of regions s of the iteration:
+//  * one warp per sibling pair while the pairs fit in kCoopPasses passes of
+//    all the launch's warps;
+//  * one thread per region (sibling lanes exchange values for the two-level
+//    estimate) while the regions fit in kRegionPasses passes of its threads;
+//  * one thread per sibling pair (the shared factor table) beyond.
+// A warp alone on a scheduler runs its dependent FP64 chains at about 64
+// cycles per step, so while few warps exist, halving each warp's chain
+// (a region instead of a pair) shortens the launch.
+constexpr int kCoopPasses = 1;
+constexpr int kRegionPasses = 2;
 
 // Arguments of the gradient kernel.
 struct GradArgs {
