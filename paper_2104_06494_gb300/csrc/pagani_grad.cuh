@@ -19,9 +19,11 @@ namespace pg {
 //     + sum_{j<k} Q_jk (w_5 s_j(1) s_k(1) + w_6 (s_j(1) s_k(2) + s_j(2) s_k(1)))
 //     + sum_{j<k<l} w_7 Q_jkl s_j(1) s_k(1) s_l(1) + w_8 prod_j s_j(0),
 // with P the product of the centre factors and Q_... the same product
-// without the named axes (the lambda_p orbit has zero basic weight).  Then
-// H_j(r) = dV/ds_j(r) is a sum of leave-one-out products, and by the chain
-// rule, with dt_j(c)/dtheta = t_j(c) dlog phi_j(x_c)/dtheta,
+// without the named axes (the lambda_p orbit has zero basic weight).  These
+// sums are coefficients of one polynomial, prod_j (t0_j + z s_j(1) +
+// y s_j(2) + x s_j(3)), so prefix and suffix products of it give V and
+// H_j(r) = dV/ds_j(r) in O(n) operations.  By the chain rule, with
+// dt_j(c)/dtheta = t_j(c) dlog phi_j(x_c)/dtheta,
 //   dV/dtheta_j = sum_{c != C0} dlog_j(c) t_j(c) H_j(r(c)) + dlog_j(C0) G_j(C0),
 // where G_j(C0) = V - sum_r s_j(r) H_j(r) is the part of V whose points sit
 // at the centre on axis j (V is linear in axis j's factors, one per point).
@@ -147,90 +149,66 @@ __global__ void __launch_bounds__(GT) k_gradient_box(const EvalRule R, const Gra
       s3[j] = PG_T(5, j) + PG_T(6, j);
       s0[j] = PG_T(7, j) + PG_T(8, j);
     }
-    // prefix / suffix products of the centre factors
-    double pre[N + 1], suf[N + 1];
-    pre[0] = 1.0;
+    // The centre, one-axis, pair and triple orbit sums are coefficients of
+    // prod_j (t0_j + z s_j(1) + y s_j(2) + x s_j(3)): of 1, z, y, x, z^2,
+    // zy, z^3.  Prefix products P_j (over the axes before j) keep the
+    // coefficients of 1, z, y, z^2, and the full product also x, zy, z^3.
+    double P1[N + 1], Pz[N + 1], Py[N + 1], Pzz[N + 1];
+    double px = 0.0, pzy = 0.0, pzzz = 0.0;
+    P1[0] = 1.0;
+    Pz[0] = Py[0] = Pzz[0] = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; ++j) pre[j + 1] = pre[j] * PG_T(0, j);
-    suf[N] = 1.0;
-#pragma unroll
-    for (int j = N - 1; j >= 0; --j) suf[j] = PG_T(0, j) * suf[j + 1];
-    double H1[N], H2[N], H3[N], H0[N];
-    double V = w0 * pre[N];
-    // one-axis orbits
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const double Q = pre[j] * suf[j + 1];
-      H1[j] = w1 * Q;
-      H2[j] = w2 * Q;
-      H3[j] = w3 * Q;
-      V = fma(H1[j], s1[j], V);
-      V = fma(H2[j], s2[j], V);
-      V = fma(H3[j], s3[j], V);
-    }
-    // axis pairs j < k: (r1, r1) and both orders of (r1, r2)
-#pragma unroll
-    for (int j = 0; j < N - 1; ++j) {
-      double PM = pre[j];
-#pragma unroll
-      for (int k = j + 1; k < N; ++k) {
-        if (k > j + 1) PM = PM * PG_T(0, k - 1);
-        const double Q = PM * suf[k + 1];
-        const double q5 = w5 * Q, q6 = w6 * Q;
-        const double a = fma(q5, s1[k], q6 * s2[k]);  // dV/ds_j(1)
-        const double b = q6 * s1[k];                  // dV/ds_j(2)
-        H1[j] += a;
-        H2[j] += b;
-        H1[k] += fma(q5, s1[j], q6 * s2[j]);
-        H2[k] = fma(q6, s1[j], H2[k]);
-        V = fma(a, s1[j], V);
-        V = fma(b, s2[j], V);
-      }
-    }
-    // axis triples at r1
-    if constexpr (N >= 3) {
-#pragma unroll
-      for (int j = 0; j < N - 2; ++j) {
-        double PM1 = pre[j];
-#pragma unroll
-        for (int k = j + 1; k < N - 1; ++k) {
-          if (k > j + 1) PM1 = PM1 * PG_T(0, k - 1);
-          double PM2 = PM1;
-#pragma unroll
-          for (int l = k + 1; l < N; ++l) {
-            if (l > k + 1) PM2 = PM2 * PG_T(0, l - 1);
-            const double Q = w7 * (PM2 * suf[l + 1]);
-            const double qj = Q * s1[j];
-            const double qjk = qj * s1[k];  // dV/ds_l(1)
-            H1[l] += qjk;
-            H1[k] = fma(qj, s1[l], H1[k]);
-            H1[j] = fma(Q * s1[k], s1[l], H1[j]);
-            V = fma(qjk, s1[l], V);
-          }
-        }
-      }
+    for (int m = 0; m < N; ++m) {
+      const double t0 = PG_T(0, m);
+      px = fma(px, t0, P1[m] * s3[m]);
+      pzy = fma(pzy, t0, fma(Pz[m], s2[m], Py[m] * s1[m]));
+      pzzz = fma(pzzz, t0, Pzz[m] * s1[m]);
+      P1[m + 1] = P1[m] * t0;
+      Pz[m + 1] = fma(Pz[m], t0, P1[m] * s1[m]);
+      Py[m + 1] = fma(Py[m], t0, P1[m] * s2[m]);
+      Pzz[m + 1] = fma(Pzz[m], t0, Pz[m] * s1[m]);
     }
     // every axis at r0: w_8 prod_j s_j(0), and its leave-one-out products
+    double H0[N];
+    double V;
     {
       double run = w8;
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        H0[j] = run;
-        run *= s0[j];
+      for (int m = 0; m < N; ++m) {
+        H0[m] = run;
+        run *= s0[m];
       }
-      V += run;
       double sr = 1.0;
 #pragma unroll
-      for (int j = N - 1; j >= 0; --j) {
-        H0[j] *= sr;
-        sr *= s0[j];
+      for (int m = N - 1; m >= 0; --m) {
+        H0[m] *= sr;
+        sr *= s0[m];
       }
+      V = fma(w0, P1[N], fma(w1, Pz[N], fma(w2, Py[N], fma(w3, px, fma(w5, Pzz[N], fma(w6, pzy, fma(w7, pzzz, run)))))));
     }
-    // per axis: the chain rule through the tabulated terms
+    // per axis, last to first with the suffix product Q (coefficients of 1,
+    // z, y, z^2): the leave-one-out product L_j = P_j Q, then
+    // H_j(r) = dV/ds_j(r), then the chain rule through the tabulated terms
     const double vol = pow2_neg(L) * prm.vol;
     part[0] = fma(vol, V, part[0]);
+    double q1 = 1.0, qz = 0.0, qy = 0.0, qzz = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
+    for (int j = N - 1; j >= 0; --j) {
+      const double L1 = P1[j] * q1;
+      const double Lz = fma(P1[j], qz, Pz[j] * q1);
+      const double Ly = fma(P1[j], qy, Py[j] * q1);
+      const double Lzz = fma(P1[j], qzz, fma(Pz[j], qz, Pzz[j] * q1));
+      const double H1 = fma(w1, L1, fma(w5, Lz, fma(w6, Ly, w7 * Lzz)));
+      const double H2 = fma(w2, L1, w6 * Lz);
+      const double H3 = w3 * L1;
+      {
+        const double t0 = PG_T(0, j);
+        const double nz = fma(qz, t0, q1 * s1[j]), ny = fma(qy, t0, q1 * s2[j]), nzz = fma(qzz, t0, qz * s1[j]);
+        q1 *= t0;
+        qz = nz;
+        qy = ny;
+        qzz = nzz;
+      }
       const double lo = A.lower[(size_t)j * A.m + r];
       const int lv = A.level[(size_t)j * A.m + r];
       double o[kGradTerms];
@@ -243,14 +221,14 @@ __global__ void __launch_bounds__(GT) k_gradient_box(const EvalRule R, const Gra
         grad_axis_terms<F, N * GT>(R, prm, j, lo, 0.5 * pow2_neg(lv), &PG_T(0, j), o);
       }
       // the part of V at the centre on axis j
-      const double gc = V - fma(s1[j], H1[j], fma(s2[j], H2[j], fma(s3[j], H3[j], s0[j] * H0[j])));
+      const double gc = V - fma(s1[j], H1, fma(s2[j], H2, fma(s3[j], H3, s0[j] * H0[j])));
       double g0 = o[0] * gc, g1 = o[1] * gc;
-      g0 = fma(o[2], H1[j], g0);
-      g1 = fma(o[3], H1[j], g1);
-      g0 = fma(o[4], H2[j], g0);
-      g1 = fma(o[5], H2[j], g1);
-      g0 = fma(o[6], H3[j], g0);
-      g1 = fma(o[7], H3[j], g1);
+      g0 = fma(o[2], H1, g0);
+      g1 = fma(o[3], H1, g1);
+      g0 = fma(o[4], H2, g0);
+      g1 = fma(o[5], H2, g1);
+      g0 = fma(o[6], H3, g0);
+      g1 = fma(o[7], H3, g1);
       g0 = fma(o[8], H0[j], g0);
       g1 = fma(o[9], H0[j], g1);
       part[(1 + j) * GT] = fma(vol, g0, part[(1 + j) * GT]);
