@@ -269,12 +269,12 @@ __device__ __forceinline__ long long dyadic_index(double lower, int level) {
 // per-axis factor cache when the level is cached, computed otherwise.  The
 // cache holds the same expression of the same arguments, so both give the
 // same bits.
-template <class F, int N, int THREADS>
+template <class F, int N, int THREADS, int SLOTS = kCacheSlots>
 __device__ __forceinline__ void axis_entries(typename F::T* tab, const EvalRule& R, const IntegrandParams& prm,
                                              const typename F::T* __restrict__ cache, int cache_levels, double lo,
                                              int lv, int j) {
   if (cache != nullptr && lv <= cache_levels) {
-    const typename F::T* src = cache + ((size_t)j * kCacheSlots + ((1 << lv) - 1) + dyadic_index(lo, lv)) * kCodes;
+    const typename F::T* src = cache + ((size_t)j * SLOTS + ((1 << lv) - 1) + dyadic_index(lo, lv)) * kCodes;
 #pragma unroll
     for (int code = 0; code < kCodes; ++code) tab[(code * N + j) * THREADS] = src[code];
   } else {
@@ -913,6 +913,35 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule 
   }
 }
 
+// ------------------------------------------------- batched factor cache
+// The per-instance factor cache of one (family, n) group: levels 0 ..
+// kBatchCacheLevels of every axis, with the instance's own parameters and
+// the expression axis_entries uses, so cached and computed entries agree.
+template <class F, int N>
+__global__ void __launch_bounds__(256) k_factor_cache_batch(const EvalRule R, const BatchArgs A, const BatchGroup G) {
+  typedef typename F::T T;
+  if (G.fcache == nullptr) return;
+  T* cache = static_cast<T*>(G.fcache);
+  const long long per_inst = (long long)N * kBatchCacheSlots * kCodes;
+  const long long total = (long long)G.count * per_inst;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int li = (int)(idx / per_inst);
+    const long long r = idx - (long long)li * per_inst;
+    const int code = (int)(r % kCodes);
+    const long long rest = r / kCodes;
+    const long long slot = rest % kBatchCacheSlots;
+    const int j = (int)(rest / kBatchCacheSlots);
+    const int L = 63 - __clzll(slot + 1);  // slot = 2^L - 1 + k
+    const long long k = slot + 1 - (1LL << L);
+    const double w = pow2_neg(L);
+    const double h = 0.5 * w;
+    const double lo = (double)k * w;
+    const IntegrandParams& prm = A.prm[G.first + li];
+    cache[idx] = F::factor(F::axis(prm, j), point_x(prm, j, lo + h, h, code_offset(R, code)));
+  }
+}
+
 // ------------------------------------------------------ batched evaluate
 // Evaluate for one (family, n) group of a batch: one thread per sibling pair
 // over every instance's slot of the group's pool; each pair reads its
@@ -949,6 +978,8 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_batch(const EvalRule R, co
     const uint8_t* __restrict__ level = G.level + (size_t)buf * N * slots;
     const IntegrandParams& prm = A.prm[G.first + li];
     const T base = F::base(prm);
+    const T* __restrict__ icache =
+        G.fcache ? static_cast<const T*>(G.fcache) + (size_t)li * N * kBatchCacheSlots * kCodes : nullptr;
     double loL[N], wL[N], wR[N];
     int lvLj[N];
     int lvL = 0, lvR = 0, diff_axis = -1, diff_lv = 0;
@@ -971,14 +1002,15 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_batch(const EvalRule R, co
     }
 #pragma unroll
     for (int j = 0; j < N; ++j)
-      axis_entries<F, N, THREADS>(tab, R, prm, (const T*)nullptr, 0, loL[j], lvLj[j], j);
+      axis_entries<F, N, THREADS, kBatchCacheSlots>(tab, R, prm, icache, kBatchCacheLevels, loL[j], lvLj[j], j);
     double S[kNumGen], D[N];
     double VL, EL, VR, ER;
     int KL, KR;
     rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
     region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL) * prm.vol, wL, VL, EL, KL, nullptr);
     if (diff_axis >= 0)
-      axis_entries<F, N, THREADS>(tab, R, prm, (const T*)nullptr, 0, diff_lo, diff_lv, diff_axis);
+      axis_entries<F, N, THREADS, kBatchCacheSlots>(tab, R, prm, icache, kBatchCacheLevels, diff_lo, diff_lv,
+                                                    diff_axis);
     rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
     region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR) * prm.vol, wR, VR, ER, KR, nullptr);
     if (it > 1) two_level(VL, VR, G.Vp[p], EL, ER);
@@ -1006,6 +1038,11 @@ cudaError_t launch_standalone(const EvalRule& R, const StandaloneArgs& A, int gr
   return cudaGetLastError();
 }
 
+template <class F, int N>
+cudaError_t launch_batch_fill(const EvalRule& R, const BatchArgs& A, const BatchGroup& G, int grid, cudaStream_t st) {
+  k_factor_cache_batch<F, N><<<grid, 256, 0, st>>>(R, A, G);
+  return cudaGetLastError();
+}
 template <class F, int N, int THREADS>
 cudaError_t launch_batch_eval(const EvalRule& R, const BatchArgs& A, const BatchGroup& G, int grid, cudaStream_t st) {
   k_evaluate_batch<F, N, THREADS><<<grid, THREADS, sizeof(typename F::T) * kCodes * N * THREADS, st>>>(R, A, G);

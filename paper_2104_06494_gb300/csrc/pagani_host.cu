@@ -1561,6 +1561,12 @@ static void release_batch(BatchWorkspace& b) {
   b.bytes = 0;
 }
 
+// Bytes of a group's per-instance factor cache (sized for the widest
+// element type, the complex factors).
+static size_t batch_cache_bytes(const BatchGroup& g) {
+  return (size_t)g.count * g.n * kBatchCacheSlots * kCodes * sizeof(double2);
+}
+
 static int integrate_batch_locked(int64_t count, const pagani_batch_item* items, int64_t slot_cap_req,
                                   const pagani_options& o, cudaStream_t st, pagani_batch_result* res,
                                   double* ms_out) {
@@ -1599,7 +1605,7 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
     g.slot_cap = slot_cap;
     const size_t slots = (size_t)g.count * slot_cap;
     bytes += align(sizeof(double) * 2 * g.n * slots) + align((size_t)2 * g.n * slots) + 2 * align(8 * slots) +
-             align(slots) + align(4 * slots + 8);
+             align(slots) + align(4 * slots + 8) + align(batch_cache_bytes(g));
     for (int64_t i : kv.second) order.push_back(i);
     groups.push_back(g);
   }
@@ -1641,6 +1647,7 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
     g.E = reinterpret_cast<double*>(take(8 * slots));
     g.K = take(slots);
     g.Vp = reinterpret_cast<double*>(take(4 * slots + 8));
+    g.fcache = take(batch_cache_bytes(g));
   }
   BatchGroup* groups_d = reinterpret_cast<BatchGroup*>(take(sizeof(BatchGroup) * groups.size()));
   a.groups = groups_d;
@@ -1701,6 +1708,10 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
     if (!rt) return fail(PAGANI_ERR_CUDA, "rule construction failed");
     rules[gi] = to_eval_rule(*rt);
   }
+  // every instance's factor cache, once per call (the parameters are fixed
+  // for the whole loop)
+  for (size_t gi = 0; gi < groups.size(); ++gi)
+    PG_CK(family_kernels(groups[gi].family).batch_fill[groups[gi].n](rules[gi], a, groups[gi], sms * 8, st));
   // autotune each group's Evaluate grid on this batch's first iteration
   std::vector<int> egrid(groups.size());
   cudaEvent_t ev0, ev1;

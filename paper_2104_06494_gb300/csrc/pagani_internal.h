@@ -20,6 +20,11 @@ constexpr double kDiffNoise = 0x1p-41;
 // [k 2^-l, (k+1) 2^-l) of levels l <= kCacheLevels, per axis, slot 2^l - 1 + k.
 constexpr int kCacheLevels = 11;
 constexpr int kCacheSlots = (1 << (kCacheLevels + 1)) - 1;
+// Batches keep a smaller per-instance cache (levels <= kBatchCacheLevels):
+// an instance of at most a few ten thousand regions rarely splits an axis
+// deeper, and thousands of instances share the device.
+constexpr int kBatchCacheLevels = 7;
+constexpr int kBatchCacheSlots = (1 << (kBatchCacheLevels + 1)) - 1;
 
 // Generator orbits of the degree-9 rule, in table order.
 enum Gen {
@@ -270,6 +275,7 @@ struct BatchGroup {
   double* E;
   uint8_t* K;
   double* Vp;       // [count * slot_cap / 2]
+  void* fcache;     // [count][n][kBatchCacheSlots][kCodes] factor values (family element type)
 };
 
 struct BatchArgs {
@@ -301,6 +307,8 @@ struct FamilyKernels {
   const void* loop_fn[kMaxDim + 1];        // kernel symbols (for occupancy queries / graph nodes)
   GradLauncher grad[kMaxDim + 1];          // gradient over a box list (positive product families)
   cudaError_t (*batch_eval[kMaxDim + 1])(const EvalRule&, const BatchArgs&, const BatchGroup&, int grid,
+                                         cudaStream_t);
+  cudaError_t (*batch_fill[kMaxDim + 1])(const EvalRule&, const BatchArgs&, const BatchGroup&, int grid,
                                          cudaStream_t);
   const void* batch_eval_fn[kMaxDim + 1];
   int threads;                             // block size

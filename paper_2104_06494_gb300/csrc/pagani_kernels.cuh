@@ -14,6 +14,7 @@ FamilyKernels make_family_kernels() {
   k.fill[NN] = &launch_fill<FamOf<NN>, NN>;                                                     \
   k.grad[NN] = &launch_grad<FamOf<NN>, NN>;                                                     \
   k.batch_eval[NN] = &launch_batch_eval<FamOf<NN>, NN, THREADS>;                                \
+  k.batch_fill[NN] = &launch_batch_fill<FamOf<NN>, NN>;                                         \
   k.batch_eval_fn[NN] = (const void*)&k_evaluate_batch<FamOf<NN>, NN, THREADS>;                 \
   cudaFuncSetAttribute((const void*)&k_evaluate_batch<FamOf<NN>, NN, THREADS>,                  \
                        cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
