@@ -398,12 +398,12 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
             C = mid_id ? suf[l + 1] : F::mul(MID, suf[l + 1]);
             c_id = false;
           }
-          const T tp = PG_TB(kR1P, l), tm = PG_TB(kR1M, l);
+          // the remaining factor of each point, C t_l(+-), is shared by the
+          // four sign pairs on (j, k)
+          const T tp = c_id ? PG_TB(kR1P, l) : F::mul(C, PG_TB(kR1P, l));
+          const T tm = c_id ? PG_TB(kR1M, l) : F::mul(C, PG_TB(kR1M, l));
 #pragma unroll
-          for (int s4 = 0; s4 < 4; ++s4) {
-            T B = c_id ? ajk[s4] : F::mul(ajk[s4], C);
-            S[kGenL1L1L1] = F::acc(F::acc(S[kGenL1L1L1], B, tp), B, tm);
-          }
+          for (int s4 = 0; s4 < 4; ++s4) S[kGenL1L1L1] = F::acc(F::acc(S[kGenL1L1L1], ajk[s4], tp), ajk[s4], tm);
         }
       }
     }
@@ -425,15 +425,25 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
         Bv[2 * s2] = F::mul(Bv[s2], fp);
       }
     }
+    // the first half's sign products by the same doubling, the family's base
+    // folded into its first axis
+    T Av[1 << H1];
+    Av[0] = F::mul(base, PG_TB(kR0P, 0));
+    Av[1] = F::mul(base, PG_TB(kR0M, 0));
+#pragma unroll
+    for (int t = 1; t < H1; ++t) {
+      const T fp = PG_TB(kR0P, t), fm = PG_TB(kR0M, t);
+#pragma unroll
+      for (int s1 = (1 << t) - 1; s1 >= 0; --s1) {
+        Av[2 * s1 + 1] = F::mul(Av[s1], fm);
+        Av[2 * s1] = F::mul(Av[s1], fp);
+      }
+    }
     double acc = 0.0;
 #pragma unroll
-    for (int s1 = 0; s1 < (1 << H1); ++s1) {
-      T Av = base;
+    for (int s1 = 0; s1 < (1 << H1); ++s1)
 #pragma unroll
-      for (int t = 0; t < H1; ++t) Av = F::mul(Av, ((s1 >> t) & 1) ? PG_TB(kR0M, t) : PG_TB(kR0P, t));
-#pragma unroll
-      for (int s2 = 0; s2 < (1 << H2); ++s2) acc = F::acc(acc, Av, Bv[s2]);
-    }
+      for (int s2 = 0; s2 < (1 << H2); ++s2) acc = F::acc(acc, Av[s1], Bv[s2]);
     S[kGenL0All] = acc;
   }
 #undef PG_TB

@@ -166,18 +166,20 @@ def region_points_work(family: int, n: int, q: float = 11.0) -> Counter:
                     if not mid_id:
                         mul()
                     c_id = False
-                for _ in range(4):
-                    if not c_id:
-                        mul()
-                    acc(2)
-    # vertices: half tables
+                if not c_id:
+                    mul(2)        # C t_l(+-), shared by the four (j, k) sign pairs
+                acc(8)
+    # vertices: both halves' sign products by doubling, then one accumulation
+    # per vertex
     h1 = n // 2
     h2 = n - h1
     for t in range(1, h2):
         mul(2 * (1 << t))
-    for _ in range(1 << h1):
-        mul(h1 - 1 if base_identity else h1)
-        acc(1 << h2)
+    if not base_identity:
+        mul(2)
+    for t in range(1, h1):
+        mul(2 * (1 << t))
+    acc(1 << n)
     return c
 
 
