@@ -315,15 +315,25 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     T Q = (j == N - 1) ? pre[N - 1] : F::mul(pre[j], suf[j + 1]);
-    // the l2 and lp points also enter the fourth difference, so they are
-    // formed individually; the l1 and l3 points go straight into their sums
-    double p2 = F::last(Q, PG_TB(kR2P, j)), m2 = F::last(Q, PG_TB(kR2M, j));
-    double pp = F::last(Q, PG_TB(kRpP, j)), mp = F::last(Q, PG_TB(kRpM, j));
+    // the l2 and lp points also enter the fourth difference through their
+    // pair sums (and, for signed families, its noise floor through their
+    // magnitudes); the l1 and l3 points go straight into their sums
+    double p2 = 0.0, m2 = 0.0, pp = 0.0, mp = 0.0, s2, sp;
+    if constexpr (F::kUnitBounded) {
+      p2 = F::last(Q, PG_TB(kR2P, j));
+      m2 = F::last(Q, PG_TB(kR2M, j));
+      pp = F::last(Q, PG_TB(kRpP, j));
+      mp = F::last(Q, PG_TB(kRpM, j));
+      s2 = p2 + m2;
+      sp = pp + mp;
+    } else {
+      s2 = F::acc(F::last(Q, PG_TB(kR2M, j)), Q, PG_TB(kR2P, j));
+      sp = F::acc(F::last(Q, PG_TB(kRpM, j)), Q, PG_TB(kRpP, j));
+    }
     if constexpr (DEG == 9) {
       S[kGenL1] = F::acc(F::acc(S[kGenL1], Q, PG_TB(kR1P, j)), Q, PG_TB(kR1M, j));
       S[kGenL3] = F::acc(F::acc(S[kGenL3], Q, PG_TB(kR3P, j)), Q, PG_TB(kR3M, j));
     }
-    const double s2 = p2 + m2, sp = pp + mp;
     S[kGenL2] += s2;
     S[kGenLp] += sp;
     // a difference within rounding noise of zero (2^12 u of the magnitude

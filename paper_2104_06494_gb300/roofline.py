@@ -129,8 +129,13 @@ def region_points_work(family: int, n: int, q: float = 11.0) -> Counter:
         if j < n - 1:
             mul()
         acc(4)            # the l1 and l3 points
-        last(4)           # the l2 and lp points (also used by D_j)
-        add(4)            # their pair sums and the two generator sums
+        if cplx or additive:
+            last(4)       # the l2 and lp points (also used by D_j)
+            add(4)        # their pair sums and the two generator sums
+        else:
+            last(2)       # one point of each pair, the other fused into
+            acc(2)        # the pair sum (D_j needs only the sums)
+            add(2)        # the two generator sums
         c["flops"] += 6   # (sp - 2 f0) - q (s2 - 2 f0): 3 FMA
         c["inst"] += 3
         if cplx:          # its noise floor over |values|: 3 ADD, 2 FMA (|x| is free)
