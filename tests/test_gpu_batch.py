@@ -69,3 +69,27 @@ def test_batch_full_workload(pg):
         w = items[i]
         g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, 16384, relerr_filter=w.relerr_filter)
         same(res[i], g, (i, w.family, w.dim, w.epsrel))
+
+
+def test_batch_deep_boxes_match_single_integrals(pg):
+    """Sharp peaks in two and three dimensions refine some axes past the
+    batch's cached levels (7), so the batch forms those boxes' factors
+    directly and the rest from its per-instance cache.  Each item's single
+    call, with its leaf set kept, shows the depth reached; the batch must
+    still reproduce every single call."""
+    from paper_2104_06494_gb300.workloads import Workload
+    items = [
+        Workload("gaussian_d2_sharp", pg.GAUSSIAN, 2, 1e-9, [60.0, 45.0, 0.31, 0.67], 16384),
+        Workload("product_peak_d3_sharp", pg.PRODUCT_PEAK, 3, 1e-8, [40.0, 30.0, 50.0, 0.2, 0.55, 0.8], 16384),
+        Workload("c0_d2_sharp", pg.C0, 2, 1e-7, [30.0, 20.0, 0.4, 0.6], 16384),
+        Workload("oscillatory_d3", pg.OSCILLATORY, 3, 1e-10, [0.3, 4.0, 3.0, 5.0], 16384),
+    ]
+    res, _ = pg.pagani_integrate_batch(items, 16384)
+    deepest = 0
+    for w, r in zip(items, res):
+        g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, 16384,
+                                   relerr_filter=w.relerr_filter, keep_leaves=1)
+        same(r, g, w.name)
+        _, level = pg.pagani_leaves(w.dim)
+        deepest = max(deepest, int(level.max().item()))
+    assert deepest > 7, deepest
