@@ -131,13 +131,29 @@ def oracle_sample(w, budget_s: float, gpu_trace=None):
 
 
 def cpu_baseline(ws, budget_s, gpu_traces):
+    """(single-threaded baseline, OpenMP baseline): the oracle on a bounded
+    sample of each integral, then the OpenMP build of the oracle (its
+    per-region Evaluate loop on all host cores, every other step serial) on
+    exactly the same sample."""
+    from oracle import capi
     parts = [oracle_sample(w, budget_s, gpu_traces.get(w.name)) for w in ws]
     evals = sum(p["evals"] for p in parts)
     secs = sum(p["seconds"] for p in parts)
     sample = "; ".join(f"{p['name']}: first {p['iterations']} iterations ({p['regions']} regions, "
                        f"{p['seconds']:.1f} s)" for p in parts)
-    return {"value": evals / secs, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": "single-threaded C oracle, " + sample}
+    single = {"value": evals / secs, "unit": METRIC, "cores": 1, "kind": "oracle",
+              "sample": "single-threaded C oracle, " + sample}
+    threads = int(capi._load(parallel=True).omp_get_max_threads())
+    psecs = 0.0
+    for w, p in zip(ws, parts):
+        t = time.perf_counter()
+        r = capi.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions,
+                           relerr_filter=w.relerr_filter, it_max=p["iterations"], parallel=True)
+        psecs += time.perf_counter() - t
+        assert r.n_regions == p["regions"], (w.name, r.n_regions, p["regions"])
+    parallel = {"value": evals / psecs, "unit": METRIC, "cores": threads, "kind": "oracle (OpenMP Evaluate)",
+                "sample": f"the same sample, OpenMP build of the C oracle on {threads} threads"}
+    return single, parallel
 
 
 # --------------------------------------------------------------- helpers
@@ -465,9 +481,9 @@ def main():
                            "estimate": r.estimate, "errorest": r.errorest,
                            "true_relerr": abs(r.estimate - ex) / abs(ex), "within_errorest": abs(r.estimate - ex) <= r.errorest,
                            "relerr_filter": w.relerr_filter}
-        cpu = None
+        cpu = cpu_par = None
         if not args.no_cpu_baseline and world >= 1:
-            cpu = cpu_baseline(ws, args.cpu_seconds, {w.name: traced[w.name].trace for w in ws})
+            cpu, cpu_par = cpu_baseline(ws, args.cpu_seconds, {w.name: traced[w.name].trace for w in ws})
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
@@ -515,6 +531,7 @@ def main():
             line["filtering"] = filtering_report(pg, torch, flush)
         if cpu is not None:
             line["cpu_baseline"] = cpu
+            line["cpu_baseline_parallel"] = cpu_par
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

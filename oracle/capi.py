@@ -21,18 +21,23 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pagani_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
+# The same source built with -fopenmp: only the per-region Evaluate loop of
+# oracle_pagani runs in parallel (for the parallel CPU baseline).
+_LIB_OMP = os.path.join(_OUT_DIR, "liboracle_omp.so")
 
 STATUS = {0: "converged", 1: "it_max", 2: "memory exhausted", 3: "tolerance unreachable"}
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, parallel: bool = False) -> str:
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    lib = _LIB_OMP if parallel else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math"] +
+                              (["-fopenmp"] if parallel else []) +
+                              ["-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Rule(ctypes.Structure):
@@ -59,17 +64,17 @@ TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.i
                         ("v", np.float64), ("e", np.float64), ("vf", np.float64), ("ef", np.float64),
                         ("threshold", np.float64), ("direction_changes", np.float64)])
 
-_lib = None
+_libs: dict = {}
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
-        _lib.oracle_evaluate.restype = ctypes.c_int
-        _lib.oracle_pagani.restype = ctypes.c_int
-        _lib.oracle_default_init_div.restype = ctypes.c_int
-    return _lib
+def _load(parallel: bool = False):
+    if parallel not in _libs:
+        lib = ctypes.CDLL(build(parallel=parallel))
+        lib.oracle_evaluate.restype = ctypes.c_int
+        lib.oracle_pagani.restype = ctypes.c_int
+        lib.oracle_default_init_div.restype = ctypes.c_int
+        _libs[parallel] = lib
+    return _libs[parallel]
 
 
 _rule_cache: dict = {}
@@ -148,10 +153,12 @@ class OracleResult:
 
 def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20, max_regions: int = 10 ** 6,
               relerr_filter: int = 1, heuristic_filter: int = 1, init_div: int = 0, it_max: int = 100,
-              want_regions: bool = False, want_leaves: bool = False, bounds=None, degree: int = 9) -> OracleResult:
+              want_regions: bool = False, want_leaves: bool = False, bounds=None, degree: int = 9,
+              parallel: bool = False) -> OracleResult:
     """bounds: None for the unit cube, else (a, b), each of length n; degree:
-    the rule (9, or 7 for the Genz-Malik variant)."""
-    lib = _load()
+    the rule (9, or 7 for the Genz-Malik variant); parallel: the OpenMP
+    build (per-region Evaluate on all host cores, same results)."""
+    lib = _load(parallel)
     p = np.ascontiguousarray(params, dtype=np.float64)
     opt = _Opt(relerr_filter, heuristic_filter, init_div, it_max, None, None)
     if bounds is not None:

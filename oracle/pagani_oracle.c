@@ -495,7 +495,10 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
     tr.s = s;
     res->n_regions += s;
     res->n_active_last = s;
-    /* V, E, K <- Evaluate(H) */
+    /* V, E, K <- Evaluate(H).  Regions are independent: the second,
+       OpenMP build of this file (the parallel CPU baseline) runs this loop
+       on all host cores; every other step stays serial and in order. */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < s; ++i) {
       int k;
       evaluate_region(R, fam, params, H_lo + i * n, H_w + i * n, &V[i], &E[i],

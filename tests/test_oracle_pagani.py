@@ -228,3 +228,20 @@ def test_constant_integrand_is_exact(n):
     hi = [1.0, 3.0, 2.5] + [1.0] * (n - 3)
     o = capi.integrate(6, n, [0.0], 1e-12, bounds=(lo, hi))
     assert o.status == 0 and abs(o.estimate - 3.0) <= 4e-16 * 3.0 and o.errorest == 0.0
+
+
+def test_openmp_build_reproduces_the_serial_oracle():
+    """The OpenMP build parallelises only the per-region Evaluate loop, whose
+    iterations are independent; every sum stays serial and in order, so the
+    two builds agree bit for bit."""
+    import os
+    os.environ.setdefault("OMP_NUM_THREADS", "4")
+    for fam, n, params, eps in ((1, 3, [9.0, 6.0, 12.0, 0.3, 0.6, 0.45], 1e-7),
+                                (2, 4, [0.2, 2.0, 3.0, 1.5, 4.0], 1e-8),
+                                (4, 3, [2.0, 3.0, 4.0, 0.4, 0.5, 0.7], 1e-4)):
+        a = capi.integrate(fam, n, params, eps, max_regions=200000, relerr_filter=0 if fam == 2 else 1)
+        b = capi.integrate(fam, n, params, eps, max_regions=200000, relerr_filter=0 if fam == 2 else 1,
+                             parallel=True)
+        assert (a.status, a.iterations, a.n_regions) == (b.status, b.iterations, b.n_regions)
+        assert a.estimate == b.estimate and a.errorest == b.errorest
+        assert a.trace.tobytes() == b.trace.tobytes()
