@@ -14,7 +14,7 @@
  * summed in region-index order, and compiled with -ffp-contract=off so the
  * results are the same on x86-64 and aarch64.
  *
- * Readings of passages the paper leaves open (all listed in the design doc):
+ * Readings of passages the paper leaves open:
  *  - Evaluate (Sec. 3.2): the rule, its null rules and the error formula come
  *    in as tables from oracle/rule.py; the error from the four null values
  *    N_1..N_4 is: r = max(N_1/N_2, N_2/N_3) (x/0 = inf for x > 0, 0 for x = 0);

@@ -50,7 +50,9 @@ __device__ __forceinline__ double null_error(double n1, double n2, double n3, do
   return 40.0 * r * r * r * n1;
 }
 
-// Two-level error refinement of a sibling pair (Sec. 3.2, reading in the design doc).
+// Two-level error refinement of a sibling pair (Sec. 3.2), as read here: with
+// delta = |V_L + V_R - V_parent| / 4 and S = E_L + E_R, each error becomes
+// E (1 + 2 delta / S) + delta (E + delta when S = 0).
 __device__ __forceinline__ void two_level(double VL, double VR, double Vpar, double& EL, double& ER) {
   double delta = fabs(VL + VR - Vpar) / 4.0;
   double S = EL + ER;

@@ -4,7 +4,7 @@
 // The paper fixes the rule family (Sec. 2.1: the Genz-Malik rules used by
 // Cuhre, 2^n + Theta(n^3) points; Sec. 3.2: four extra rules whose
 // differences give the error).  It prints no constants, so the construction
-// is the reading documented in the design doc:
+// is this reading of them:
 //  * squared radii l0 = 0.4707, l1 = 4/(15 - 5/l0), rho = (1 - l1/l0)/27,
 //    l2 = (5 - 7 l1 - 35 rho)/(7 - 35 l1/3 - 35 rho/l0), rho' = rho (1 - l2/l0)/3,
 //    l3 = (7 - 9(l2+l1) + 63 l2 l1/5 - 63 rho')/(9 - 63(l2+l1)/5 + 21 l2 l1 - 63 rho'/l0),
