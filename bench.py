@@ -488,7 +488,7 @@ def main():
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded splitmix64 parameters, BASELINE ranges)",
+            "data": "synthetic (seeded splitmix64 parameters in the Genz-family ranges of the workloads)",
             "config": {"workload": wl_name, "time_to_result_ms": {n: None for n in per},
                        "integrals": per, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
