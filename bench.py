@@ -222,8 +222,8 @@ def differentiation_report(pg, torch, flush, reps: int = 3):
 
 
 def hbm_peak_gbs():
-    """The measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json,
-    written by the driver), else the profiling recipe's fallback."""
+    """The measured HBM copy bandwidth from MEASURED_PEAKS.json when that
+    file is present, else a fallback figure of 6.8 TB/s."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:

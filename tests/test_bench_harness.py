@@ -1,6 +1,6 @@
 """The N > 1 path of bench.py on CPU: torchrun with two gloo ranks running
 the reference arm (rank 0 times the oracle and prints one JSON line, rank 1
-exits without work), as the driver launches it."""
+exits without work), launched as a multi-GPU run would launch it."""
 import json
 import os
 import socket
