@@ -128,3 +128,27 @@ def test_differentiation_workload_d6(pg):
         rm = pg.pagani_integrate_ex(n, w.family, pm, w.epsrel, w.epsabs, w.max_regions)
         fd = (rp.estimate - rm.estimate) / (2 * h)
         assert abs(fd - g[k]) <= (rp.errorest + rm.errorest) / (2 * h) + 1e-6 * abs(g[k]), (k, fd, g[k])
+
+
+@pytest.mark.parametrize("family,n", [(1, 2), (0, 5), (4, 5), (1, 8)])
+def test_gradient_on_deep_boxes_matches_oracle(pg, family, n):
+    """Random dyadic boxes with levels up to 30 per axis: intervals of level
+    11 or less take their factor values and chain-rule terms from the
+    tables filled for the call, deeper ones compute them in place.  Both
+    must give the oracle's point-by-point gradient on the same boxes."""
+    import torch
+    from paper_2104_06494_gb300.workloads import random_dyadic_regions
+    m = 3000 if n < 8 else 400
+    lo_l, wd_l = random_dyadic_regions(n, m, seed=900 + 10 * family + n, max_level=30)
+    lo, wd = np.array(lo_l), np.array(wd_l)
+    lv = np.rint(-np.log2(wd)).astype(np.uint8)
+    assert lv.max() > 11 and lv.min() <= 11
+    p = draw_params(family, n, 400 + family + n, RANGES[family])
+    lower = torch.tensor(lo.T.copy(), dtype=torch.float64, device="cuda")
+    level = torch.tensor(lv.T.copy(), dtype=torch.uint8, device="cuda")
+    v, g = pg.pagani_gradient(n, family, p, lower, level)
+    vo, go, ab = oracle.gradient(family, n, p, lo, wd)
+    tol = (point_count(n) + 4 * n + 32 + kappa(family, n, p)) * EPS
+    assert abs(v - vo) <= 1e-12 * abs(vo) + tol * ab[0]
+    for k in range(2 * n):
+        assert abs(g[k] - go[k]) <= 1e-12 * abs(go[k]) + tol * ab[1 + k], (k, g[k], go[k])
