@@ -95,6 +95,7 @@ def region_points_work(family: int, n: int, q: float = 11.0) -> Counter:
         c["inst"] += pm * k
 
     def last(k=1):
+        c["points"] += k  # a rule point's value formed
         if cplx:          # real part only: 1 MUL + 1 FMA
             c["flops"] += 3 * k
             c["inst"] += 2 * k
@@ -109,6 +110,7 @@ def region_points_work(family: int, n: int, q: float = 11.0) -> Counter:
         c["inst"] += k
 
     def acc(k=1):         # S += f(point) formed from its last two factors
+        c["points"] += k
         if cplx:          # 2 FMA
             c["flops"] += 4 * k
             c["inst"] += 2 * k
