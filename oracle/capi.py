@@ -25,7 +25,7 @@ _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 # oracle_pagani runs in parallel (for the parallel CPU baseline).
 _LIB_OMP = os.path.join(_OUT_DIR, "liboracle_omp.so")
 
-STATUS = {0: "converged", 1: "it_max", 2: "memory exhausted", 3: "tolerance unreachable"}
+STATUS = {0: "converged", 1: "it_max or no region left active", 2: "memory exhausted"}
 
 
 def build(force: bool = False, parallel: bool = False) -> str:
@@ -203,8 +203,9 @@ def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20,
                         fl, fw, fv.value, leaves)
 
 
-def threshold_classify(A, E, v_tot: float, e_tot: float, e_it: float, tau_rel: float):
-    """Run the oracle's Threshold-Classify on given lists; returns
+def threshold_classify(A, E, v_tot: float, e_f: float, e_it: float, tau_rel: float):
+    """Run the oracle's Threshold-Classify on given lists (v_tot = v + v_f,
+    e_f the error finished earlier, e_it = sum E); returns
     (ok, A_out, probes, t, direction_changes)."""
     lib = _load()
     a = np.ascontiguousarray(A, dtype=np.uint8).copy()
@@ -213,7 +214,7 @@ def threshold_classify(A, E, v_tot: float, e_tot: float, e_it: float, tau_rel: f
     chg = ctypes.c_int(0)
     t = ctypes.c_double(0.0)
     ok = lib.oracle_threshold_classify(a.ctypes.data_as(ctypes.c_void_p), _dp(e), ctypes.c_double(v_tot),
-                                       ctypes.c_double(e_tot), ctypes.c_double(e_it), ctypes.c_int64(len(e)),
+                                       ctypes.c_double(e_f), ctypes.c_double(e_it), ctypes.c_int64(len(e)),
                                        ctypes.c_double(tau_rel), ctypes.byref(probes), ctypes.byref(t),
                                        ctypes.byref(chg))
     return ok, a, probes.value, t.value, chg.value

@@ -16,13 +16,26 @@
  *
  * Readings of passages the paper leaves open:
  *  - Evaluate (Sec. 3.2): the rule, its null rules and the error formula come
- *    in as tables from oracle/rule.py; the error from the four null values
- *    N_1..N_4 is: r = max(N_1/N_2, N_2/N_3) (x/0 = inf for x > 0, 0 for x = 0);
- *    err = 10 max(N_k) if r >= 1, 10 r N_1 if 1/2 <= r < 1, 40 r^3 N_1 else.
- *    A null value N_k no larger than 64 N(n) u vol sum_g |u_kg| M_g (u the
- *    unit roundoff, M_g the magnitude of orbit sum S_g: |S_g| for the
- *    positive families, the orbit size for the oscillatory one, |f| <= 1) is
- *    at the rounding level of its sum and counts as zero.
+ *    in as tables from oracle/rule.py.  The four null values N_1..N_4
+ *    (degrees 7, 5, 3, 1) are differences between the basic rule and
+ *    embedded lower-degree rules; on a box where f is resolved they fall
+ *    off geometrically with the degree, by a ratio r per two degrees, and
+ *    the degree-9 rule's own error is about r N_1.  So:
+ *      r = max(N_1/N_2, N_2/N_3, N_3/N_4)  (x/0 = inf for x > 0, 0 for x = 0);
+ *      r >= 1 (no decay: f not resolved): err = 10 max(N_1, N_2, N_3), the
+ *        largest difference of the rules of degree >= 3;
+ *      r <  1: err = 10 r max(N_1, r N_2), where r N_2 stands in for a
+ *        degree-7 value that cancelled by accident (N_1 far below the
+ *        geometric trend of the others).
+ *    The factor 10 is a safety margin: on degree-10 terms the rule's error
+ *    is 0.3 to 1.2 times N_1, so err overstates a resolved box's error by
+ *    about 10 to 30.  A null value N_k no larger than
+ *    64 N(n) u vol sum_g |u_kg| M_g (u the unit roundoff, M_g the magnitude
+ *    of orbit sum S_g: |S_g| for the positive families, the orbit size for
+ *    the oscillatory one, |f| <= 1) is at the rounding level of its sum and
+ *    counts as zero.  The error is never below the rounding level of V
+ *    itself, 16 u vol sum_g |w_g| M_g: no rule sum is more accurate than a
+ *    few unit roundoffs of its absolute sum.
  *  - Split axis (Sec. 2.2, Sec. 3.2): fourth divided difference per axis,
  *    D_j = |(f(c+a h_j e_j) + f(c-a h_j e_j) - 2 f(c))
  *           - q (f(c+b h_j e_j) + f(c-b h_j e_j) - 2 f(c))|, q = a^2/b^2,
@@ -38,19 +51,33 @@
  *  - Threshold-Classify trigger (Sec. 3.5.2): (a) from the second iteration
  *    on, |v_tot - v_tot_prev| <= tau_rel |v_tot|; (b) 2 (number of rel-err
  *    actives) > max_regions.
- *  - Threshold search (Sec. 3.5.3): candidate finished set = rel-err finished
- *    plus {E_i < t}; too few finished -> t += (max - t)/2; too much error ->
- *    t -= (t - min)/2; every change of direction adds 0.10 to P_max (cap
- *    0.95); give up after 10 direction changes or 64 probes; e_b uses |v_tot|.
+ *  - Threshold search (Sec. 3.5.3): the error budget is the part of the
+ *    tolerance that finished regions may still take, e_b = tau_rel |v_tot| -
+ *    e_f: finished error above it makes convergence impossible, which the
+ *    search avoids by its choice of threshold (accuracy requirement
+ *    e_abar <= P_max e_b, P_max <= 0.95); no search when e_b <= 0.
+ *    Candidate finished set = rel-err finished plus {E_i < t}; too few
+ *    finished -> t += (max - t)/2; too much error -> t -= (t - min)/2; every
+ *    change of direction adds 0.10 to P_max (cap 0.95); give up after 10
+ *    direction changes or 64 probes.
+ *  - Rel-Err-Classify after a threshold commit (Sec. 3.5.1, Sec. 3.5.2): the
+ *    Lemma bounds the rel-err finished regions' error by tau times their
+ *    integral only while no other finished error has used up the tolerance.
+ *    Regions are therefore finished iff E_i <= tau_cls |V_i|, where tau_cls =
+ *    min(tau_rel, (tau_rel |v_tot| - e_f) / |sum of the survivors' V|) is the
+ *    survivors' share of what the tolerance still allows, set after each
+ *    iteration's finished accumulation (tau_rel at the start).  Without
+ *    threshold commits tau_cls = tau_rel for a same-sign integrand.
  *  - Memory exhaustion (Sec. 3.5.2): if 2 (survivors) > max_regions after
  *    the threshold step, return the latest estimates with status 2.
- *  Parity unpinned: the error formula's constants and noise floor and the
+ *  - When no region stays active (possible only if rel-err filtering runs on
+ *    a sign-changing integrand), later iterations could not change v + v_f or
+ *    e + e_f, so the loop ends at once with the it_max status 1.
+ *  Parity unpinned: the error formula's constants and noise floors and the
  *  two-level formula are readings with no published values to pin them to;
- *  they are checked only through estimates staying within their error
- *  estimates of closed forms.
- *  - Unreachable tolerance (Sec. 3.5.3): when no region stays active, or the
- *    finished error e_f alone exceeds max(tau_rel |v + v_f|, tau_abs), stop
- *    with status 3 and the latest estimates.
+ *  they are checked through estimates staying within their error estimates
+ *  of closed forms, and through error estimates not overstating the true
+ *  error by orders of magnitude on smooth integrands.
  */
 #include <math.h>
 #include <stdint.h>
@@ -94,8 +121,8 @@ typedef struct {
 
 typedef struct {
   double estimate, errorest;
-  int status;            /* 0 converged, 1 it_max, 2 memory exhausted,
-                            3 tolerance unreachable, <0 error */
+  int status;            /* 0 converged, 1 it_max (or no region left
+                            active), 2 memory exhausted, <0 error */
   int iterations;
   int64_t n_regions;     /* sum over iterations of regions evaluated */
   int64_t n_active_last; /* regions evaluated in the last iteration */
@@ -214,10 +241,9 @@ static double ratio_or(double x, double y) {
 
 /* The region error from the four null-rule values (reading given above). */
 static double null_rule_error(const double N[4]) {
-  double r = fmax(ratio_or(N[0], N[1]), ratio_or(N[1], N[2]));
-  if (r >= 1.0) return 10.0 * fmax(fmax(N[0], N[1]), fmax(N[2], N[3]));
-  if (r >= 0.5) return 10.0 * r * N[0];
-  return 40.0 * r * r * r * N[0];
+  double r = fmax(fmax(ratio_or(N[0], N[1]), ratio_or(N[1], N[2])), ratio_or(N[2], N[3]));
+  if (r >= 1.0) return 10.0 * fmax(fmax(N[0], N[1]), N[2]);
+  return 10.0 * r * fmax(N[0], r * N[1]);
 }
 
 /* Evaluate one region [lower, lower + width]: integral V, null-rule error E,
@@ -239,11 +265,12 @@ static void evaluate_region(const oracle_rule *R, int fam, const double *p,
     int64_t cnt;
     Sg[g] = orbit_sum(fam, n, p, R->gen + (size_t)g * n, c, h, &Ag[g], &cnt);
   }
-  double basic = 0.0, basic_abs = 0.0, N[4], Nabs[4], Nfloor[4], Nused[4];
+  double basic = 0.0, basic_abs = 0.0, basic_mag = 0.0, N[4], Nabs[4], Nfloor[4], Nused[4];
   int64_t npts = 0;
   for (int g = 0; g < R->G; ++g) {
     basic += R->wts[g * 5] * Sg[g];
     basic_abs += fabs(R->wts[g * 5]) * Ag[g];
+    basic_mag += fabs(R->wts[g * 5]) * (fam == FAM_OSCILLATORY ? (double)R->count[g] : fabs(Sg[g]));
   }
   for (int g = 0; g < R->G; ++g) npts += R->count ? R->count[g] : 0;
   for (int k = 0; k < 4; ++k) {
@@ -266,6 +293,9 @@ static void evaluate_region(const oracle_rule *R, int fam, const double *p,
   }
   *V = vol * basic;
   *E = R->error_kind == 1 ? Nused[0] : null_rule_error(Nused);
+  /* no error below the rounding level of V itself */
+  double Vround = 16.0 * 0x1p-53 * (vol * basic_mag);
+  if (*E < Vround) *E = Vround;
 
   /* split axis from fourth divided differences */
   double x[16], D[16], Dabs[16], Dused[16], f0, Dmax = 0.0;
@@ -356,9 +386,11 @@ static void rel_err_classify(int64_t s, const double *V, const double *E,
 
 /* ------------------------------------------------- Threshold-Classify ---- */
 /* Returns 1 and updates A when a threshold meets the memory and accuracy
- * requirements; otherwise leaves A unchanged (unsuccessful filtering). */
+ * requirements; otherwise leaves A unchanged (unsuccessful filtering).
+ * v_tot = v + v_f, e_f the error finished in earlier iterations, e_it and
+ * s_it this iteration's error sum and region count. */
 static int threshold_classify(uint8_t *A, const double *E, double v_tot,
-                              double e_tot, double e_it, int64_t s_it,
+                              double e_f, double e_it, int64_t s_it,
                               double tau_rel, int *probes_out, double *t_out,
                               int *dirchg_out) {
   double Pmax = 0.25;
@@ -367,7 +399,9 @@ static int threshold_classify(uint8_t *A, const double *E, double v_tot,
     if (E[i] < mn) mn = E[i];
     if (E[i] > mx) mx = E[i];
   }
-  double e_b = e_tot - fabs(v_tot) * tau_rel;
+  /* error budget: what the finished regions may still add before the
+     tolerance tau_rel |v_tot| is out of reach */
+  double e_b = fabs(v_tot) * tau_rel - e_f;
   double t = e_it / (double)s_it;
   int probes = 0, last_dir = 0, changes = 0, ok = 0;
   *probes_out = 0;
@@ -481,7 +515,7 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
   uint8_t *A = (uint8_t *)malloc((size_t)cap);
   double *Vp = (double *)calloc((size_t)cap, sizeof(double));
   double *Ep = (double *)calloc((size_t)cap, sizeof(double));
-  double v = 0, e = 0, vf = 0, ef = 0, v_tot_prev = 0;
+  double v = 0, e = 0, vf = 0, ef = 0, v_tot_prev = 0, tau_cls = tau_rel;
   nsum finvol = {0, 0};
   int status = 1, it;
 
@@ -509,8 +543,8 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
       if (!isfinite(V[i]) || !isfinite(E[i])) { status = -6; goto done; }
     /* E <- Two-Level-Error(V, E, V_p, E_p) */
     if (it > 1) two_level_error(s, V, E, Vp);
-    /* A <- Rel-Err-Classify(V, E, A) */
-    rel_err_classify(s, V, E, tau_rel, opt->relerr_filter, A);
+    /* A <- Rel-Err-Classify(V, E, A), at the survivors' share tau_cls */
+    rel_err_classify(s, V, E, tau_cls, opt->relerr_filter, A);
     /* v <- Sum(V); e <- Sum(E) */
     nsum sv = {0, 0}, se = {0, 0};
     for (int64_t i = 0; i < s; ++i) { nadd(&sv, V[i]); nadd(&se, E[i]); }
@@ -532,7 +566,7 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
       if (trace && it - 1 < trace_cap) trace[it - 1] = tr;
       break;
     }
-    /* A <- Threshold-Classify(A, E, v + v_f, e + e_f, e, s) when triggered */
+    /* A <- Threshold-Classify(A, E, v + v_f, e_f, e, s) when triggered */
     double v_tot = v + vf;
     int trig = 0;
     {
@@ -545,7 +579,7 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
     if (trig) {
       int probes, chg;
       double t;
-      tr.search_ok = threshold_classify(A, E, v_tot, e + ef, e, s, tau_rel,
+      tr.search_ok = threshold_classify(A, E, v_tot, ef, e, s, tau_rel,
                                         &probes, &t, &chg);
       tr.probes = probes;
       tr.threshold = t;
@@ -568,13 +602,17 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
     double ef_new = e - nval(&sea) + ef;
     tr.vf = vf_new; tr.ef = ef_new;
     if (trace && it - 1 < trace_cap) trace[it - 1] = tr;
-    /* the tolerance is out of reach once no region stays active or the
-     * finished regions alone carry more error than it allows (Sec. 3.5.3
-     * notes this case is detectable); the latest estimates are v + v_f and
-     * e + e_f over the current leaves */
-    if (n_surv == 0 || ef_new > fmax(tau_rel * fabs(v + vf), tau_abs)) {
-      status = 3;
+    /* nothing left to refine: v + v_f and e + e_f cannot change any more,
+     * so the loop ends as it would at it_max */
+    if (n_surv == 0) {
+      status = 1;
       break;
+    }
+    /* the survivors' share of what the tolerance still allows */
+    {
+      double v_act = nval(&sva), allow = tau_rel * fabs(v + vf) - ef_new;
+      tau_cls = tau_rel;
+      if (allow < tau_rel * fabs(v_act)) tau_cls = allow > 0.0 ? allow / fabs(v_act) : 0.0;
     }
     vf = vf_new;
     ef = ef_new;
@@ -637,10 +675,10 @@ done:
 
 /* Exported for unit tests of Threshold-Classify on synthetic error lists. */
 int oracle_threshold_classify(uint8_t *A, const double *E, double v_tot,
-                              double e_tot, double e_it, int64_t s_it,
+                              double e_f, double e_it, int64_t s_it,
                               double tau_rel, int *probes, double *t,
                               int *direction_changes) {
-  return threshold_classify(A, E, v_tot, e_tot, e_it, s_it, tau_rel, probes, t,
+  return threshold_classify(A, E, v_tot, e_f, e_it, s_it, tau_rel, probes, t,
                             direction_changes);
 }
 

@@ -17,14 +17,22 @@ from paper_2104_06494_gb300.workloads import (draw_params, random_dyadic_regions
 FAMS = [PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0]
 
 
-@pytest.mark.parametrize("family", FAMS)
-@pytest.mark.parametrize("n,tau", [(2, 1e-3), (2, 1e-6), (2, 1e-9), (3, 1e-4), (3, 1e-7), (4, 1e-5)])
+# (family, n, tau): the five families on low dimensions.  The C0 family at
+# n = 2, tau = 1e-9 is left to test_kink_in_the_outer_margin_is_invisible:
+# with that seed a kink line sits in the outer 0.1 % of a column of boxes,
+# where no rule point sees it.
+LOW_DIM_CASES = [(f, n, tau) for f in FAMS
+                 for n, tau in [(2, 1e-3), (2, 1e-6), (2, 1e-9), (3, 1e-4), (3, 1e-7), (4, 1e-5)]
+                 if (f, n, tau) != (C0, 2, 1e-9)]
+
+
+@pytest.mark.parametrize("family,n,tau", LOW_DIM_CASES)
 def test_estimate_within_errorest_of_closed_form(family, n, tau):
     p = draw_params(family, n, 100 + 7 * family + n)
     ex = cf.closed_form(family, n, p)
     r = capi.integrate(family, n, p, tau, max_regions=2_000_000, relerr_filter=0 if family == OSCILLATORY else 1)
-    assert r.status in (0, 3), r.status
-    assert abs(r.estimate - ex) <= r.errorest + 1e-15 * abs(ex), (r.estimate, ex, r.errorest)
+    assert r.status in (0, 2), r.status
+    assert abs(r.estimate - ex) <= r.errorest, (r.estimate, ex, r.errorest)
     if r.status == 0:
         assert r.errorest <= tau * abs(r.estimate) * (1 + 1e-12) or r.errorest <= 1e-20
 
@@ -116,28 +124,62 @@ def test_bookkeeping_invariants(family, n, tau):
 
 
 def test_threshold_search_meets_requirements_when_it_accepts():
+    """On acceptance (Algorithm 3): more than half the regions finished, and
+    their error within P_max (<= .95) of the budget e_b = tau |v_tot| - e_f,
+    so the finished error e_f + e_abar stays below the tolerance tau |v_tot|
+    (convergence stays possible, Sec. 3.5.3)."""
     rng = SplitMix64(99)
+    accepted = 0
     for trial in range(40):
         s = 200 + trial * 37
-        E = np.array([10 ** rng.uniform(-12, -6) for _ in range(s)])
+        E = np.array([10 ** rng.uniform(-14, -6) for _ in range(s)])
         V = np.array([rng.uniform(1e-6, 2e-6) for _ in range(s)])
         tau = 1e-3
         A = (E > tau * V).astype(np.uint8)
         e_it = float(np.sum(E))
-        v_tot = float(np.sum(V))
-        e_tot = e_it * (1 + rng.uniform(0, 0.5))
-        e_b = e_tot - abs(v_tot) * tau
-        ok, Aout, probes, t, chg = capi.threshold_classify(A, E, v_tot, e_tot, e_it, tau)
+        v_tot = float(np.sum(V)) * (1 + rng.uniform(0, 4))
+        e_f = tau * v_tot * rng.uniform(0, 0.9)
+        e_b = tau * v_tot - e_f
+        ok, Aout, probes, t, chg = capi.threshold_classify(A, E, v_tot, e_f, e_it, tau)
         if ok:
+            accepted += 1
             fin = Aout == 0
             assert fin.sum() > 0.5 * s                       # memory requirement
             assert np.sum(E[fin]) <= 0.95 * e_b * (1 + 1e-12)  # accuracy requirement (P_max <= 0.95)
+            assert e_f + np.sum(E[fin]) < tau * v_tot          # the tolerance stays reachable
             assert np.all(Aout <= A)                          # rel-err finished stay finished
             assert np.all(Aout[E < t] == 0) and np.all(Aout[(E >= t) & (A == 1)] == 1)
             assert E.min() <= t <= E.max()
         else:
             assert np.array_equal(Aout, A)
-            assert probes == 64 or chg >= 10 or e_b <= 0
+            assert probes == 64 or chg >= 10
+    assert accepted >= 10
+
+
+def test_threshold_search_never_commits_more_error_than_the_tolerance_allows():
+    """The case the needed-decrease reading of the budget gets wrong: the
+    error estimate e is 100 times the tolerance while the digits of v have
+    settled (trigger (a)).  The needed decrease e - tau |v| is then about e,
+    so a threshold at the mean error would pass an accuracy requirement
+    against it while finishing error 20 times the whole tolerance; Sec. 3.5.3
+    calls such a commit one that makes convergence impossible.  Against the
+    allowance tau |v| - e_f the search must lower the threshold until the
+    finished error fits, or give up and leave A unchanged."""
+    tau, v_tot = 1e-6, 1.0
+    E = np.concatenate([np.full(600, 2e-11), np.full(300, 6.8e-8), np.full(100, 1e-6)])
+    e_it = float(E.sum())
+    assert e_it > 100 * tau * v_tot
+    mean = e_it / len(E)
+    assert np.count_nonzero(E < mean) == 900 and E[E < mean].sum() > 20 * tau * v_tot
+    A = np.ones(len(E), dtype=np.uint8)
+    ok, Aout, probes, t, chg = capi.threshold_classify(A, E, v_tot, 0.0, e_it, tau)
+    assert ok == 1 and t < mean and probes > 1
+    fin = Aout == 0
+    assert fin.sum() > len(E) / 2
+    assert E[fin].sum() <= 0.95 * tau * v_tot
+    # with most of the allowance already spent no threshold fits: unchanged
+    ok, Aout, probes, t, chg = capi.threshold_classify(A, E, v_tot, 0.99999 * tau * v_tot, e_it, tau)
+    assert ok == 0 and np.array_equal(Aout, A)
 
 
 def test_threshold_search_lowers_mean_threshold_when_budget_exceeded():
@@ -152,20 +194,60 @@ def test_threshold_search_lowers_mean_threshold_when_budget_exceeded():
     fin_at_mean = float(E[E < mean].sum())
     assert np.count_nonzero(E < mean) == 800
     e_b = fin_at_mean / 4.88
-    v_tot, tau = 1e3, 1e-6
-    e_tot = e_b + v_tot * tau
+    v_tot, tau = 1e3, 1e-1
+    e_f = v_tot * tau - e_b
     A = np.ones(s, dtype=np.uint8)
-    ok, Aout, probes, t, chg = capi.threshold_classify(A, E, v_tot, e_tot, e_it, tau)
+    ok, Aout, probes, t, chg = capi.threshold_classify(A, E, v_tot, e_f, e_it, tau)
     assert ok == 1 and probes > 1 and t < mean
     fin = Aout == 0
     assert fin.sum() > s / 2 and E[fin].sum() <= 0.95 * e_b
 
 
 def test_threshold_search_no_budget_returns_unchanged():
+    """e_f already at the tolerance: nothing more may be finished."""
     E = np.linspace(1, 2, 10)
     A = np.ones(10, dtype=np.uint8)
-    ok, Aout, probes, t, chg = capi.threshold_classify(A, E, 1.0, 1e-9, float(E.sum()), 1e-3)
+    ok, Aout, probes, t, chg = capi.threshold_classify(A, E, 1.0, 1e-3, float(E.sum()), 1e-3)
     assert ok == 0 and probes == 0 and np.array_equal(A, Aout)
+
+
+@pytest.mark.parametrize("family,n,tau,seed", [(GAUSSIAN, 4, 1e-8, 1), (PRODUCT_PEAK, 5, 1e-4, 2),
+                                               (GAUSSIAN, 5, 1e-6, 3), (CORNER_PEAK, 5, 1e-8, 4),
+                                               (C0, 3, 1e-4, 5), (GAUSSIAN, 5, 1e-4, 6)])
+def test_finished_error_never_exceeds_the_tolerance(family, n, tau, seed):
+    """Sec. 3.5.2: finished regions are never refined again, so the loop
+    must not commit more finished error than the tolerance allows.  The
+    threshold search keeps e_f + e_abar within P_max of the allowance, and
+    Rel-Err-Classify at the survivors' share tau_cls keeps the later rel-err
+    finishing inside what is left (Lemma of Sec. 3.5.1).  So at every
+    iteration e_f <= tau |v_tot| (tau_cls is set from the previous
+    iteration's survivors, whose children's sum differs from theirs by the
+    error estimate; the slack below covers that)."""
+    p = draw_params(family, n, 7000 + seed)
+    r = capi.integrate(family, n, p, tau, max_regions=1 << 16)
+    assert r.status in (0, 2)
+    searched = False
+    vf_old = 0.0
+    for t in r.trace:
+        v_tot = t["v"] + vf_old
+        assert t["ef"] <= tau * abs(v_tot) * (1 + 1e-3), (t, tau * abs(v_tot))
+        searched |= bool(t["search_ok"])
+        vf_old = t["vf"]
+    assert searched
+
+
+def test_no_region_left_ends_with_the_it_max_status():
+    """Rel-err filtering on a sign-changing integrand (which Sec. 3.5.1 warns
+    against): cos(2 pi (0.1 + x_0 + x_1)) integrates to 0 over whole
+    periods, no box centre of the first pass lies on a zero of it, so every
+    box has E_i <= tau |V_i| and is finished, yet (e + e_f) / |v + v_f|
+    fails.  Later iterations would evaluate nothing and change nothing, so
+    the loop ends at once with status 1 and the same estimates."""
+    two_pi = 2 * math.pi
+    r = capi.integrate(OSCILLATORY, 2, [0.1, two_pi, two_pi], 1e-6, relerr_filter=1)
+    assert r.status == 1 and r.iterations == 1
+    assert r.trace[0]["n_survivors"] == 0
+    assert abs(r.estimate) < 1e-15 and r.errorest > 1e-6 * abs(r.estimate)
 
 
 def test_status_memory_exhausted():
@@ -198,14 +280,17 @@ def test_default_initial_divisions():
 
 
 @pytest.mark.parametrize("p", [[4, 0], [2, 2], [5, 0], [3, 1], [1, 1]])
-def test_error_vanishes_for_exactly_integrated_polynomials(p):
+def test_error_at_rounding_level_for_exactly_integrated_polynomials(p):
     """Degree <= 5: the degree-7 and degree-5 null rules annihilate f, so
     N_1 and N_2 are pure rounding; below their noise floors they count as
-    zero, r = 0 and the region error is exactly 0 (the rule is exact here)."""
+    zero, r = 0, and the region error is the rounding level of V alone,
+    16 u vol sum_g |w_g| |S_g| (here at most 16 u times the rule's absolute
+    sum vol sum_g |w_g| sum_orbit |f|)."""
     V, E, K, D = capi.evaluate(100, 2, p, [[0.1, 0.2]], [[0.5, 0.25]], diag=True)
-    assert E[0] == 0.0
     n = 2
     assert D[0, 0] <= D[0, 9 + 2 * n] and D[0, 1] <= D[0, 10 + 2 * n]
+    assert 0.0 < E[0] <= 16 * 2.0 ** -53 * D[0, 8] * (1 + 1e-12)
+    assert E[0] <= 1e-14 * abs(V[0])
 
 
 @pytest.mark.parametrize("n", [2, 5, 8])
@@ -219,15 +304,21 @@ def test_identically_zero_integrand(n):
 
 @pytest.mark.parametrize("n", [3, 8])
 def test_constant_integrand_is_exact(n):
-    """(sum x^2)^0 = 1: the rule integrates constants exactly, every null rule
-    annihilates them, so the first pass returns the volume with zero error,
-    on the unit cube and on a general box."""
+    """(sum x^2)^0 = 1: the rule integrates constants exactly and every null
+    rule annihilates them, so the first pass returns the volume, with an
+    error estimate at the rounding level of the rule sums, on the unit cube
+    and on a general box."""
     o = capi.integrate(6, n, [0.0], 1e-12)
-    assert (o.status, o.iterations, o.estimate, o.errorest) == (0, 1, 1.0, 0.0)
+    # the error is the rounding level of the rule sums: 16 u sum_g |w_g| count_g
+    wsum = float(np.sum(np.abs(np.array(rule.rule_tables(n)[1], dtype=float)[:, 0]) *
+                        np.array(rule.exact_rule(n)[1], dtype=float)))
+    assert (o.status, o.iterations, o.estimate) == (0, 1, 1.0)
+    assert 0.0 < o.errorest <= 16 * 2.0 ** -53 * wsum * (1 + 1e-9)
     lo = [-1.0, 0.0, 2.0] + [0.0] * (n - 3)
     hi = [1.0, 3.0, 2.5] + [1.0] * (n - 3)
     o = capi.integrate(6, n, [0.0], 1e-12, bounds=(lo, hi))
-    assert o.status == 0 and abs(o.estimate - 3.0) <= 4e-16 * 3.0 and o.errorest == 0.0
+    assert o.status == 0 and abs(o.estimate - 3.0) <= 4e-16 * 3.0
+    assert 0.0 < o.errorest <= 3.0 * 16 * 2.0 ** -53 * wsum * (1 + 1e-9)
 
 
 def test_openmp_build_reproduces_the_serial_oracle():
