@@ -67,7 +67,10 @@
  *    min(tau_rel, (tau_rel |v_tot| - e_f) / |sum of the survivors' V|) is the
  *    survivors' share of what the tolerance still allows, set after each
  *    iteration's finished accumulation (tau_rel at the start).  Without
- *    threshold commits tau_cls = tau_rel for a same-sign integrand.
+ *    threshold commits tau_cls = tau_rel for a same-sign integrand.  A share
+ *    below tau_rel is rounded down to a power of two: once most of the
+ *    tolerance is spent, the allowance is a difference of nearly equal sums
+ *    whose rounding would otherwise move the tolerance itself.
  *  - Memory exhaustion (Sec. 3.5.2): if 2 (survivors) > max_regions after
  *    the threshold step, return the latest estimates with status 2.
  *  - When no region stays active (possible only if rel-err filtering runs on
@@ -608,11 +611,19 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
       status = 1;
       break;
     }
-    /* the survivors' share of what the tolerance still allows */
+    /* the survivors' share of what the tolerance still allows, rounded down
+     * to a power of two */
     {
       double v_act = nval(&sva), allow = tau_rel * fabs(v + vf) - ef_new;
       tau_cls = tau_rel;
-      if (allow < tau_rel * fabs(v_act)) tau_cls = allow > 0.0 ? allow / fabs(v_act) : 0.0;
+      if (allow < tau_rel * fabs(v_act)) {
+        int ex;
+        tau_cls = 0.0;
+        if (allow > 0.0) {
+          frexp(allow / fabs(v_act), &ex);
+          tau_cls = ldexp(0.5, ex);
+        }
+      }
     }
     vf = vf_new;
     ef = ef_new;
