@@ -55,7 +55,14 @@
  *    tolerance that finished regions may still take, e_b = tau_rel |v_tot| -
  *    e_f: finished error above it makes convergence impossible, which the
  *    search avoids by its choice of threshold (accuracy requirement
- *    e_abar <= P_max e_b, P_max <= 0.95); no search when e_b <= 0.
+ *    e_abar <= P_max e_b, P_max <= 0.95); no search when e_b <= 0.  e_b is
+ *    rounded down to a power of two: once most of the tolerance is spent it
+ *    is a difference of nearly equal sums, whose low bits are rounding.
+ *  - Sums of Algorithm 2/3 that are small differences of large sums are
+ *    formed directly: e_abar (= e_it - sum A.E) as the sum of E over the
+ *    finished candidates, v - sum V.A and e - sum E.A over the finished
+ *    regions.  Equal in exact arithmetic; the direct sums carry the
+ *    rounding of the finished part only.
  *    Candidate finished set = rel-err finished plus {E_i < t}; too few
  *    finished -> t += (max - t)/2; too much error -> t -= (t - min)/2; every
  *    change of direction adds 0.10 to P_max (cap 0.95); give up after 10
@@ -403,8 +410,15 @@ static int threshold_classify(uint8_t *A, const double *E, double v_tot,
     if (E[i] > mx) mx = E[i];
   }
   /* error budget: what the finished regions may still add before the
-     tolerance tau_rel |v_tot| is out of reach */
+     tolerance tau_rel |v_tot| is out of reach, rounded down to a power of
+     two (a difference of nearly equal sums once most of the tolerance is
+     spent: its low bits are the rounding of e_f) */
   double e_b = fabs(v_tot) * tau_rel - e_f;
+  if (e_b > 0.0) {
+    int ex;
+    frexp(e_b, &ex);
+    e_b = ldexp(0.5, ex);
+  }
   double t = e_it / (double)s_it;
   int probes = 0, last_dir = 0, changes = 0, ok = 0;
   *probes_out = 0;
@@ -413,19 +427,21 @@ static int threshold_classify(uint8_t *A, const double *E, double v_tot,
   if (!(e_b > 0.0)) return 0;
   uint8_t *Acand = (uint8_t *)malloc((size_t)s_it);
   for (;;) {
-    /* Apply-Threshold: finished = rel-err finished or E_i < t */
-    nsum sumAE = {0, 0};
+    /* Apply-Threshold: finished = rel-err finished or E_i < t; e_abar, the
+     * error of the finished candidates, summed directly (e_it - sum(A.E) is
+     * the same number formed by cancellation) */
+    nsum fin = {0, 0};
     int64_t sumA = 0;
     for (int64_t i = 0; i < s_it; ++i) {
       Acand[i] = A[i] && !(E[i] < t);
       sumA += Acand[i];
-      if (Acand[i]) nadd(&sumAE, E[i]);
+      if (!Acand[i]) nadd(&fin, E[i]);
     }
     ++probes;
     int64_t s_abar = s_it - sumA;
     int dir;
     if (s_abar > 0.5 * (double)s_it) {           /* memory requirement */
-      double e_abar = e_it - nval(&sumAE);
+      double e_abar = nval(&fin);
       if (e_abar <= Pmax * e_b) { ok = 1; break; } /* accuracy requirement */
       dir = -1;                                   /* too much error: lower t */
     } else {
@@ -597,12 +613,13 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
       if (trace && it - 1 < trace_cap) trace[it - 1] = tr;
       break;
     }
-    /* v_f <- v - Sum(V.A) + v_f ; e_f <- e - Sum(E.A) + e_f */
-    nsum sva = {0, 0}, sea = {0, 0};
+    /* v_f <- v - Sum(V.A) + v_f ; e_f <- e - Sum(E.A) + e_f, with v - Sum(V.A)
+     * and e - Sum(E.A) summed directly over the finished regions */
+    nsum svf = {0, 0}, sef = {0, 0};
     for (int64_t i = 0; i < s; ++i)
-      if (A[i]) { nadd(&sva, V[i]); nadd(&sea, E[i]); }
-    double vf_new = v - nval(&sva) + vf;
-    double ef_new = e - nval(&sea) + ef;
+      if (!A[i]) { nadd(&svf, V[i]); nadd(&sef, E[i]); }
+    double vf_new = vf + nval(&svf);
+    double ef_new = ef + nval(&sef);
     tr.vf = vf_new; tr.ef = ef_new;
     if (trace && it - 1 < trace_cap) trace[it - 1] = tr;
     /* nothing left to refine: v + v_f and e + e_f cannot change any more,
@@ -614,7 +631,7 @@ int oracle_pagani(const oracle_rule *R, int fam, const double *params,
     /* the survivors' share of what the tolerance still allows, rounded down
      * to a power of two */
     {
-      double v_act = nval(&sva), allow = tau_rel * fabs(v + vf) - ef_new;
+      double v_act = v - nval(&svf), allow = tau_rel * fabs(v + vf) - ef_new;
       tau_cls = tau_rel;
       if (allow < tau_rel * fabs(v_act)) {
         int ex;
