@@ -63,6 +63,11 @@
  *    finished candidates, v - sum V.A and e - sum E.A over the finished
  *    regions.  Equal in exact arithmetic; the direct sums carry the
  *    rounding of the finished part only.
+ *    The first threshold is the mean error and the range [min, max] of the
+ *    errors, rounded to powers of two (the mean down, min down, max up):
+ *    errors carry the rounding of the null-rule and two-level differences
+ *    they come from, and rounded inputs let two implementations of the same
+ *    arithmetic probe the same thresholds.
  *    Candidate finished set = rel-err finished plus {E_i < t}; too few
  *    finished -> t += (max - t)/2; too much error -> t -= (t - min)/2; every
  *    change of direction adds 0.10 to P_max (cap 0.95); give up after 10
@@ -409,6 +414,9 @@ static int threshold_classify(uint8_t *A, const double *E, double v_tot,
     if (E[i] < mn) mn = E[i];
     if (E[i] > mx) mx = E[i];
   }
+  /* the search range [min, max] rounded outward to powers of two */
+  if (mn > 0.0) { int ex; frexp(mn, &ex); mn = ldexp(0.5, ex); }
+  if (mx > 0.0) { int ex; double m = frexp(mx, &ex); mx = m == 0.5 ? mx : ldexp(1.0, ex); }
   /* error budget: what the finished regions may still add before the
      tolerance tau_rel |v_tot| is out of reach, rounded down to a power of
      two (a difference of nearly equal sums once most of the tolerance is
@@ -419,7 +427,9 @@ static int threshold_classify(uint8_t *A, const double *E, double v_tot,
     frexp(e_b, &ex);
     e_b = ldexp(0.5, ex);
   }
+  /* start: the mean error, rounded down to a power of two */
   double t = e_it / (double)s_it;
+  if (t > 0.0) { int ex; frexp(t, &ex); t = ldexp(0.5, ex); }
   int probes = 0, last_dir = 0, changes = 0, ok = 0;
   *probes_out = 0;
   *t_out = t;
