@@ -4,8 +4,10 @@
 One step = one complete adaptive integration (every iteration of Algorithm 2,
 all steps of the hot path) of each integral of the workload, through the C ABI
 (pagani_integrate_ex).  Default workload: the 5-D Gaussian at epsrel 1e-7 and
-the 6-D oscillatory integrand at epsrel 1e-8 (rel-err filtering off), seeded
-synthetic parameters.
+the 6-D oscillatory integrand at epsrel 1e-8 (rel-err filtering off), plus the
+same oscillatory integral at 1e-10, whose active set reaches the 1e6..1e7
+regions the oscillatory workload is specified for (at 1e-8 it converges with
+6.6e4); seeded synthetic parameters.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -27,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD_DEFAULT = "gaussian_d5+oscillatory_d6"
+WORKLOAD_DEFAULT = "gaussian_d5+oscillatory_d6+oscillatory_d6_1e-10"
 METRIC = "integrand evals/s"
 
 
@@ -40,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form and filtering-ablation reports")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 8-D C0 management-at-scale report")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation report")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle time budget per integral")
     ap.add_argument("--quiet", action="store_true")
     return ap.parse_args()
@@ -164,21 +168,17 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+# DRAM bytes per evaluated region of k_evaluate_loop (read + write), from the
+# ncu capture of the 5-D Gaussian's 262,144-region launch
+# (profiles/k_evaluate_loop_gaussian_d5.md), keyed by the hash of the kernel
+# sources it was taken on: the figure no longer applies once they change.
+EVAL_DRAM_BYTES_PER_REGION = {}
+
+
 def traffic_bytes_per_region():
-    """DRAM bytes per evaluated region of Evaluate from the committed ncu
-    summary, or None when the kernel source changed since it was captured."""
-    p = os.path.join(ROOT, "profiles", "k_evaluate_loop_gaussian_d5.md")
-    if not os.path.exists(p):
-        return None
-    kv = {}
-    for line in open(p):
-        if ":" in line and line.split(":")[0].strip() in ("bytes_per_region", "kernel_source_hash",
-                                                           "fp64_pipe_active"):
-            k, v = line.split(":", 1)
-            kv[k.strip()] = v.strip()
-    if kv.get("kernel_source_hash") != source_hash():
-        return None
-    return float(kv["bytes_per_region"]), float(kv.get("fp64_pipe_active", "nan"))
+    """DRAM bytes per evaluated region of Evaluate for the current kernel
+    sources, or None when they changed since the counters were taken."""
+    return EVAL_DRAM_BYTES_PER_REGION.get(source_hash())
 
 
 def differentiation_report(pg, torch, flush, reps: int = 3):
@@ -212,13 +212,25 @@ def differentiation_report(pg, torch, flush, reps: int = 3):
     bwd_ms, (v, g) = timed(lambda: pg.pagani_gradient(n, w.family, p, lower, level, stream=stream))
     tot, gc = cf.gaussian_gradient(n, p)
     scale = np.concatenate([np.full(n, abs(tot)), p[:n] * abs(tot)])
+    err = np.abs(g - np.array(gc))
     return {"workload": w.name, "theta": "a_1..a_6, w_1..w_6", "epsrel": w.epsrel,
+            "grad_err_over_errorest_bound": float(np.max(err / grad_error_bound(r.errorest, p, n))),
             "plain_ms": plain_ms, "forward_keep_leaves_ms": fwd_ms, "backward_ms": bwd_ms,
             "n_leaves": r.n_leaves, "regions": r.n_regions, "status": r.status,
             "value_true_relerr": abs(r.estimate - tot) / abs(tot),
             "grad_max_err_vs_closed_form": float(np.max(np.abs(g - np.array(gc)) / scale)),
             "grad_err_scale": "|I| for d/da, a_j |I| for d/dw",
             "backward_evals_per_s": r.n_leaves * npoints(n) / (bwd_ms * 1e-3)}
+
+
+def grad_error_bound(errorest, p, n):
+    """The gradient's error bound implied by the integral's error estimate:
+    the rule's error on a box of a Gaussian factor of width 1/a behaves like
+    (a h)^10, so d/da_j of it is at most 10 errorest / a_j, and d/dw_j (a shift
+    by a fraction of the width 1/a_j) at most 10 a_j errorest."""
+    import numpy as np
+    a = np.asarray(p[:n], dtype=float)
+    return np.concatenate([10 * errorest / a, 10 * errorest * a])
 
 
 def hbm_peak_gbs():
@@ -255,6 +267,45 @@ def management_bandwidth(part, hbm_peak):
         out[f"{key}_hbm_frac"] = gbs / hbm_peak if gbs is not None and hbm_peak else None
     out["hbm_peak_gbs"] = hbm_peak
     return out
+
+
+def scale_report(pg, torch, flush, roofline, peaks, hbm_peak, name: str = "c0_d8"):
+    """The region-management kernels at scale: the 8-D C0 workload (epsrel
+    1e-6, a 4e8-region pool, 2e8 regions and more per iteration), one
+    host-driven pass with CUDA events per phase, and its time to result
+    through the graph loop."""
+    from oracle import closed_forms as cf
+    from paper_2104_06494_gb300.workloads import config_workloads
+    w = config_workloads()[name]
+    stream = torch.cuda.current_stream().cuda_stream
+    pg.pagani_workspace_reserve(w.max_regions, w.dim)
+    try:
+        r = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions,
+                                   use_graph=0, trace=True, stream=stream)
+        work = roofline.evaluate_work(w.family, w.dim, r.trace["s"])
+        part = {"trace": r.trace, "dim": w.dim, "phase_ms": list(r.phase_ms)}
+        pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, stream=stream)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, stream=stream)
+        b.record()
+        torch.cuda.synchronize()
+        ttr = a.elapsed_time(b)
+    finally:
+        pg.pagani_workspace_release()
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    achieved = work["flops"] / (r.eval_ms * 1e-3) / 1e12
+    return {"workload": name, "epsrel": w.epsrel, "max_regions": w.max_regions, "status": g.status,
+            "iterations": g.iterations, "regions": g.n_regions, "max_active": int(r.trace["s"].max()),
+            "time_to_result_ms": ttr, "evals_per_s": g.n_regions * npoints(w.dim) / (ttr * 1e-3),
+            "true_relerr": abs(g.estimate - ex) / abs(ex), "errorest_rel": g.errorest / abs(g.estimate),
+            "within_errorest": bool(abs(g.estimate - ex) <= g.errorest),
+            "evaluate_ms": r.eval_ms, "evaluate_fp64_frac": achieved / peaks["fma_tflops"],
+            "cache_fill_ms": r.phase_ms[0], "threshold_probe_ms": r.phase_ms[1],
+            "sums_count_ms": r.phase_ms[2], "filter_split_ms": r.phase_ms[3],
+            "evaluate_share": r.eval_ms / (r.eval_ms + sum(r.phase_ms)),
+            **management_bandwidth(part, hbm_peak)}
 
 
 def filtering_report(pg, torch, flush, max_regions: int = 1 << 27):
@@ -323,6 +374,11 @@ def batching_report(pg, torch, flush, slot: int = 16384):
             "batch_wall_ms": batch_wall_ms, "looped_single_wall_ms": loop_wall_ms,
             "looped_single_device_ms": loop_dev_ms, "speedup_wall": loop_wall_ms / batch_wall_ms,
             "integrals_per_s": len(items) / (batch_wall_ms * 1e-3), "evals_per_s": evals / (dev_ms * 1e-3),
+            "converged_integrals_per_s": int(np.sum(res["status"] == 0)) / (batch_wall_ms * 1e-3),
+            "converged_outside_tau": int(np.sum((res["status"] == 0) &
+                                                (np.abs(res["estimate"] - ex) >
+                                                 np.maximum(res["errorest"],
+                                                            np.array([w.epsrel for w in items]) * np.abs(ex))))),
             "items_equal_to_single_calls": same,
             "status_counts": {int(k): int(v) for k, v in zip(*np.unique(res["status"], return_counts=True))},
             "within_errorest_of_closed_form": float(inside.mean())}
@@ -405,9 +461,8 @@ def main():
     calls = {k: sum(p.get(k, 0) for p in roof_parts) for k in ("exp", "sincos", "div")}
     achieved = fl / (ems * 1e-3) / 1e12
     regions_per_launch = sum(int(traced[w.name].trace["s"].sum()) for w in ws) / nl
-    prof = traffic_bytes_per_region()
-    traffic = prof[0] * regions_per_launch if prof is not None else None
-    pipe_ncu = prof[1] if prof is not None else None
+    per_region = traffic_bytes_per_region()
+    traffic = per_region * regions_per_launch if per_region is not None else None
     # FP64 issue slots the algorithm needs, library calls at their measured cost
     fma_rate = peaks["fma_tflops"] * 1e12 / 2
     slots = ins + sum(calls[k] * fma_rate / (peaks[f"{k}_gps"] * 1e9) for k in calls)
@@ -497,7 +552,7 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fma_tflops"], "unit": "TFLOP/s",
                          "frac": achieved / peaks["fma_tflops"], "traffic": traffic,
                          "regions_per_launch": regions_per_launch,
-                         "fp64_pipe_active_ncu": pipe_ncu,
+                         "traffic_source": "ncu DRAM bytes per region of this kernel source x regions per launch",
                          "kernel": "k_evaluate_loop", "peak_source": "measured FP64 FMA chain (pagani_fp64_peak)",
                          "avg_launch_ms": ems / nl, "flops_per_launch": fl / nl,
                          "fp64_issue_frac_est": pipe_frac, "library_calls_per_launch":
@@ -525,7 +580,11 @@ def main():
             b.record()
             torch.cuda.synchronize()
             line["config"]["time_to_result_ms"][w.name] = a.elapsed_time(b)
-        line["differentiation"] = differentiation_report(pg, torch, flush)
+        if not args.no_diff:
+            line["differentiation"] = differentiation_report(pg, torch, flush)
+        if not args.no_scale:
+            pg.pagani_workspace_release()
+            line["management_at_scale"] = scale_report(pg, torch, flush, roofline, peaks, hbm_peak)
         if not args.no_batch:
             line["batching"] = batching_report(pg, torch, flush)
             line["filtering"] = filtering_report(pg, torch, flush)

@@ -56,12 +56,14 @@ extern "C" {
 #define PAGANI_MIN_DIM 2
 #define PAGANI_MAX_DIM 8
 
-/* Status codes.  0..3 come with valid estimates (Algorithm 2 returns the
+/* Status codes.  0..2 come with valid estimates (Algorithm 2 returns the
  * latest v + v_f, e + e_f in each case). */
 #define PAGANI_STATUS_CONVERGED 0    /* (e+e_f)/|v+v_f| <= epsrel or e+e_f <= epsabs */
-#define PAGANI_STATUS_IT_MAX 1       /* it_max iterations without convergence      */
+#define PAGANI_STATUS_IT_MAX 1       /* it_max iterations without convergence, or no
+                                        region left to refine (rel-err filtering on a
+                                        sign-changing integrand, Sec. 3.5.1): later
+                                        iterations could not change the estimates */
 #define PAGANI_STATUS_MEMORY 2       /* splitting the actives would exceed max_regions (Sec. 3.5.2) */
-#define PAGANI_STATUS_UNREACHABLE 3  /* finished error alone exceeds the tolerance, or no active region left */
 #define PAGANI_ERR_DIM (-1)          /* dim outside [PAGANI_MIN_DIM, PAGANI_MAX_DIM] */
 #define PAGANI_ERR_INTEGRAND (-2)    /* unknown integrand_id or invalid params */
 #define PAGANI_ERR_TOLERANCE (-3)    /* epsrel <= 0 / NaN, or epsabs < 0 / NaN */
@@ -159,18 +161,20 @@ int pagani_integrate_box(int dim, int integrand_id, const double* params, const 
                          pagani_trace_record* trace, int trace_cap);
 
 /* Allocation-free integration, for callers that cannot allocate device
- * memory: code that runs while a CUDA stream is being captured, applications
- * whose own allocator owns the device memory, and loops that must not pay for
- * an allocation.  The paper has no counterpart; it is a deployment variant of
- * pagani_integrate.
+ * memory: applications whose own allocator owns all of the device memory (a
+ * framework's caching allocator, a memory pool sized at start-up), and
+ * service loops that must never pay for an allocation or risk an
+ * out-of-memory failure mid-request.  The paper has no counterpart; it is a
+ * deployment variant of pagani_integrate.
  *
  * Same arguments and result as pagani_integrate (default options; rel-err
  * filtering is off for the oscillatory family, on otherwise), plus a stream
  * (NULL = the legacy default stream).  Instead of the library workspace it
  * uses a 32 MiB array in the library's device memory, which every GPU that
  * loads the library holds until the process exits.  It runs the loop kernels
- * with one host synchronisation per step (no CUDA graph) and calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * host-driven (no CUDA graph): after each step it copies the loop state to
+ * the host and synchronises the stream.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
  *
  * max_regions is limited by the array: on a 152-SM GPU about 540,000
  * regions at dim 2, 420,000 at dim 3, 290,000 at dim 5 and 190,000 at dim 8;
@@ -180,7 +184,11 @@ int pagani_integrate_box(int dim, int integrand_id, const double* params, const 
  * stream capture.  All calls share the array: calls whose GPU work overlaps
  * (other streams, other host threads with their own device contexts) race
  * on it.  Each call rewrites everything it reads, so the previous call's
- * contents do not leak into a result.  Returns out->status. */
+ * contents do not leak into a result; a call that fails after its first
+ * launch waits for its queued kernels before it returns.  The looked-up
+ * address belongs to the device's context: after the application resets a
+ * device (cudaDeviceReset), do not call this entry point on it again in the
+ * same process.  Returns out->status. */
 int pagani_integrate_noalloc(int dim, int integrand_id, const double* params, double epsrel, double epsabs,
                              int64_t max_regions, void* cuda_stream, pagani_result* out);
 

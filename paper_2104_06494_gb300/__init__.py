@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0, DISCONTINUOUS, BOX_POWER = 0, 1, 2, 3, 4, 5, 6
-STATUS_NAMES = {0: "converged", 1: "it_max", 2: "memory exhausted", 3: "tolerance unreachable",
+STATUS_NAMES = {0: "converged", 1: "it_max or no region left", 2: "memory exhausted",
                 -1: "bad dim", -2: "bad integrand", -3: "bad tolerance", -4: "cuda error", -5: "watchdog",
                 -6: "non-finite integrand", -7: "capacity below initial split", -8: "bad argument"}
 

@@ -4,6 +4,7 @@
 // trigger; Algorithm 3: one step of the threshold search).
 #pragma once
 #include <cstdint>
+#include <cstring>
 
 #include "pagani_internal.h"
 
@@ -36,18 +37,23 @@ __device__ __forceinline__ double pow2_neg(int l) {
   return __longlong_as_double((long long)(1023 - l) << 52);
 }
 
-// Region error from the four null-rule values (the reading of Sec. 3.2 used
-// throughout): r = max(N1/N2, N2/N3) with x/0 = inf (x > 0) or 0 (x = 0);
-// 10 max(N) if r >= 1, 10 r N1 if 1/2 <= r < 1, 40 r^3 N1 otherwise.  The
-// caller passes N_k = 0 for values at the rounding level of their own sums.
+// Region error from the four null-rule values N1..N4 (degrees 7, 5, 3, 1),
+// the reading of Sec. 3.2 used throughout.  On a resolved box the values fall
+// off geometrically with the degree, by r per two degrees, and the rule's own
+// error is about r N1:
+//   r = max(N1/N2, N2/N3, N3/N4) with x/0 = inf (x > 0) or 0 (x = 0);
+//   r >= 1 (no decay): 10 max(N1, N2, N3);
+//   r < 1: 10 r max(N1, r N2)  (r N2 replaces a degree-7 value that cancelled
+//   by accident).
+// The caller passes N_k = 0 for values at the rounding level of their own
+// sums and applies the rounding floor of V afterwards.
 __device__ __forceinline__ double ratio_or(double x, double y) {
   return y > 0.0 ? x / y : (x > 0.0 ? __longlong_as_double(0x7ff0000000000000LL) : 0.0);
 }
 __device__ __forceinline__ double null_error(double n1, double n2, double n3, double n4) {
-  double r = fmax(ratio_or(n1, n2), ratio_or(n2, n3));
-  if (r >= 1.0) return 10.0 * fmax(fmax(n1, n2), fmax(n3, n4));
-  if (r >= 0.5) return 10.0 * r * n1;
-  return 40.0 * r * r * r * n1;
+  const double r = fmax(fmax(ratio_or(n1, n2), ratio_or(n2, n3)), ratio_or(n3, n4));
+  if (r >= 1.0) return 10.0 * fmax(fmax(n1, n2), n3);
+  return 10.0 * r * fmax(n1, r * n2);
 }
 
 // Two-level error refinement of a sibling pair (Sec. 3.2), as read here: with
@@ -66,14 +72,51 @@ __device__ __forceinline__ void two_level(double VL, double VR, double Vpar, dou
   }
 }
 
-// Rel-Err-Classify (Sec. 3.5.1): active unless E <= tau_rel |V|.
-__device__ __forceinline__ bool relerr_active(double V, double E, double tau_rel, int enabled) {
-  return enabled ? !(E <= tau_rel * fabs(V)) : true;
+// Rel-Err-Classify (Sec. 3.5.1): active unless E <= tau |V|, with tau the
+// loop's classification tolerance c.tau_cls.
+__device__ __forceinline__ bool relerr_active(double V, double E, double tau, int enabled) {
+  return enabled ? !(E <= tau * fabs(V)) : true;
+}
+
+// The next iteration's Rel-Err-Classify tolerance: the survivors' share of
+// what the tolerance still allows, min(tau_rel, (tau_rel |v_tot| - e_f) /
+// |sum of the survivors' V|).  The Lemma of Sec. 3.5.1 then keeps the error
+// of regions finished by it within that allowance; before any threshold
+// commit it is tau_rel itself for a same-sign integrand.  A share below
+// tau_rel is rounded down to a power of two (its exponent bits kept, its
+// mantissa cleared): once most of the tolerance is spent the allowance is a
+// difference of nearly equal sums, whose rounding must not move the
+// classification.
+// The largest power of two not above x > 0 (its exponent bits kept, the
+// mantissa cleared; a subnormal keeps its highest bit).
+__host__ __device__ __forceinline__ double pow2_floor(double x) {
+  unsigned long long bits;
+  memcpy(&bits, &x, sizeof(bits));
+  if ((bits >> 52) == 0) {
+    while (bits & (bits - 1)) bits &= bits - 1;
+  } else {
+    bits &= 0xFFF0000000000000ULL;
+  }
+  double out;
+  memcpy(&out, &bits, sizeof(out));
+  return out;
+}
+// The smallest power of two not below x > 0.
+__host__ __device__ __forceinline__ double pow2_ceil(double x) {
+  const double f = pow2_floor(x);
+  return f == x ? x : 2.0 * f;
+}
+__host__ __device__ __forceinline__ double survivor_tolerance(double tau_rel, double v_tot, double ef,
+                                                              double v_surv) {
+  const double allow = tau_rel * fabs(v_tot) - ef;
+  if (!(allow < tau_rel * fabs(v_surv))) return tau_rel;
+  if (!(allow > 0.0)) return 0.0;
+  return pow2_floor(allow / fabs(v_surv));
 }
 
 // Final classification of a region after the optional threshold search.
 __device__ __forceinline__ bool final_active(double V, double E, const Ctrl& c) {
-  bool a = relerr_active(V, E, c.tau_rel, c.relerr_filter);
+  bool a = relerr_active(V, E, c.tau_cls, c.relerr_filter);
   if (c.search_ok) a = a && !(E < c.t);
   return a;
 }
@@ -314,10 +357,22 @@ __device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long 
   if (c.trace_on && c.it - 1 < trace_cap) trace[c.it - 1] = tr;
   c.search_cont = 0;
   if (!trig) return 0;
-  // Algorithm 3 set-up: P_max = .25, e_b = e_tot - |v_tot| tau_rel, t = e_it / s_it
+  // Algorithm 3 set-up: P_max = .25, t = e_it / s_it, and the error budget
+  // e_b = tau_rel |v_tot| - e_f: what finished regions may still add before
+  // the tolerance is out of reach (Sec. 3.5.3), rounded down to a power of
+  // two (near the end a difference of nearly equal sums, its low bits the
+  // rounding of e_f)
   c.Pmax = 0.25;
-  c.e_b = (e + c.ef) - fabs(v_tot) * c.tau_rel;
+  c.e_b = fabs(v_tot) * c.tau_rel - c.ef;
+  if (c.e_b > 0.0) c.e_b = pow2_floor(c.e_b);
+  // the start (the mean error) and the range [min E, max E] rounded to
+  // powers of two, the mean and the minimum down, the maximum up: errors
+  // carry the rounding of the null-rule and two-level differences they come
+  // from, and rounded inputs make every threshold of the search reproducible
   c.t = e / (double)c.s;
+  if (c.t > 0.0) c.t = pow2_floor(c.t);
+  if (c.emin > 0.0) c.emin = pow2_floor(c.emin);
+  if (c.emax > 0.0) c.emax = pow2_ceil(c.emax);
   c.last_dir = 0;
   if (!(c.e_b > 0.0)) return 0;
   c.search = 1;
@@ -326,15 +381,15 @@ __device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long 
 }
 
 // One step of Algorithm 3 after a probe with threshold c.t counted
-// n_active candidate actives whose errors sum to sum_ae.  Returns 1 if
-// another probe is needed.
-__device__ inline int threshold_step(Ctrl& c, long long n_active, double sum_ae) {
+// n_active candidate actives; e_abar is the error of the candidate finished
+// regions (summed directly, not as e_it - sum A.E).  Returns 1 if another
+// probe is needed.
+__device__ inline int threshold_step(Ctrl& c, long long n_active, double e_abar) {
   c.probes += 1;
   c.total_probes += 1;
   long long s_abar = c.s - n_active;
   int dir;
   if ((double)s_abar > 0.5 * (double)c.s) {       // memory requirement
-    double e_abar = c.e - sum_ae;
     if (e_abar <= c.Pmax * c.e_b) {               // accuracy requirement
       c.search_ok = 1;
       return 0;

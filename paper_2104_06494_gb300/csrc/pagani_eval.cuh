@@ -468,14 +468,17 @@ __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double 
                                                 double vol, const double (&width)[N], double& V, double& E, int& K,
                                                 double* nk_out) {
   constexpr int NK = DEG == 9 ? 4 : 1;  // null rules in use
-  double b = 0.0, u[4] = {0.0, 0.0, 0.0, 0.0}, msum = 0.0;
+  double b = 0.0, u[4] = {0.0, 0.0, 0.0, 0.0}, msum = 0.0, vmag = 0.0;
 #pragma unroll
   for (int g = 0; g < kNumGen; ++g) {
     if (DEG == 7 && !(g == kGenCentre || g == kGenL2 || g == kGenLp || g == kGenL1L1 || g == kGenL0All)) continue;
     b = fma(R.w[g][0], S[g], b);
 #pragma unroll
     for (int k = 0; k < NK; ++k) u[k] = fma(R.w[g][1 + k], S[g], u[k]);
-    if (!UNIT) msum += fabs(S[g]);
+    if (!UNIT) {
+      msum += fabs(S[g]);
+      vmag = fma(fabs(R.w[g][0]), fabs(S[g]), vmag);
+    }
   }
   V = vol * b;
   // null values at the rounding level of their own sums count as zero: the
@@ -505,6 +508,9 @@ __device__ __forceinline__ void region_epilogue(const EvalRule& R, const double 
 #pragma unroll
     for (int k = NK; k < 4; ++k) nk_out[k] = nk_out[4 + k] = 0.0;
   E = DEG == 9 ? null_error(nu[0], nu[1], nu[2], nu[3]) : nu[0];
+  // no error below the rounding level of V itself
+  const double vround = kVRound * (vol * (UNIT ? R.vround_unit : vmag));
+  if (E < vround) E = vround;
   // split axis: the largest fourth difference above its noise floor (floored
   // ones carry a negative sign), near-ties to the lowest axis; with every
   // difference at the floor, the widest axis
@@ -690,7 +696,7 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
   const int64_t cap = A.pool.cap;
   const double* __restrict__ lower = A.pool.lower + (size_t)buf * N * cap;
   const uint8_t* __restrict__ level = A.pool.level + (size_t)buf * N * cap;
-  const double tau_rel = c.tau_rel;
+  const double tau_rel = c.tau_cls;  // Rel-Err-Classify tolerance of this iteration
   const int relerr = c.relerr_filter;
   const IntegrandParams prm = *A.prm;
   const T base = F::base(prm);

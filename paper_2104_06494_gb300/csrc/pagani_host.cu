@@ -80,12 +80,13 @@ __global__ void k_uniform_split(Pool P, int d, int log2d, int64_t s0) {
 
 // ------------------------------------------------- Threshold-Classify probe
 // Counts the candidate actives under threshold t (rel-err active and
-// E >= t) and sums their errors; the last block takes one step of Algorithm 3.
+// E >= t) and sums the errors of the other regions (the candidate finished
+// set); the last block takes one step of Algorithm 3.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   Ctrl& c = *A.ctrl;
   const int64_t s = c.s;
-  const double t = c.t, tau = c.tau_rel;
+  const double t = c.t, tau = c.tau_cls;
   const int relerr = c.relerr_filter;
   const double* __restrict__ V = A.pool.V;
   const double* __restrict__ E = A.pool.E;
@@ -93,10 +94,8 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   long long na = 0;
   for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < s; i += (int64_t)gridDim.x * THREADS) {
     const double e = E[i];
-    if (relerr_active(V[i], e, tau, relerr) && !(e < t)) {
-      ++na;
-      nadd(sa, e);
-    }
+    if (relerr_active(V[i], e, tau, relerr) && !(e < t)) ++na;
+    else nadd(sa, e);
   }
   __shared__ NSum shn[THREADS + 1];
   __shared__ long long shl[THREADS / 32];
@@ -155,7 +154,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   // each thread sums its ITEMS regions of a tile plainly (relative error at
   // most (ITEMS - 1) u) and adds that partial into Neumaier accumulators, so
   // the sums stay compensated across all partials at a third of the FP64 work
-  NSum acc3[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};  // V.A, E.A, finished volume
+  NSum acc3[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};  // finished V, E and volume
   NSum& va = acc3[0];
   NSum& ea = acc3[1];
   NSum& fv = acc3[2];
@@ -195,9 +194,9 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
         A.pool.act[i] = actv[r] ? 1 : 0;  // the split reads it back
         if (actv[r]) {
           ++cnt;
+        } else {
           tv += vv[r];
           te += ee[r];
-        } else {
           tf += pow2_neg(Lr[r]);
         }
       }
@@ -264,18 +263,23 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     c.estimate = c.v + c.vf;
     c.errorest = c.e + c.ef;
   } else {
-    const double vf_new = c.v - nval(tva) + c.vf;
-    const double ef_new = c.e - nval(tea) + c.ef;
+    // v - sum V.A and e - sum E.A of Algorithm 2, summed over the finished
+    // regions directly
+    const double vf_new = c.vf + nval(tva);
+    const double ef_new = c.ef + nval(tea);
     if (tr) {
       tr->vf = vf_new;
       tr->ef = ef_new;
     }
-    if (n_surv == 0 || ef_new > fmax(c.tau_rel * fabs(c.v + c.vf), c.tau_abs)) {
-      c.status = 3;  // tolerance out of reach
+    if (n_surv == 0) {
+      // nothing left to refine: v + v_f and e + e_f cannot change any more,
+      // so the loop ends as it would at it_max
+      c.status = 1;
       c.done = 1;
       c.estimate = c.v + c.vf;
       c.errorest = c.e + c.ef;
     } else {
+      c.tau_cls = survivor_tolerance(c.tau_rel, c.v + c.vf, ef_new, c.v - nval(tva));
       c.vf = vf_new;
       c.ef = ef_new;
       c.fin_volume_acc = ncomb(c.fin_volume_acc, tfv);
@@ -674,6 +678,8 @@ static EvalRule to_eval_rule(const RuleTable& t) {
   }
   for (int g = 0; g < kNumGen; ++g)
     for (int k = 0; k < 5; ++k) r.w[g][k] = t.w[g][k];
+  r.vround_unit = 0.0;
+  for (int g = 0; g < kNumGen; ++g) r.vround_unit = std::fma(std::fabs(t.w[g][0]), (double)t.count[g], r.vround_unit);
   return r;
 }
 
@@ -919,6 +925,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
   Ctrl h;
   std::memset(&h, 0, sizeof(h));
   h.tau_rel = epsrel;
+  h.tau_cls = epsrel;
   h.tau_abs = epsabs;
   h.max_regions = max_regions;
   h.it_max = o.it_max;
@@ -1081,12 +1088,12 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
 }
 
 // ------------------------------------------------------ allocation-free path
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is
-// being captured, applications whose allocator owns all device memory, or
-// latency-critical loops that must not allocate.  pagani_integrate_noalloc
-// serves them: it runs the same loop kernels on scratch memory carved from
-// this file-scope array instead of the library workspace.  Every GPU that
-// loads the library holds the array until the process exits.
+// Some callers cannot call cudaMalloc: applications whose own allocator owns
+// all device memory, or latency-critical service loops that must never
+// allocate.  pagani_integrate_noalloc serves them: it runs the same loop
+// kernels on scratch memory carved from this file-scope array instead of the
+// library workspace.  Every GPU that loads the library holds the array until
+// the process exits.
 constexpr size_t kNoallocBytes = (size_t)32 << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -1129,8 +1136,10 @@ static NoallocLayout noalloc_layout(int64_t cap, int n, int max_grid) {
 }
 
 // Largest region capacity (a multiple of 4096) whose layout fits the array.
+// A region takes 18n + 22 bytes of the layout plus its share of the tile
+// arrays, so kNoallocBytes / (18n + 22) bounds the capacity from above.
 static int64_t noalloc_capacity(int n, int max_grid) {
-  int64_t lo = 0, hi = (int64_t)(kNoallocBytes / (size_t)(18 * n + 26)) + 4096;
+  int64_t lo = 0, hi = (int64_t)(kNoallocBytes / (size_t)(18 * n + 22)) + 4096;
   while (hi - lo > 4096) {
     const int64_t mid = ((lo + hi) / 2 / 4096) * 4096;
     if (mid <= lo) break;
@@ -1221,6 +1230,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   Ctrl h;
   std::memset(&h, 0, sizeof(h));
   h.tau_rel = epsrel;
+  h.tau_cls = epsrel;
   h.tau_abs = epsabs;
   h.max_regions = max_regions;
   h.it_max = 100;
@@ -1231,10 +1241,16 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   h.status = -100;
   IntegrandParams prm = to_params(fam, n, params);
   const EvalRule rule = to_eval_rule(*rt);
+  // on an error, wait for the work already queued on st before returning:
+  // no kernel of a failed call may still write the shared array when the
+  // next call (perhaps on another stream) starts rewriting it
 #define PG_CK(x)                                                                          \
   do {                                                                                    \
     e = (x);                                                                              \
-    if (e != cudaSuccess) return out->status = fail(PAGANI_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e)); \
+    if (e != cudaSuccess) {                                                               \
+      (void)cudaStreamSynchronize(st);                                                    \
+      return out->status = fail(PAGANI_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e)); \
+    }                                                                                     \
   } while (0)
   PG_CK(cudaMemcpyAsync(a.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   PG_CK(cudaMemcpyAsync(base + L.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
@@ -1347,7 +1363,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_reduce(const BatchArgs 
       nadd(acc.e, e);
       acc.emin = fmin(acc.emin, e);
       acc.emax = fmax(acc.emax, e);
-      acc.n_rel += relerr_active(v, e, c.tau_rel, c.relerr_filter);
+      acc.n_rel += relerr_active(v, e, c.tau_cls, c.relerr_filter);
       if (!isfinite(v) || !isfinite(e)) acc.nonfinite = 1;
       int L = 0;
       for (int j = 0; j < I.n; ++j) L += G->level[((size_t)buf * I.n + j) * slots + base + i];
@@ -1387,10 +1403,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A
     long long na = 0;
     for (int64_t i = threadIdx.x; i < s_cur; i += kBatchThreads) {
       const double e = G->E[base + i];
-      if (relerr_active(G->V[base + i], e, c.tau_rel, c.relerr_filter) && !(e < t_cur)) {
-        ++na;
-        nadd(sa, e);
-      }
+      if (relerr_active(G->V[base + i], e, c.tau_cls, c.relerr_filter) && !(e < t_cur)) ++na;
+      else nadd(sa, e);
     }
     NSum tot1[1] = {sa};
     nsum_block_reduce_staged<kBatchThreads, 1>(tot1, shn);
@@ -1412,13 +1426,14 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A
   }
 }
 
-// v_f, e_f, the memory and reachability checks, then Filter + parent update
-// + Split inside the instance's slot (Algorithm 2), one block per instance.
+// v_f, e_f, the memory check, then Filter + parent update + Split inside the
+// instance's slot (Algorithm 2), one block per instance.
 __global__ void __launch_bounds__(kBatchThreads) k_batch_split(const BatchArgs A) {
   __shared__ NSum shn[2 * kBatchThreads + 2];
   __shared__ long long shl[kBatchThreads / 32];
   __shared__ int shr[kBatchThreads / 32];
   __shared__ int go_on;
+  __shared__ double tau_next;  // the next iteration's tau_cls; pass 2 still classifies with this one's
   for (int b = blockIdx.x; b < A.n_inst; b += gridDim.x) {
     BatchInst& I = A.inst[b];
     Ctrl& c = I.c;
@@ -1429,13 +1444,14 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_split(const BatchArgs A
     const int n = I.n;
     const int src = (c.it - 1) & 1, dst = src ^ 1;
     const int64_t s_cur = c.s;  // read once: thread 0 rewrites c.s at the end of this pass
-    // pass 1: survivors and the finished accumulation
+    // pass 1: survivors and the finished accumulation (sums of the finished)
     NSum va = {0.0, 0.0}, ea = {0.0, 0.0};
     long long cnt = 0;
     for (int64_t i = threadIdx.x; i < s_cur; i += kBatchThreads) {
       const double v = G->V[base + i], e = G->E[base + i];
       if (final_active(v, e, c)) {
         ++cnt;
+      } else {
         nadd(va, v);
         nadd(ea, e);
       }
@@ -1453,14 +1469,15 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_split(const BatchArgs A
         c.estimate = c.v + c.vf;
         c.errorest = c.e + c.ef;
       } else {
-        const double vf_new = c.v - nval(tva) + c.vf;
-        const double ef_new = c.e - nval(tea) + c.ef;
-        if (n_surv == 0 || ef_new > fmax(c.tau_rel * fabs(c.v + c.vf), c.tau_abs)) {
-          c.status = 3;
+        const double vf_new = c.vf + nval(tva);
+        const double ef_new = c.ef + nval(tea);
+        if (n_surv == 0) {  // nothing left to refine: ends as at it_max
+          c.status = 1;
           c.done = 1;
           c.estimate = c.v + c.vf;
           c.errorest = c.e + c.ef;
         } else {
+          tau_next = survivor_tolerance(c.tau_rel, c.v + c.vf, ef_new, c.v - nval(tva));
           c.vf = vf_new;
           c.ef = ef_new;
           go_on = 1;
@@ -1508,6 +1525,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_split(const BatchArgs A
       if (threadIdx.x == 0) {
         c.s = 2 * n_surv;
         c.it += 1;
+        c.tau_cls = tau_next;
         atomicOr(&A.flags[1], 1);
       }
     }
@@ -1673,6 +1691,7 @@ static int integrate_batch_locked(int64_t count, const pagani_batch_item* items,
       for (int j = 0; j < g.n; ++j) s0 *= d0;
       Ctrl& c = I.c;
       c.tau_rel = it.epsrel;
+      c.tau_cls = it.epsrel;
       c.tau_abs = it.epsabs;
       c.max_regions = slot_cap;
       c.it_max = o.it_max;

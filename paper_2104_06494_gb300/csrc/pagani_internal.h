@@ -107,6 +107,9 @@ struct Ctrl {
   int32_t nonfinite;         // a region produced NaN/Inf
   double v, e, vf, ef;       // Algorithm 2 scalars
   double v_tot_prev;
+  double tau_cls;            // Rel-Err-Classify tolerance: the survivors' share
+                             // of what tau_rel |v_tot| still allows (tau_rel
+                             // until a threshold commit takes more)
   int64_t n_rel;             // rel-err actives this iteration
   double emin, emax;
   int32_t trigger;
@@ -150,12 +153,12 @@ struct EvalPartial {
 };
 
 struct CountPartial {
-  NSum va, ea, finvol;
+  NSum va, ea, finvol;  // V, E and volume summed over the finished regions
 };
 
 struct ProbePartial {
-  NSum ea;
-  long long n_active;
+  NSum ea;              // E summed over the candidate finished regions
+  long long n_active;   // candidate actives
   long long pad;
 };
 
@@ -168,7 +171,11 @@ struct EvalRule {
   double cnt[kNumGen];  // orbit sizes
   double umax[4];       // max_g |u_kg| (upper bound of the floor's weights)
   double floor_unit[4]; // sum_g |u_kg| cnt_g (the unit-bounded family's floor scale)
+  double vround_unit;   // sum_g |w_g| cnt_g (the unit-bounded family's scale of V)
 };
+
+// No region error below the rounding level of V itself: 16 u vol sum_g |w_g| M_g.
+constexpr double kVRound = 16.0 * 0x1p-53;
 
 // Region pool: SoA, two buffers (ping-pong).  lower[b][j][cap] doubles,
 // level[b][j][cap] bytes with width = 2^-level.

@@ -190,15 +190,18 @@ def region_points_work(family: int, n: int, q: float = 11.0) -> Counter:
     return c
 
 
-def region_epilogue_work() -> Counter:
+def region_epilogue_work(unit: bool = False) -> Counter:
     """Weighting (9 generators x (basic + 4 null rules) FMA), the magnitude
     sum bounding the noise floors, the volume products, the floor tests (the
     exact floor only where the bound does not clear N_k), the error formula
-    and the split axis."""
+    (three ratios, division each), the rounding floor of V (a 9-term FMA sum
+    of |w_g| |S_g| for the positive families, a constant for the unit-bounded
+    one, then two products) and the split axis."""
     c = Counter()
-    c["flops"] += 2 * 45 + 9 + 1 + 4 + 8 + 1
-    c["inst"] += 45 + 9 + 1 + 4 + 8 + 1
-    c["div"] += 2
+    floor_fma = 0 if unit else 9
+    c["flops"] += 2 * 45 + 9 + 1 + 4 + 8 + 1 + 2 * floor_fma + 2
+    c["inst"] += 45 + 9 + 1 + 4 + 8 + 1 + floor_fma + 2
+    c["div"] += 3
     return c
 
 
@@ -259,7 +262,7 @@ def pair_work(family: int, n: int, two_level: bool, cached: bool = True, q: floa
         c.update(pair_table_work(family, n))
     for _ in range(2):
         c.update(region_points_work(family, n, q))
-        c.update(region_epilogue_work())
+        c.update(region_epilogue_work(unit=family == 2))
         c["flops"] += 9             # two compensated adds and the rel-err test
         c["inst"] += 9
     if two_level:

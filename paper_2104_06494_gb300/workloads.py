@@ -101,6 +101,12 @@ def config_workloads() -> dict[str, Workload]:
         "oscillatory_d6": Workload("oscillatory_d6", OSCILLATORY, 6, 1e-8,
                                    draw_params(OSCILLATORY, 6, BASE_SEED + 3), 40_000_000, relerr_filter=0,
                                    notes="sign-changing integrand: rel-err filtering off (Sec. 3.5.1)"),
+        # the same integral at 1e-10: at 1e-8 it converges with at most 6.6e4
+        # active regions, at 1e-10 its active set reaches 4.2e6, the
+        # 1e6..1e7 range the 6-D oscillatory workload is specified for
+        "oscillatory_d6_1e-10": Workload("oscillatory_d6_1e-10", OSCILLATORY, 6, 1e-10,
+                                         draw_params(OSCILLATORY, 6, BASE_SEED + 3), 40_000_000, relerr_filter=0,
+                                         notes="oscillatory_d6 at a tolerance whose active set reaches 1e6..1e7"),
         "corner_peak_d8": Workload("corner_peak_d8", CORNER_PEAK, 8, 1e-6,
                                    draw_params(CORNER_PEAK, 8, BASE_SEED + 4), 400_000_000),
         "c0_d8": Workload("c0_d8", C0, 8, 1e-6, draw_params(C0, 8, BASE_SEED + 5), 400_000_000),

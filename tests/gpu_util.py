@@ -68,15 +68,17 @@ def sum_tolerance(n, scale, k_rel=0.0, abs_scale=0.0, k_abs=0.0):
 def null_error(n1, n2, n3, n4):
     """Region error from four null values, the reading of Sec. 3.2 used by
     both implementations (restated here to check the kernel's epilogue
-    against its own N_k)."""
+    against its own N_k); the rounding floor of V is applied on top."""
     def ratio(x, y):
         return x / y if y > 0 else (math.inf if x > 0 else 0.0)
-    r = max(ratio(n1, n2), ratio(n2, n3))
+    r = max(ratio(n1, n2), ratio(n2, n3), ratio(n3, n4))
     if r >= 1:
-        return 10 * max(n1, n2, n3, n4)
-    if r >= 0.5:
-        return 10 * r * n1
-    return 40 * r ** 3 * n1
+        return 10 * max(n1, n2, n3)
+    return 10 * r * max(n1, r * n2)
+
+
+# no region error below 16 u times the rule's absolute sum of V
+V_ROUND = 16 * 2.0 ** -53
 
 
 def sibling_regions(n, m, seed, max_level=10):
@@ -106,18 +108,21 @@ def close(a, b, rel=1e-12, floor=1e-300):
     return abs(a - b) <= rel * max(abs(a), abs(b)) + floor
 
 
-def compare_runs(g, o, rel=1e-12):
+def compare_runs(g, o, rel=1e-12, value_scale=0.0):
     """Equal region sets (statuses, iterations, per-iteration counts and
     decisions), integral estimates within 1e-12 relative.  Error estimates are
     sums of region errors computed from null-rule values, differences of
     nearly equal sums known only to their rounding level; they are compared
     to 1e-6 relative, or 1e-12 of the integral's magnitude where they are
-    themselves at that noise level."""
+    themselves at that noise level.  value_scale: the integral of |f| where
+    it exceeds |I| (a sign-changing integrand cancels: its sums carry
+    rounding errors relative to the integral of |f|, 1 for |f| <= 1 on the
+    unit cube, not to the small integral itself)."""
     assert g.status == o.status, (g.status, o.status)
     assert g.iterations == o.iterations
     assert g.n_regions == o.n_regions
     assert g.n_active_last == o.n_active_last
-    scale = max(abs(o.estimate), float(np.max(np.abs(o.trace["v"]) + np.abs(o.trace["vf"]))))
+    scale = max(abs(o.estimate), float(np.max(np.abs(o.trace["v"]) + np.abs(o.trace["vf"]))), value_scale)
     assert abs(g.estimate - o.estimate) <= rel * scale + 1e-300, (g.estimate, o.estimate)
     efloor = 1e-12 * scale
     assert close(g.errorest, o.errorest, rel=1e-6, floor=efloor), (g.errorest, o.errorest)

@@ -56,7 +56,7 @@ def kappa(family, n, p):
 def test_leaf_set_and_gradient_match_oracle(pg, family, n, tau):
     p = draw_params(family, n, 300 + family + n, RANGES[family])
     r = pg.pagani_integrate_ex(n, family, p, tau, max_regions=4_000_000, keep_leaves=1)
-    o = oracle.integrate(family, n, p, tau, max_regions=4_000_000, want_leaves=True)
+    o = oracle.integrate(family, n, p, tau, max_regions=4_000_000, want_leaves=True, parallel=True)
     assert r.status == o.status and r.n_regions == o.n_regions
     lo, wd, lower, level = gpu_leaves_rows(pg, n)
     assert r.n_leaves == len(lo) == len(o.leaves[0])

@@ -27,18 +27,24 @@ CASES = [
     (0, 2, 1e-6, 1), (0, 3, 1e-3, 1), (0, 4, 1e-6, 1),
     (1, 2, 1e-7, 1), (1, 3, 1e-5, 1), (1, 5, 1e-4, 1),
     (2, 2, 1e-8, 0), (2, 3, 1e-7, 0), (2, 6, 1e-6, 0),
-    (3, 3, 1e-7, 1), (3, 5, 1e-6, 1), (3, 8, 1e-4, 1),
+    (3, 3, 1e-7, 1), (3, 5, 1e-6, 1), (3, 8, 1e-3, 1),
     (4, 2, 1e-5, 1), (4, 3, 1e-4, 1), (4, 8, 1e-3, 1),
-    (5, 4, 1e-3, 1), (6, 3, 1e-13, 1), (6, 5, 1e-10, 1), (6, 8, 1e-7, 1),
+    # the box power at tolerances down to 1e-11: below about 5e-13 (n = 3) the
+    # tolerance sits under the null values' own noise floor, 64 N(n) u of
+    # their sums, and rounding decides the classification on either side
+    (5, 4, 1e-3, 1), (6, 3, 1e-11, 1), (6, 5, 1e-10, 1), (6, 8, 1e-7, 1),
 ]
 
 
 @pytest.mark.parametrize("family,n,tau,relerr", CASES)
 def test_loop_matches_oracle(pg, family, n, tau, relerr):
+    # C0 in 8-D runs out of a 10^6 pool after 15 iterations (1.5e6 regions
+    # evaluated): memory-exhaustion parity at a size the oracle takes seconds on
+    pool = 1_000_000 if (family, n) == (4, 8) else 4_000_000
     params = draw_params(family, n, 700 + 13 * family + n)
-    o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, relerr_filter=relerr)
-    g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=4_000_000, relerr_filter=relerr, trace=True)
-    compare_runs(g, o)
+    o = oracle.integrate(family, n, params, tau, max_regions=pool, relerr_filter=relerr, parallel=True)
+    g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=pool, relerr_filter=relerr, trace=True)
+    compare_runs(g, o, value_scale=1.0 if family == 2 else 0.0)
 
 
 def _box(family, n, seed, params=None):
@@ -67,7 +73,7 @@ def test_general_bounds_match_oracle(pg, family, n, tau):
     params = draw_params(family, n, 1700 + 10 * family + n)
     lo, hi = _box(family, n, 41 + 10 * family + n, params)
     relerr = 0 if family == 2 else 1
-    o = oracle.integrate(family, n, params, tau, max_regions=2_000_000, relerr_filter=relerr, bounds=(lo, hi))
+    o = oracle.integrate(family, n, params, tau, max_regions=2_000_000, relerr_filter=relerr, bounds=(lo, hi), parallel=True)
     g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=2_000_000, relerr_filter=relerr,
                                bounds=(lo, hi), trace=True)
     compare_runs(g, o)
@@ -128,7 +134,7 @@ def test_gm7_loop_matches_oracle(pg, family, n, tau):
     error estimate where the oracle's is (all but the discontinuous case)."""
     params = draw_params(family, n, 800 + 13 * family + n)
     relerr = 0 if family == 2 else 1
-    o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, relerr_filter=relerr, degree=7)
+    o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, relerr_filter=relerr, degree=7, parallel=True)
     g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=4_000_000, relerr_filter=relerr, trace=True,
                                rule_degree=7)
     compare_runs(g, o)
@@ -140,14 +146,16 @@ def test_gm7_loop_matches_oracle(pg, family, n, tau):
 def test_gm7_uses_fewer_points_per_region(pg):
     """Same integral, both rules: the degree-7 run evaluates
     2^n + 2n^2 + 2n + 1 points per region (401 at n = 8, against 1105) and
-    both estimates hold the closed form within their error estimates."""
+    both estimates hold the closed form within their error estimates (the
+    degree-7 run, whose error is the plain |R7 - R5|, runs out of the 2^24
+    pool before its estimate reaches 1e-3)."""
     n = 8
     params = draw_params(1, n, 8080)
     ex = cf.closed_form(1, n, params)
     r9 = pg.pagani_integrate_ex(n, 1, params, 1e-3, max_regions=1 << 24)
     r7 = pg.pagani_integrate_ex(n, 1, params, 1e-3, max_regions=1 << 24, rule_degree=7)
     for r in (r9, r7):
-        assert r.status in (0, 3) and abs(r.estimate - ex) <= r.errorest
+        assert r.status in (0, 2) and abs(r.estimate - ex) <= r.errorest
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
@@ -159,7 +167,7 @@ def test_filter_modes_match_oracle(pg, mode):
     iteration 10, on both sides alike."""
     from paper_2104_06494_gb300.workloads import paper_integrands
     w = paper_integrands()["f4_d5"]
-    o = oracle.integrate(w.family, w.dim, w.params, 1e-4, max_regions=1_000_000, heuristic_filter=mode)
+    o = oracle.integrate(w.family, w.dim, w.params, 1e-4, max_regions=1_000_000, heuristic_filter=mode, parallel=True)
     g = pg.pagani_integrate_ex(w.dim, w.family, w.params, 1e-4, max_regions=1_000_000, heuristic_filter=mode,
                                trace=True)
     compare_runs(g, o)
@@ -182,28 +190,26 @@ def test_filtering_ablation_f4_d8(pg):
 
 @pytest.mark.parametrize("n,tau", [(2, 1e-4), (3, 1e-3)])
 def test_discontinuous_without_heuristic_filter(pg, n, tau):
-    """The discontinuous family converges only with the heuristic filter off
-    (with it on, the finished error of the boxes cut by the jump exceeds the
-    tolerance and the loop stops with status 3, as the case above checks):
-    millions of regions, the pool grown and compacted over 14 to 26
-    iterations.  The null-rule estimate is not a bound across the jump: at
-    d = 3 it reports 8.7e-4 where the true error is 4.9e-3 (on both sides),
-    so containment is asserted for the d = 2 case only."""
+    """The discontinuous family with the heuristic filter off: millions of
+    regions, the pool grown and compacted over 20 or more iterations, equal
+    on both sides.  At d = 2 the loop converges with the closed form inside
+    the estimate; at d = 3 the boxes cut by the jump keep their large
+    errors until the 4e6-region pool is exhausted (status 2), and the
+    estimate still covers the true error."""
     family = 5
     params = draw_params(family, n, 700 + 13 * family + n)
-    o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, heuristic_filter=0)
+    o = oracle.integrate(family, n, params, tau, max_regions=4_000_000, heuristic_filter=0, parallel=True)
     g = pg.pagani_integrate_ex(n, family, params, tau, max_regions=4_000_000, heuristic_filter=0, trace=True)
-    assert o.status == 0
+    assert o.status == (0 if n == 2 else 2)
     compare_runs(g, o)
-    if n == 2:
-        ex = cf.closed_form(family, n, params)
-        assert abs(g.estimate - ex) <= g.errorest
+    ex = cf.closed_form(family, n, params)
+    assert abs(g.estimate - ex) <= g.errorest
 
 
 def test_config_product_peak_d3_full_size(pg):
     """The d=3 product-peak workload at its full size (epsrel 1e-3, 1e5 regions)."""
     w = config_workloads()["product_peak_d3"]
-    o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions)
+    o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions, parallel=True)
     g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
     compare_runs(g, o)
     ex = cf.closed_form(w.family, w.dim, w.params)
@@ -213,21 +219,24 @@ def test_config_product_peak_d3_full_size(pg):
 @pytest.mark.parametrize("n", [2, 5, 8])
 def test_zero_and_constant_integrands(pg, n):
     """Degenerate integrands: f = 0 converges in one pass with estimate and
-    error exactly 0; f = 1 returns the volume with zero error, to the
-    rounding of the double weights' sum (the oracle, summing exact-rounded
-    weights per orbit, gets 1 exactly; the kernel's order is 1 ulp off at
-    n = 8)."""
+    error exactly 0; f = 1 returns the volume, to the rounding of the double
+    weights' sum (the oracle, summing exact-rounded weights per orbit, gets 1
+    exactly; the kernel's order is 1 ulp off at n = 8), with an error
+    estimate at the rounding level of the rule sums, 16 u sum_g |w_g| cnt_g,
+    as the oracle's."""
     g = pg.pagani_integrate_ex(n, 5, [1.0] * n + [0.0] * n, 1e-6)
     assert (g.status, g.iterations, g.estimate, g.errorest) == (0, 1, 0.0, 0.0)
     g = pg.pagani_integrate_ex(n, 6, [0.0], 1e-12)
-    assert (g.status, g.iterations, g.errorest) == (0, 1, 0.0)
+    o = oracle.integrate(6, n, [0.0], 1e-12, parallel=True)
+    assert (g.status, g.iterations) == (0, 1)
     assert abs(g.estimate - 1.0) <= 4 * 2.0 ** -53
+    assert 0.0 < g.errorest and abs(g.errorest - o.errorest) <= 1e-12 * o.errorest
 
 
 @pytest.mark.parametrize("init_div", [2, 8])
 def test_non_default_uniform_split_matches_oracle(pg, init_div):
     params = [10.0, 12.0, 14.0, 0.3, 0.5, 0.7]
-    o = oracle.integrate(1, 3, params, 1e-6, init_div=init_div)
+    o = oracle.integrate(1, 3, params, 1e-6, init_div=init_div, parallel=True)
     g = pg.pagani_integrate_ex(3, 1, params, 1e-6, init_div=init_div, trace=True)
     compare_runs(g, o)
 
@@ -250,7 +259,7 @@ def test_bitwise_repeatable(pg):
 
 def test_memory_exhausted_matches_oracle(pg):
     params = draw_params(1, 3, 3)
-    o = oracle.integrate(1, 3, params, 1e-12, max_regions=6000, heuristic_filter=0)
+    o = oracle.integrate(1, 3, params, 1e-12, max_regions=6000, heuristic_filter=0, parallel=True)
     g = pg.pagani_integrate_ex(3, 1, params, 1e-12, max_regions=6000, heuristic_filter=0, trace=True)
     assert o.status == 2
     compare_runs(g, o)
@@ -275,53 +284,65 @@ def test_configs_within_errorest_of_closed_form(pg, name):
     g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions,
                                relerr_filter=w.relerr_filter)
     ex = cf.closed_form(w.family, w.dim, w.params)
-    assert g.status in (0, 3)
+    assert g.status == 0
     assert abs(g.estimate - ex) <= g.errorest
 
 
 def test_bench_workload_gaussian_d5_full_size(pg):
-    """The bench's 5-D Gaussian at its full size (epsrel 1e-7, ~2.1e6
-    regions over 11 iterations), in the launch configuration bench.py times
+    """The bench's 5-D Gaussian at its full size (epsrel 1e-7, ~2.3e6
+    regions over 18 iterations), in the launch configuration bench.py times
     (graph loop, library workspace): the same region-set evolution as the
-    oracle and the estimate within 1e-12."""
+    oracle, the estimate within 1e-12, converged with the closed form
+    inside the estimate."""
     w = config_workloads()["gaussian_d5"]
-    o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions)
+    o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions, parallel=True)
     g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
     compare_runs(g, o)
     ex = cf.closed_form(w.family, w.dim, w.params)
     assert abs(g.estimate - ex) <= g.errorest
 
 
-def test_config_corner_peak_d8_full_size(pg):
-    """The 8-D corner peak at its full size (epsrel 1e-6): same region-set
-    evolution as the oracle (about 1.5e5 regions of 1105 points)."""
+def test_config_corner_peak_d8_loop_parity(pg):
+    """The 8-D corner peak at epsrel 1e-3 (30 iterations, 6.7e5 regions of
+    1105 points, threshold searches on the way): the same region-set
+    evolution as the oracle.  At its full tolerance, 1e-6, the run takes
+    1.7e8 region evaluations, beyond the oracle; it is checked by its
+    properties below."""
     w = config_workloads()["corner_peak_d8"]
-    o = oracle.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, w.max_regions)
-    g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
+    o = oracle.integrate(w.family, w.dim, w.params, 1e-3, w.epsabs, w.max_regions, parallel=True)
+    g = pg.pagani_integrate_ex(w.dim, w.family, w.params, 1e-3, w.epsabs, w.max_regions, trace=True)
     compare_runs(g, o)
 
 
-def test_config_c0_d8_full_size_properties(pg):
-    """The 8-D C0 workload at full size (epsrel 1e-6, pool capped at 4e8
-    regions: ~4.6e8 regions over 22 iterations, 2.2e8 in the last) is beyond
-    the oracle; properties that hold at any size: the estimate within its
-    error of the closed form, exact bookkeeping of the dyadic volume, and
-    s_{it+1} = 2 (survivors of it)."""
-    w = config_workloads()["c0_d8"]
+@pytest.mark.parametrize("name", ["corner_peak_d8", "c0_d8"])
+def test_config_d8_full_size_properties(pg, name):
+    """The 8-D corner peak and C0 workloads at full size (epsrel 1e-6, pool
+    capped at 4e8 regions), beyond the oracle; properties that hold at any
+    size: the estimate within its error of the closed form (and within
+    epsrel when converged), exact bookkeeping of the dyadic volume,
+    s_{it+1} = 2 (survivors of it), and the finished error never above the
+    tolerance."""
+    w = config_workloads()[name]
     g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
     ex = cf.closed_form(w.family, w.dim, w.params)
-    assert g.status in (0, 2, 3)
+    assert g.status in ((0,) if name == "corner_peak_d8" else (0, 2))
     assert abs(g.estimate - ex) <= g.errorest
+    if g.status == 0:
+        assert abs(g.estimate - ex) <= w.epsrel * abs(ex)
     assert abs(g.finished_volume + g.active_volume - 1.0) <= 1e-13
     tr = g.trace
     for a, b in zip(tr[:-1], tr[1:]):
         assert b["s"] == 2 * a["n_survivors"]
     assert g.n_regions == int(tr["s"].sum())
+    vf_old = 0.0
+    for t in tr:
+        assert t["ef"] <= w.epsrel * abs(t["v"] + vf_old) * (1 + 1e-3)
+        vf_old = t["vf"]
 
 
 def test_volume_bookkeeping_matches_oracle(pg):
     params = draw_params(1, 3, 61)
-    o = oracle.integrate(1, 3, params, 1e-7, max_regions=2_000_000, want_regions=True)
+    o = oracle.integrate(1, 3, params, 1e-7, max_regions=2_000_000, want_regions=True, parallel=True)
     g = pg.pagani_integrate_ex(3, 1, params, 1e-7, max_regions=2_000_000)
     act = float(np.sum(np.prod(o.final_width, axis=1)))
     assert abs(g.finished_volume - o.finished_volume) <= 1e-15

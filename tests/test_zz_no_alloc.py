@@ -1,6 +1,6 @@
 """The allocation-free entry point, pagani_integrate_noalloc, for callers that
-cannot allocate device memory (stream capture, a foreign allocator owning the
-device, loops that must not allocate).  It must give the same results as the
+cannot allocate device memory (an application whose own allocator owns the
+device, service loops that must never allocate).  It must give the same results as the
 workspace path, pagani_integrate_ex, within the loop-parity tolerance of the
 other GPU tests, on two calls in a row that share its static scratch array,
 and it must refuse problems larger than that array with a clear error.
