@@ -247,9 +247,15 @@ def hbm_peak_gbs():
 def management_bandwidth(part, hbm_peak):
     """Achieved HBM bandwidth of the region-management kernels over one
     host-driven integration: algorithmic bytes from the per-iteration trace
-    (s regions, n_surv survivors, n axes) over the phase's CUDA-event time.
-      count: V and E read, the classification byte written, the n level
-             bytes of every finished region read: 17 s + n (s - n_surv)
+    (s regions, r rel-err actives, n_surv survivors, n axes, whether a
+    threshold search succeeded) over the phase's CUDA-event time.
+      probe: per pass, every region's classification byte and error, 9 s;
+             a pass takes three steps of the search, so an iteration with p
+             probes makes ceil(p / 3) passes
+      count: the classification bytes, s; V and the n level bytes of every
+             finished region, (8 + n)(s - n_surv); E of the finished, or
+             after a search E of every region and the byte of each region
+             the threshold finished, 8 (s - n_surv) or 8 s + (r - n_surv)
       split: the classification byte read; per survivor K and V read, its
              bounds and levels (9n) read, V_p and both halves (2 * 9n)
              written: s + n_surv (17 + 27 n)"""
@@ -257,14 +263,21 @@ def management_bandwidth(part, hbm_peak):
     tr, n = part["trace"], part["dim"]
     s = tr["s"].astype(float)
     surv = tr["n_survivors"].astype(float)
-    count_b = float(np.sum(17 * s + n * (s - surv)))
+    rel = tr["n_relerr_active"].astype(float)
+    ok = tr["search_ok"].astype(bool)
+    passes = np.ceil(tr["probes"].astype(float) / 3.0)
+    probe_b = float(np.sum(passes * 9 * s))
+    fin = s - surv
+    count_b = float(np.sum(s + (8 + n) * fin + np.where(ok, 8 * s + (rel - surv), 8 * fin)))
     # the last iteration is split only when the loop goes on (not here: it ended)
     split_b = float(np.sum((s + surv * (17 + 27 * n))[:-1]))
     out = {}
-    for key, b, ms in (("sums_count", count_b, part["phase_ms"][2]), ("filter_split", split_b, part["phase_ms"][3])):
+    for key, b, ms in (("threshold_probe", probe_b, part["phase_ms"][1]), ("sums_count", count_b, part["phase_ms"][2]),
+                       ("filter_split", split_b, part["phase_ms"][3])):
         gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else None
         out[f"{key}_gbs"] = gbs
         out[f"{key}_hbm_frac"] = gbs / hbm_peak if gbs is not None and hbm_peak else None
+    out["probe_passes"] = int(np.sum(passes))
     out["hbm_peak_gbs"] = hbm_peak
     return out
 

@@ -380,6 +380,14 @@ __device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long 
   return 1;
 }
 
+// The threshold after t in the search of Algorithm 3: too few regions
+// finished (dir > 0) moves it halfway to max E, too much error (dir < 0)
+// halfway to min E.  The probe kernel builds its tree of coming thresholds
+// with this same function, so they are the bits threshold_step arrives at.
+__host__ __device__ __forceinline__ double search_next(double t, int dir, double emin, double emax) {
+  return dir > 0 ? t + (emax - t) / 2.0 : t - (t - emin) / 2.0;
+}
+
 // One step of Algorithm 3 after a probe with threshold c.t counted
 // n_active candidate actives; e_abar is the error of the candidate finished
 // regions (summed directly, not as e_it - sum A.E).  Returns 1 if another
@@ -404,8 +412,7 @@ __device__ inline int threshold_step(Ctrl& c, long long n_active, double e_abar)
   }
   c.last_dir = dir;
   if (c.dir_changes >= 10 || c.probes >= 64) return 0;  // unsuccessful filtering
-  if (dir > 0) c.t = c.t + (c.emax - c.t) / 2.0;
-  else c.t = c.t - (c.t - c.emin) / 2.0;
+  c.t = search_next(c.t, dir, c.emin, c.emax);
   return 1;
 }
 

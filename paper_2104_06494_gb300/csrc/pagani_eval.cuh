@@ -665,6 +665,8 @@ __device__ __forceinline__ void coop_pairs(const EvalRule& R, const LoopArgs& A,
       *reinterpret_cast<double2*>(A.pool.V + 2 * p) = make_double2(VL, VR);
       *reinterpret_cast<double2*>(A.pool.E + 2 * p) = make_double2(EL, ER);
       *reinterpret_cast<uchar2*>(A.pool.K + 2 * p) = make_uchar2((unsigned char)K, (unsigned char)KR);
+      const bool aL = relerr_active(VL, EL, tau_rel, relerr), aR = relerr_active(VR, ER, tau_rel, relerr);
+      *reinterpret_cast<uchar2*>(A.pool.act + 2 * p) = make_uchar2(aL, aR);
       nadd(sv, VL);
       nadd(sv, VR);
       nadd(se, EL);
@@ -673,7 +675,7 @@ __device__ __forceinline__ void coop_pairs(const EvalRule& R, const LoopArgs& A,
       nadd(svol, pow2_neg(lvR));
       emin = fmin(emin, fmin(EL, ER));
       emax = fmax(emax, fmax(EL, ER));
-      nrel += relerr_active(VL, EL, tau_rel, relerr) + relerr_active(VR, ER, tau_rel, relerr);
+      nrel += aL + aR;
       if (!isfinite(VL) || !isfinite(VR) || !isfinite(EL) || !isfinite(ER)) nonfinite = 1;
     }
     __syncwarp();  // the table is rewritten for the next pair
@@ -754,12 +756,14 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
         A.pool.V[i] = V;
         A.pool.E[i] = Em;
         A.pool.K[i] = (unsigned char)K;
+        const bool a = relerr_active(V, Em, tau_rel, relerr);
+        A.pool.act[i] = a;
         nadd(sv, V);
         nadd(se, Em);
         nadd(svol, pow2_neg(lvsum));
         emin = fmin(emin, Em);
         emax = fmax(emax, Em);
-        nrel += relerr_active(V, Em, tau_rel, relerr);
+        nrel += a;
         if (!isfinite(V) || !isfinite(Em)) nonfinite = 1;
       }
     }
@@ -808,6 +812,9 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     *reinterpret_cast<double2*>(A.pool.V + iL) = make_double2(VL, VR);
     *reinterpret_cast<double2*>(A.pool.E + iL) = make_double2(EL, ER);
     *reinterpret_cast<uchar2*>(A.pool.K + iL) = make_uchar2((unsigned char)KL, (unsigned char)KR);
+    // Rel-Err-Classify, kept per region for the probe and count kernels
+    const bool aL = relerr_active(VL, EL, tau_rel, relerr), aR = relerr_active(VR, ER, tau_rel, relerr);
+    *reinterpret_cast<uchar2*>(A.pool.act + iL) = make_uchar2(aL, aR);
 
     nadd(sv, VL);
     nadd(sv, VR);
@@ -817,7 +824,7 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     nadd(svol, pow2_neg(lvR));
     emin = fmin(emin, fmin(EL, ER));
     emax = fmax(emax, fmax(EL, ER));
-    nrel += relerr_active(VL, EL, tau_rel, relerr) + relerr_active(VR, ER, tau_rel, relerr);
+    nrel += aL + aR;
     if (!isfinite(VL) || !isfinite(VR) || !isfinite(EL) || !isfinite(ER)) nonfinite = 1;
   }
 

@@ -79,63 +79,188 @@ __global__ void k_uniform_split(Pool P, int d, int log2d, int64_t s0) {
 }
 
 // ------------------------------------------------- Threshold-Classify probe
-// Counts the candidate actives under threshold t (rel-err active and
-// E >= t) and sums the errors of the other regions (the candidate finished
-// set); the last block takes one step of Algorithm 3.
+// Bit pattern of a non-negative double (errors and thresholds); with the
+// sign bit cleared, these order like the numbers, so E >= t is an integer
+// comparison and costs no FP64 issue slot.
+__device__ __forceinline__ unsigned long long ebits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+
+// Counts of `cnt` (kProbeBuckets per thread) reduced over the block; valid
+// on thread 0.  sh holds kProbeBuckets * THREADS / 32 words.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
+__device__ __forceinline__ void bucket_counts_reduce(long long (&cnt)[kProbeBuckets], long long* sh) {
+  constexpr int NW = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int b = 0; b < kProbeBuckets; ++b) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cnt[b] += __shfl_down_sync(0xffffffffu, cnt[b], off);
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int b = 0; b < kProbeBuckets; ++b) sh[b * NW + warp] = cnt[b];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int b = 0; b < kProbeBuckets; ++b) {
+      long long t = 0;
+      for (int w = 0; w < NW; ++w) t += sh[b * NW + w];
+      cnt[b] = t;
+    }
+}
+
+// Threshold-Classify (Algorithm 3), kProbeDepth steps of the search per
+// pass.  From the current threshold t every step moves halfway to max E or
+// to min E, so the thresholds of the next kProbeDepth steps form a binary
+// tree (node k's children 2k+1, lower, and 2k+2, upper).  One pass places
+// every rel-err active region in the bucket between the tree's sorted
+// thresholds its error falls into, counting the regions and summing their
+// errors per bucket, and sums the errors of the rel-err finished regions
+// (Evaluate's classification byte).  For each node that gives the
+// candidate actives (E >= t) and the candidate finished error e_abar, so
+// the last block takes the steps of Algorithm 3 along the path the search
+// follows through the tree, with the same threshold_step a probe per step
+// would run: same thresholds, probe count, P_max and outcome.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 2) k_probe(const LoopArgs A) {
   Ctrl& c = *A.ctrl;
   const int64_t s = c.s;
-  const double t = c.t, tau = c.tau_cls;
-  const int relerr = c.relerr_filter;
-  const double* __restrict__ V = A.pool.V;
+  double node[kProbeNodes];
+  node[0] = c.t;
+#pragma unroll
+  for (int k = 0; k < kProbeNodes / 2; ++k) {
+    node[2 * k + 1] = search_next(node[k], -1, c.emin, c.emax);
+    node[2 * k + 2] = search_next(node[k], +1, c.emin, c.emax);
+  }
+  unsigned long long T[kProbeNodes];  // the thresholds, ascending
+#pragma unroll
+  for (int k = 0; k < kProbeNodes; ++k) T[k] = ebits(node[k]);
+  for (int a = 1; a < kProbeNodes; ++a)
+    for (int b = a; b > 0 && T[b - 1] > T[b]; --b) {
+      const unsigned long long x = T[b];
+      T[b] = T[b - 1];
+      T[b - 1] = x;
+    }
+  // per-thread bucket sums: plain (a thread's relative error stays below
+  // its element count times u), combined compensated across threads
+  double bsum[kProbeBuckets + 1];
+  long long bcnt[kProbeBuckets];
+#pragma unroll
+  for (int b = 0; b < kProbeBuckets; ++b) {
+    bsum[b] = 0.0;
+    bcnt[b] = 0;
+  }
+  bsum[kProbeBuckets] = 0.0;
+  const uint8_t* __restrict__ act = A.pool.act;
   const double* __restrict__ E = A.pool.E;
-  NSum sa = {0.0, 0.0};
-  long long na = 0;
   for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < s; i += (int64_t)gridDim.x * THREADS) {
     const double e = E[i];
-    if (relerr_active(V[i], e, tau, relerr) && !(e < t)) ++na;
-    else nadd(sa, e);
+    if (!act[i]) {
+      bsum[kProbeBuckets] += e;
+      continue;
+    }
+    const unsigned long long eb = ebits(e);
+    int k = 0;
+#pragma unroll
+    for (int j = 0; j < kProbeNodes; ++j) k += eb >= T[j];
+    bsum[k] += e;
+    bcnt[k] += 1;
   }
-  __shared__ NSum shn[THREADS + 1];
-  __shared__ long long shl[THREADS / 32];
-  // blocks without regions hold exact zeros and skip the FP64 shuffles; the
-  // last block reads only the partials that can be non-zero
+  __shared__ NSum shn[(kProbeBuckets + 1) * THREADS + kProbeBuckets + 1];
+  __shared__ long long shl[kProbeBuckets * (THREADS / 32)];
+  // blocks without regions hold exact zeros and skip the FP64 reductions;
+  // the last block reads only the partials that can be non-zero
   const int64_t nblk = (s + THREADS - 1) / THREADS;
   const int64_t nparts = nblk < (int64_t)gridDim.x ? nblk : (int64_t)gridDim.x;
   if ((int64_t)blockIdx.x < nparts) {
-    NSum bs[1] = {sa};
-    nsum_block_reduce_staged<THREADS, 1>(bs, shn);
-    long long bn = block_sum_ll<THREADS>(na, shl);
+    NSum bs[kProbeBuckets + 1];
+#pragma unroll
+    for (int b = 0; b <= kProbeBuckets; ++b) bs[b] = {bsum[b], 0.0};
+    nsum_block_reduce_staged<THREADS, kProbeBuckets + 1>(bs, shn);
+    bucket_counts_reduce<THREADS>(bcnt, shl);
     if (threadIdx.x == 0) {
-      A.probe_part[blockIdx.x].ea = bs[0];
-      A.probe_part[blockIdx.x].n_active = bn;
+#pragma unroll
+      for (int b = 0; b <= kProbeBuckets; ++b) A.probe_part[blockIdx.x].sum[b] = bs[b];
+#pragma unroll
+      for (int b = 0; b < kProbeBuckets; ++b) A.probe_part[blockIdx.x].cnt[b] = bcnt[b];
     }
   }
   if (!last_block_arrived(&c.ticket_probe)) return;
-  NSum pa[1] = {{0.0, 0.0}};
-  long long pn = 0;
-  for (int64_t b = threadIdx.x; b < nparts; b += THREADS) {
-    pa[0] = ncomb(pa[0], A.probe_part[b].ea);
-    pn += A.probe_part[b].n_active;
+  NSum ps[kProbeBuckets + 1];
+  long long pc[kProbeBuckets];
+#pragma unroll
+  for (int b = 0; b <= kProbeBuckets; ++b) ps[b] = {0.0, 0.0};
+#pragma unroll
+  for (int b = 0; b < kProbeBuckets; ++b) pc[b] = 0;
+  for (int64_t blk = threadIdx.x; blk < nparts; blk += THREADS) {
+#pragma unroll
+    for (int b = 0; b <= kProbeBuckets; ++b) ps[b] = ncomb(ps[b], A.probe_part[blk].sum[b]);
+#pragma unroll
+    for (int b = 0; b < kProbeBuckets; ++b) pc[b] += A.probe_part[blk].cnt[b];
   }
-  nsum_block_reduce_staged<THREADS, 1>(pa, shn);
-  const long long n = block_sum_ll<THREADS>(pn, shl);
-  if (threadIdx.x == 0) {
-    const int cont = threshold_step(c, n, nval(pa[0]));
-    c.search_cont = cont;
-    set_cond(A.use_graph, A.h_probe, (unsigned)cont);
-    __threadfence();
+  nsum_block_reduce_staged<THREADS, kProbeBuckets + 1>(ps, shn);
+  bucket_counts_reduce<THREADS>(pc, shl);
+  if (threadIdx.x != 0) return;
+  // at the sorted threshold T[j]: the candidate actives are the rel-err
+  // actives of buckets j+1.., the candidate finished error that of buckets
+  // 0..j plus the rel-err finished
+  long long n_at[kProbeNodes];
+  double e_at[kProbeNodes];
+  {
+    long long above = 0;
+    for (int j = kProbeNodes - 1; j >= 0; --j) {
+      above += pc[j + 1];
+      n_at[j] = above;
+    }
+    NSum below = ps[kProbeBuckets];
+    for (int j = 0; j < kProbeNodes; ++j) {
+      below = ncomb(below, ps[j]);
+      e_at[j] = nval(below);
+    }
   }
+  int k = 0, cont = 1;
+  for (int depth = 0; depth < kProbeDepth && cont; ++depth) {
+    int j = 0;
+    while (j < kProbeNodes - 1 && T[j] != ebits(node[k])) ++j;
+    cont = threshold_step(c, n_at[j], e_at[j]);
+    if (cont && depth + 1 < kProbeDepth) {
+      // the step moved t to one of node k's children, bit for bit
+      if (c.t == node[2 * k + 1]) {
+        k = 2 * k + 1;
+      } else if (c.t == node[2 * k + 2]) {
+        k = 2 * k + 2;
+      } else {
+        c.watchdog = 3;
+        c.search_ok = 0;
+        cont = 0;
+      }
+    }
+  }
+  c.search_cont = cont;
+  set_cond(A.use_graph, A.h_probe, (unsigned)cont);
+  __threadfence();
 }
 
 // ------------------------------------------- finished sums + survivor count
-// Per tile of kTile regions: the number of survivors under the final
-// classification.  Per block: sum V.A, sum E.A and the finished volume.  The
-// last block scans the tile counts and takes the decisions that follow
-// Threshold-Classify in Algorithm 2 (v_f, e_f, the memory check).
+// The final classification of every region (Evaluate's Rel-Err-Classify
+// byte and, after a successful threshold search, E >= t), the survivors of
+// every 256-region warp slice of a tile, and per block the sums of V, E and
+// the volume of the finished regions.  The last block scans the tile counts
+// and takes the decisions that follow Threshold-Classify in Algorithm 2
+// (v_f, e_f, the memory check).
+//
+// Built for bandwidth: a thread takes ITEMS contiguous regions of a tile
+// (one 8-byte load of their classification bytes), the bytes of kCountAhead
+// tiles are requested before the first is used, every warp stores its own
+// slice count (no block-wide barrier per tile), and V, E and the levels are
+// read only where they are needed: E of the rel-err actives after a search,
+// V, E and levels of the finished.
+constexpr int kCountAhead = 8;
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
+  static_assert(ITEMS == 8 && THREADS / 32 == kTileWarps, "one 8-byte load per thread, one slice per warp");
   Ctrl& c = *A.ctrl;
   if (c.done) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(A.use_graph, A.h_main, 0u);
@@ -148,64 +273,87 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   const uint8_t* __restrict__ level = A.pool.level + (size_t)((c.it - 1) & 1) * n * cap;
   const double* __restrict__ V = A.pool.V;
   const double* __restrict__ E = A.pool.E;
+  uint8_t* __restrict__ act = A.pool.act;
   const int64_t ntiles = (s + TILE - 1) / TILE;
+  const bool searched = c.search_ok != 0;
+  const unsigned long long tb = ebits(c.t);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ long long shl[2 * (THREADS / 32)];
   __shared__ NSum shn[3 * THREADS + 3];
-  // each thread sums its ITEMS regions of a tile plainly (relative error at
-  // most (ITEMS - 1) u) and adds that partial into Neumaier accumulators, so
-  // the sums stay compensated across all partials at a third of the FP64 work
+  // a thread adds its finished regions of a tile plainly (relative error at
+  // most (ITEMS - 1) u) and that partial into Neumaier accumulators
   NSum acc3[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};  // finished V, E and volume
-  NSum& va = acc3[0];
-  NSum& ea = acc3[1];
-  NSum& fv = acc3[2];
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    long long cnt = 0;
-    double tv = 0.0, te = 0.0, tf = 0.0;
-    // every item's V and E are requested before the first is used
-    double vv[ITEMS], ee[ITEMS];
+  for (int64_t t0 = blockIdx.x; t0 < ntiles; t0 += (int64_t)gridDim.x * kCountAhead) {
+    unsigned long long bytes[kCountAhead];
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-      const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-      vv[r] = i < s ? V[i] : 0.0;
-      ee[r] = i < s ? E[i] : 0.0;
+    for (int u = 0; u < kCountAhead; ++u) {
+      const int64_t tile = t0 + (int64_t)u * gridDim.x;
+      const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * ITEMS;
+      // the act array holds cap >= s entries, cap a multiple of 4096: the
+      // 8-byte load stays inside it; bytes past s are masked below
+      bytes[u] = tile < ntiles && i0 < s ? *reinterpret_cast<const unsigned long long*>(act + i0) : 0ull;
     }
-    // classification of every item, then the levels of the finished ones
-    // (all loads issued before the first store), then the stores and sums
-    bool actv[ITEMS];
+#pragma unroll 1
+    for (int u = 0; u < kCountAhead; ++u) {
+      const int64_t tile = t0 + (int64_t)u * gridDim.x;
+      if (tile >= ntiles) break;
+      const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * ITEMS;
+      const int valid = i0 < s ? (s - i0 < ITEMS ? (int)(s - i0) : ITEMS) : 0;
+      int a0[ITEMS];
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-      const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-      actv[r] = i < s && final_active(vv[r], ee[r], c);
-    }
-    int Lr[ITEMS];
+      for (int r = 0; r < ITEMS; ++r) a0[r] = r < valid && ((bytes[u] >> (8 * r)) & 0xff) != 0;
+      double ee[ITEMS];
+      bool actv[ITEMS];
+      if (searched) {
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) Lr[r] = 0;
-    for (int j = 0; j < n; ++j) {
+        for (int r = 0; r < ITEMS; ++r) ee[r] = a0[r] ? E[i0 + r] : 0.0;
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) actv[r] = a0[r] && ebits(ee[r]) >= tb;
+      } else {
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) actv[r] = a0[r];
+      }
+      int cnt = 0, nfin = 0;
 #pragma unroll
       for (int r = 0; r < ITEMS; ++r) {
-        const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-        if (i < s && !actv[r]) Lr[r] += level[(size_t)j * cap + i];
+        cnt += actv[r];
+        nfin += r < valid && !actv[r];
       }
-    }
+      if (nfin) {
+        double vv[ITEMS];
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-      const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-      if (i < s) {
-        A.pool.act[i] = actv[r] ? 1 : 0;  // the split reads it back
-        if (actv[r]) {
-          ++cnt;
-        } else {
-          tv += vv[r];
-          te += ee[r];
-          tf += pow2_neg(Lr[r]);
+        for (int r = 0; r < ITEMS; ++r) {
+          const bool fin = r < valid && !actv[r];
+          vv[r] = fin ? V[i0 + r] : 0.0;
+          if (fin && !(searched && a0[r])) ee[r] = E[i0 + r];
         }
+        int Lr[ITEMS];
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) Lr[r] = 0;
+        for (int j = 0; j < n; ++j) {
+          const unsigned long long lv = *reinterpret_cast<const unsigned long long*>(level + (size_t)j * cap + i0);
+#pragma unroll
+          for (int r = 0; r < ITEMS; ++r) Lr[r] += (int)((lv >> (8 * r)) & 0xff);
+        }
+        double tv = 0.0, te = 0.0, tf = 0.0;
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r)
+          if (r < valid && !actv[r]) {
+            tv += vv[r];
+            te += ee[r];
+            tf += pow2_neg(Lr[r]);
+          }
+        nadd(acc3[0], tv);
+        nadd(acc3[1], te);
+        nadd(acc3[2], tf);
+        if (searched)  // regions finished by the threshold: the split reads the byte back
+#pragma unroll
+          for (int r = 0; r < ITEMS; ++r)
+            if (a0[r] && !actv[r]) act[i0 + r] = 0;
       }
+      const int wc = __reduce_add_sync(0xffffffffu, cnt);
+      if (lane == 0) A.pool.tile_count[tile * kTileWarps + warp] = wc;
     }
-    nadd(va, tv);
-    nadd(ea, te);
-    nadd(fv, tf);
-    const long long tc = block_sum_ll<THREADS>(cnt, shl);
-    if (threadIdx.x == 0) A.pool.tile_count[tile] = tc;
   }
   // a block without tiles holds exact zeros: it skips the FP64 shuffles (a
   // warp-wide FP64 instruction costs the SM's FP64 pipe 16 cycles) and the
@@ -215,23 +363,29 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   if ((int64_t)blockIdx.x < nparts) {
     nsum_block_reduce_staged<THREADS, 3>(acc3, shn);
     if (threadIdx.x == 0) {
-      A.count_part[blockIdx.x].va = va;
-      A.count_part[blockIdx.x].ea = ea;
-      A.count_part[blockIdx.x].finvol = fv;
+      A.count_part[blockIdx.x].va = acc3[0];
+      A.count_part[blockIdx.x].ea = acc3[1];
+      A.count_part[blockIdx.x].finvol = acc3[2];
     }
   }
   if (!last_block_arrived(&c.ticket_count)) return;
 
-  // exclusive scan of the tile counts: each thread a contiguous chunk, the
-  // chunk sums scanned by warp shuffles
+  // exclusive scan of the tile counts (each the sum of its warp slices):
+  // each thread a contiguous chunk of tiles, the chunk sums scanned by warp
+  // shuffles
   const int64_t per = (ntiles + THREADS - 1) / THREADS;
-  const int64_t t0 = threadIdx.x * per, t1 = t0 + per < ntiles ? t0 + per : ntiles;
+  const int64_t q0 = threadIdx.x * per, q1 = q0 + per < ntiles ? q0 + per : ntiles;
+  auto tile_total = [&](int64_t t) {
+    const int4* w = reinterpret_cast<const int4*>(A.pool.tile_count + t * kTileWarps);
+    const int4 a = w[0], b = w[1];
+    return (long long)a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w;
+  };
   long long acc = 0;
-  for (int64_t t = t0; t < t1; ++t) acc += A.pool.tile_count[t];
+  for (int64_t t = q0; t < q1; ++t) acc += tile_total(t);
   long long n_surv = 0;
   long long run = block_exclusive_scan<THREADS>(acc, shl, &n_surv);
-  for (int64_t t = t0; t < t1; ++t) {
-    const long long x = A.pool.tile_count[t];
+  for (int64_t t = q0; t < q1; ++t) {
+    const long long x = tile_total(t);
     A.pool.tile_offset[t] = run;
     run += x;
   }
@@ -594,7 +748,7 @@ static int ensure_workspace(int64_t want_cap, int n) {
   PG_ALLOC(w.pool.K, cap);
   PG_ALLOC(w.pool.act, cap);
   PG_ALLOC(w.pool.Vp, cap / 2 + 1);
-  PG_ALLOC(w.pool.tile_count, ntiles);
+  PG_ALLOC(w.pool.tile_count, ntiles * kTileWarps);
   PG_ALLOC(w.pool.tile_offset, ntiles);
   PG_ALLOC(w.ctrl, 1);
   PG_ALLOC(w.prm, 1);
@@ -1080,6 +1234,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
     }
   }
   if (h.watchdog == 1) return out->status = fail(PAGANI_ERR_WATCHDOG, "region depth limit reached on one axis");
+  if (h.watchdog == 3) return out->status = fail(PAGANI_ERR_WATCHDOG, "threshold search left its probe tree");
   if (h.watchdog) return out->status = fail(PAGANI_ERR_WATCHDOG, "device loop exceeded its iteration bound");
   if (!h.done) return out->status = fail(PAGANI_ERR_WATCHDOG, "device loop ended without a result");
   out->status = h.status;
@@ -1129,7 +1284,7 @@ static NoallocLayout noalloc_layout(int64_t cap, int n, int max_grid) {
   L.K = take((size_t)cap);
   L.act = take((size_t)cap);
   L.Vp = take(sizeof(double) * (size_t)(cap / 2 + 1));
-  L.tile_count = take(sizeof(long long) * (size_t)ntiles);
+  L.tile_count = take(sizeof(int) * (size_t)ntiles * kTileWarps);
   L.tile_offset = take(sizeof(long long) * (size_t)ntiles);
   L.total = off;
   return L;
@@ -1211,7 +1366,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   a.pool.K = base + L.K;
   a.pool.act = base + L.act;
   a.pool.Vp = reinterpret_cast<double*>(base + L.Vp);
-  a.pool.tile_count = reinterpret_cast<long long*>(base + L.tile_count);
+  a.pool.tile_count = reinterpret_cast<int*>(base + L.tile_count);
   a.pool.tile_offset = reinterpret_cast<long long*>(base + L.tile_offset);
   a.pool.cap = cap;
   a.pool.n = n;

@@ -156,10 +156,16 @@ struct CountPartial {
   NSum va, ea, finvol;  // V, E and volume summed over the finished regions
 };
 
+// Threshold-Classify probes take the search kProbeDepth steps per pass: the
+// tree of the coming thresholds has kProbeNodes nodes, and the sorted
+// thresholds cut the errors into kProbeBuckets buckets.
+constexpr int kProbeDepth = 3;
+constexpr int kProbeNodes = (1 << kProbeDepth) - 1;
+constexpr int kProbeBuckets = kProbeNodes + 1;
+
 struct ProbePartial {
-  NSum ea;              // E summed over the candidate finished regions
-  long long n_active;   // candidate actives
-  long long pad;
+  NSum sum[kProbeBuckets + 1];      // E of the rel-err actives per bucket; last: E of the rel-err finished
+  long long cnt[kProbeBuckets];     // rel-err actives per bucket
 };
 
 // Rule data passed by value to the evaluate kernels.
@@ -185,9 +191,10 @@ struct Pool {
   double* V;            // cap
   double* E;            // cap
   uint8_t* K;           // cap
-  uint8_t* act;         // cap: final classification of the iteration (1 = survivor)
+  uint8_t* act;         // cap: Rel-Err-Classify of the iteration (written by Evaluate), then the
+                        // final classification (the count kernel clears threshold-finished ones)
   double* Vp;           // cap / 2 + 1
-  long long* tile_count;   // n_tiles + 1
+  int* tile_count;         // (n_tiles + 1) * kTileWarps: survivors per warp slice of a tile
   long long* tile_offset;  // n_tiles + 1
   int64_t cap;
   int n;
@@ -341,6 +348,7 @@ const FamilyKernels& kernels_box_power_gm7();
 constexpr int kSplitThreads = 256;
 constexpr int kItemsPerThread = 8;
 constexpr int kTile = kSplitThreads * kItemsPerThread;  // regions per compaction tile
+constexpr int kTileWarps = 8;  // warp slices per tile in the survivor count (256 regions each)
 constexpr int kReduceThreads = 256;
 
 }  // namespace pg
