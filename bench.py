@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation report")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle time budget per integral")
     ap.add_argument("--quiet", action="store_true")
+    ap.add_argument("--paper-suite", action="store_true",
+                    help="instead of the bench line: digits of precision reached on the paper's f1..f8 (Sec. 4.2)")
     return ap.parse_args()
 
 
@@ -249,9 +251,8 @@ def management_bandwidth(part, hbm_peak):
     host-driven integration: algorithmic bytes from the per-iteration trace
     (s regions, r rel-err actives, n_surv survivors, n axes, whether a
     threshold search succeeded) over the phase's CUDA-event time.
-      probe: per pass, every region's classification byte and error, 9 s;
-             a pass takes three steps of the search, so an iteration with p
-             probes makes ceil(p / 3) passes
+      probe: per pass, every region's classification byte and error, 9 s
+             (the passes of each iteration are in the trace)
       count: the classification bytes, s; V and the n level bytes of every
              finished region, (8 + n)(s - n_surv); E of the finished, or
              after a search E of every region and the byte of each region
@@ -265,7 +266,7 @@ def management_bandwidth(part, hbm_peak):
     surv = tr["n_survivors"].astype(float)
     rel = tr["n_relerr_active"].astype(float)
     ok = tr["search_ok"].astype(bool)
-    passes = np.ceil(tr["probes"].astype(float) / 3.0)
+    passes = tr["probe_passes"].astype(float)
     probe_b = float(np.sum(passes * 9 * s))
     fin = s - surv
     count_b = float(np.sum(s + (8 + n) * fin + np.where(ok, 8 * s + (rel - surv), 8 * fin)))
@@ -397,6 +398,40 @@ def batching_report(pg, torch, flush, slot: int = 16384):
             "within_errorest_of_closed_form": float(inside.mean())}
 
 
+def paper_suite_report(pg, torch, max_regions: int = 1 << 28, digits=range(3, 11)):
+    """The accuracy experiment of Sec. 4.2 on the paper's fixed-parameter
+    integrands f1..f8: each at epsrel 1e-3, 1e-4, ... until a run does not
+    converge, with a pool of max_regions regions; time to result (CUDA
+    events), status, iterations, regions, the error estimate and, where a
+    closed form exists, the true relative error."""
+    from oracle import closed_forms as cf
+    from paper_2104_06494_gb300.workloads import paper_integrands
+    stream = torch.cuda.current_stream().cuda_stream
+    pg.pagani_workspace_reserve(max_regions, 8)
+    out = {"max_regions": max_regions}
+    for name, w in paper_integrands().items():
+        ex = cf.closed_form(w.family, w.dim, w.params)
+        runs = []
+        for dg in digits:
+            tau = 10.0 ** -dg
+            kw = dict(max_regions=max_regions, relerr_filter=w.relerr_filter, stream=stream)
+            pg.pagani_integrate_ex(w.dim, w.family, w.params, tau, **kw)  # warm-up: graph
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r = pg.pagani_integrate_ex(w.dim, w.family, w.params, tau, **kw)
+            b.record()
+            torch.cuda.synchronize()
+            runs.append({"digits": dg, "ms": a.elapsed_time(b), "status": r.status, "iterations": r.iterations,
+                         "regions": r.n_regions, "errorest_rel": r.errorest / abs(r.estimate),
+                         "true_relerr": None if ex is None else abs(r.estimate - ex) / abs(ex),
+                         "within_errorest": None if ex is None else bool(abs(r.estimate - ex) <= r.errorest)})
+            if r.status != 0:
+                break
+        out[name] = runs
+    pg.pagani_workspace_release()
+    return out
+
+
 def main():
     args = parse()
     import torch
@@ -446,6 +481,12 @@ def main():
     from paper_2104_06494_gb300 import build as pbuild, roofline
     pbuild.build()
     pg.load()
+    if args.paper_suite:
+        if rank == 0:
+            print(json.dumps({"paper_suite": paper_suite_report(pg, torch)}))
+        if world > 1:
+            dist.destroy_process_group()
+        return
     stream = torch.cuda.current_stream(dev).cuda_stream
 
     # workspace outside the timed region (the paper times integration only)

@@ -125,6 +125,8 @@ typedef struct {
   int32_t it, trigger, probes, search_ok;
   int64_t s, n_relerr_active, n_survivors;
   double v, e, vf, ef, threshold, direction_changes;
+  int32_t probe_passes;   /* probe kernel launches of this iteration's threshold search */
+  int32_t reserved;
 } pagani_trace_record;
 
 /* Fills *opt with the defaults listed above. */

@@ -62,7 +62,8 @@ class Options(ctypes.Structure):
 TRACE_DTYPE = np.dtype([("it", np.int32), ("trigger", np.int32), ("probes", np.int32), ("search_ok", np.int32),
                         ("s", np.int64), ("n_relerr_active", np.int64), ("n_survivors", np.int64),
                         ("v", np.float64), ("e", np.float64), ("vf", np.float64), ("ef", np.float64),
-                        ("threshold", np.float64), ("direction_changes", np.float64)])
+                        ("threshold", np.float64), ("direction_changes", np.float64),
+                        ("probe_passes", np.int32), ("reserved", np.int32)])
 
 # every symbol include/pagani.h declares
 EXPORTED = ["pagani_default_options", "pagani_integrate", "pagani_integrate_ex", "pagani_workspace_reserve",

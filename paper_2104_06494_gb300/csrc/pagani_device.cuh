@@ -320,6 +320,7 @@ __device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long 
   c.search_ok = 0;
   c.trigger = 0;
   c.probes = 0;
+  c.passes = 0;
   c.dir_changes = 0;
   c.t = 0.0;
   if (nonfinite || !isfinite(v) || !isfinite(e)) {

@@ -86,156 +86,177 @@ __device__ __forceinline__ unsigned long long ebits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
 }
 
-// Counts of `cnt` (kProbeBuckets per thread) reduced over the block; valid
-// on thread 0.  sh holds kProbeBuckets * THREADS / 32 words.
-template <int THREADS>
-__device__ __forceinline__ void bucket_counts_reduce(long long (&cnt)[kProbeBuckets], long long* sh) {
-  constexpr int NW = THREADS / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int b = 0; b < kProbeBuckets; ++b) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) cnt[b] += __shfl_down_sync(0xffffffffu, cnt[b], off);
+// E as an unsigned 128-bit fixed-point multiple of the error budget:
+// floor(E 2^kProbeFrac / e_b) for E < e_b (below 2^kProbeFrac), and exactly
+// 2^kProbeFrac (the budget itself) for E >= e_b.  e_b = 2^B is a power of
+// two, so this is a shift of E's significand; integer operations only.
+// e_bits: the bit pattern of e_b.
+__device__ __forceinline__ void probe_fixed(unsigned long long eb, unsigned long long e_bits, int B,
+                                            unsigned long long& lo, unsigned long long& hi) {
+  if (eb >= e_bits) {
+    lo = 0ull;
+    hi = 1ull << (kProbeFrac - 64);
+    return;
   }
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int b = 0; b < kProbeBuckets; ++b) sh[b * NW + warp] = cnt[b];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int b = 0; b < kProbeBuckets; ++b) {
-      long long t = 0;
-      for (int w = 0; w < NW; ++w) t += sh[b * NW + w];
-      cnt[b] = t;
-    }
+  int ex = (int)(eb >> 52);
+  unsigned long long m = eb & ((1ull << 52) - 1);
+  if (ex) m |= 1ull << 52;
+  else ex = 1;
+  // E = m 2^(ex - 1075); E 2^(kProbeFrac - B) = m 2^sh, below 2^kProbeFrac
+  const int sh = ex - 1075 + kProbeFrac - B;
+  if (sh >= 64) {
+    lo = 0ull;
+    hi = m << (sh - 64);
+  } else if (sh > 0) {
+    lo = m << sh;
+    hi = m >> (64 - sh);
+  } else if (sh > -64) {
+    lo = m >> (-sh);
+    hi = 0ull;
+  } else {
+    lo = hi = 0ull;
+  }
 }
 
-// Threshold-Classify (Algorithm 3), kProbeDepth steps of the search per
-// pass.  From the current threshold t every step moves halfway to max E or
-// to min E, so the thresholds of the next kProbeDepth steps form a binary
-// tree (node k's children 2k+1, lower, and 2k+2, upper).  One pass places
-// every rel-err active region in the bucket between the tree's sorted
-// thresholds its error falls into, counting the regions and summing their
-// errors per bucket, and sums the errors of the rel-err finished regions
-// (Evaluate's classification byte).  For each node that gives the
-// candidate actives (E >= t) and the candidate finished error e_abar, so
-// the last block takes the steps of Algorithm 3 along the path the search
-// follows through the tree, with the same threshold_step a probe per step
-// would run: same thresholds, probe count, P_max and outcome.
+// Threshold-Classify (Algorithm 3): one probe pass takes the search from the
+// current threshold t through up to kProbeRay + 1 of its steps.  A step that
+// keeps the direction of the one before moves t halfway towards min E (down)
+// or max E (up) again, so a run of steps in one direction visits the
+// thresholds of one of two rays from t, computed here with search_next, the
+// function threshold_step moves by.  Every block places each region's error
+// among the kProbeThr sorted thresholds (down ray reversed, t, up ray) and
+// adds it to its bucket (rel-err actives) or to the finished bin; the bins
+// hold exact integer sums (probe_fixed) and counts, combined over the grid by
+// integer atomics.  The last block then takes the steps of Algorithm 3 with
+// those totals: at a threshold, the candidate actives are the rel-err actives
+// of the buckets above it and e_abar is the error of the buckets below it
+// plus the rel-err finished.  The pass ends when the search ends, changes
+// direction after its first step, or reaches the end of a ray; a following
+// pass starts from the threshold it left in c.t.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 2) k_probe(const LoopArgs A) {
+__global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   Ctrl& c = *A.ctrl;
-  const int64_t s = c.s;
-  double node[kProbeNodes];
-  node[0] = c.t;
-#pragma unroll
-  for (int k = 0; k < kProbeNodes / 2; ++k) {
-    node[2 * k + 1] = search_next(node[k], -1, c.emin, c.emax);
-    node[2 * k + 2] = search_next(node[k], +1, c.emin, c.emax);
-  }
-  unsigned long long T[kProbeNodes];  // the thresholds, ascending
-#pragma unroll
-  for (int k = 0; k < kProbeNodes; ++k) T[k] = ebits(node[k]);
-  for (int a = 1; a < kProbeNodes; ++a)
-    for (int b = a; b > 0 && T[b - 1] > T[b]; --b) {
-      const unsigned long long x = T[b];
-      T[b] = T[b - 1];
-      T[b - 1] = x;
+  constexpr int NW = THREADS / 32;
+  __shared__ unsigned long long thr[32];               // sorted thresholds, padded with all ones
+  __shared__ ulonglong2 hist[kProbeBins * THREADS];    // per thread: (lo, hi | count << 44) per bin
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 2) {
+    const int dir = threadIdx.x ? 1 : -1;
+    double t = c.t;
+    for (int k = 1; k <= kProbeRay; ++k) {
+      t = search_next(t, dir, c.emin, c.emax);
+      thr[kProbeRay + dir * k] = ebits(t);
     }
-  // per-thread bucket sums: plain (a thread's relative error stays below
-  // its element count times u), combined compensated across threads
-  double bsum[kProbeBuckets + 1];
-  long long bcnt[kProbeBuckets];
-#pragma unroll
-  for (int b = 0; b < kProbeBuckets; ++b) {
-    bsum[b] = 0.0;
-    bcnt[b] = 0;
+  } else if (threadIdx.x == 2) {
+    thr[kProbeRay] = ebits(c.t);
+  } else if (threadIdx.x >= kProbeThr && threadIdx.x < 32) {
+    thr[threadIdx.x] = ~0ull;
   }
-  bsum[kProbeBuckets] = 0.0;
+#pragma unroll
+  for (int b = 0; b < kProbeBins; ++b) hist[b * THREADS + threadIdx.x] = make_ulonglong2(0ull, 0ull);
+  __syncthreads();
+  const unsigned long long e_bits = ebits(c.e_b);
+  int B;  // e_b = 2^B
+  if (e_bits >> 52) B = (int)(e_bits >> 52) - 1023;
+  else B = -1074 + 63 - __clzll((long long)e_bits);
+  const int64_t s = c.s;
   const uint8_t* __restrict__ act = A.pool.act;
   const double* __restrict__ E = A.pool.E;
-  for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < s; i += (int64_t)gridDim.x * THREADS) {
-    const double e = E[i];
-    if (!act[i]) {
-      bsum[kProbeBuckets] += e;
-      continue;
+  ulonglong2* mine = hist + threadIdx.x;
+  constexpr int U = 4;  // loads in flight per thread
+  const int64_t stride = (int64_t)gridDim.x * THREADS;
+  for (int64_t i0 = (int64_t)blockIdx.x * THREADS + threadIdx.x; i0 < s; i0 += U * stride) {
+    unsigned long long eb[U];
+    int a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      eb[u] = i < s ? ebits(E[i]) : 0ull;
+      a[u] = i < s ? (int)act[i] : -1;
     }
-    const unsigned long long eb = ebits(e);
-    int k = 0;
 #pragma unroll
-    for (int j = 0; j < kProbeNodes; ++j) k += eb >= T[j];
-    bsum[k] += e;
-    bcnt[k] += 1;
+    for (int u = 0; u < U; ++u) {
+      if (a[u] < 0) continue;
+      // number of thresholds at or below E (branch-free search of 32 entries)
+      int k = thr[15] <= eb[u] ? 16 : 0;
+      k += thr[k + 7] <= eb[u] ? 8 : 0;
+      k += thr[k + 3] <= eb[u] ? 4 : 0;
+      k += thr[k + 1] <= eb[u] ? 2 : 0;
+      k += thr[k] <= eb[u] ? 1 : 0;
+      const int bin = a[u] ? k : kProbeBuckets;
+      unsigned long long lo, hi;
+      probe_fixed(eb[u], e_bits, B, lo, hi);
+      ulonglong2 h = mine[bin * THREADS];
+      h.x += lo;
+      h.y += hi + (h.x < lo ? 1ull : 0ull) + (1ull << 44);
+      mine[bin * THREADS] = h;
+    }
   }
-  __shared__ NSum shn[(kProbeBuckets + 1) * THREADS + kProbeBuckets + 1];
-  __shared__ long long shl[kProbeBuckets * (THREADS / 32)];
-  // blocks without regions hold exact zeros and skip the FP64 reductions;
-  // the last block reads only the partials that can be non-zero
-  const int64_t nblk = (s + THREADS - 1) / THREADS;
-  const int64_t nparts = nblk < (int64_t)gridDim.x ? nblk : (int64_t)gridDim.x;
-  if ((int64_t)blockIdx.x < nparts) {
-    NSum bs[kProbeBuckets + 1];
+  __syncthreads();
+  // per bin: the block's sum and count, then one set of atomics
+  for (int b = warp; b < kProbeBins; b += NW) {
+    unsigned long long lo = 0ull, hi = 0ull, cnt = 0ull;
 #pragma unroll
-    for (int b = 0; b <= kProbeBuckets; ++b) bs[b] = {bsum[b], 0.0};
-    nsum_block_reduce_staged<THREADS, kProbeBuckets + 1>(bs, shn);
-    bucket_counts_reduce<THREADS>(bcnt, shl);
-    if (threadIdx.x == 0) {
+    for (int t = lane; t < THREADS; t += 32) {
+      const ulonglong2 h = hist[b * THREADS + t];
+      lo += h.x;
+      hi += (h.y & ((1ull << 44) - 1)) + (lo < h.x ? 1ull : 0ull);
+      cnt += h.y >> 44;
+    }
 #pragma unroll
-      for (int b = 0; b <= kProbeBuckets; ++b) A.probe_part[blockIdx.x].sum[b] = bs[b];
-#pragma unroll
-      for (int b = 0; b < kProbeBuckets; ++b) A.probe_part[blockIdx.x].cnt[b] = bcnt[b];
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long lo2 = __shfl_down_sync(0xffffffffu, lo, off);
+      const unsigned long long hi2 = __shfl_down_sync(0xffffffffu, hi, off);
+      const unsigned long long c2 = __shfl_down_sync(0xffffffffu, cnt, off);
+      lo += lo2;
+      hi += hi2 + (lo < lo2 ? 1ull : 0ull);
+      cnt += c2;
+    }
+    if (lane == 0 && cnt != 0ull) {
+      ProbeAcc& g = A.probe_acc[b];
+      const unsigned long long old = atomicAdd(&g.lo, lo);
+      atomicAdd(&g.hi, hi + (old + lo < old ? 1ull : 0ull));
+      atomicAdd(&g.cnt, cnt);
     }
   }
   if (!last_block_arrived(&c.ticket_probe)) return;
-  NSum ps[kProbeBuckets + 1];
-  long long pc[kProbeBuckets];
-#pragma unroll
-  for (int b = 0; b <= kProbeBuckets; ++b) ps[b] = {0.0, 0.0};
-#pragma unroll
-  for (int b = 0; b < kProbeBuckets; ++b) pc[b] = 0;
-  for (int64_t blk = threadIdx.x; blk < nparts; blk += THREADS) {
-#pragma unroll
-    for (int b = 0; b <= kProbeBuckets; ++b) ps[b] = ncomb(ps[b], A.probe_part[blk].sum[b]);
-#pragma unroll
-    for (int b = 0; b < kProbeBuckets; ++b) pc[b] += A.probe_part[blk].cnt[b];
-  }
-  nsum_block_reduce_staged<THREADS, kProbeBuckets + 1>(ps, shn);
-  bucket_counts_reduce<THREADS>(pc, shl);
   if (threadIdx.x != 0) return;
-  // at the sorted threshold T[j]: the candidate actives are the rel-err
-  // actives of buckets j+1.., the candidate finished error that of buckets
-  // 0..j plus the rel-err finished
-  long long n_at[kProbeNodes];
-  double e_at[kProbeNodes];
-  {
-    long long above = 0;
-    for (int j = kProbeNodes - 1; j >= 0; --j) {
-      above += pc[j + 1];
-      n_at[j] = above;
-    }
-    NSum below = ps[kProbeBuckets];
-    for (int j = 0; j < kProbeNodes; ++j) {
-      below = ncomb(below, ps[j]);
-      e_at[j] = nval(below);
-    }
+  unsigned long long slo[kProbeBins], shi[kProbeBins], scnt[kProbeBins];
+  for (int b = 0; b < kProbeBins; ++b) {
+    slo[b] = __ldcg(&A.probe_acc[b].lo);
+    shi[b] = __ldcg(&A.probe_acc[b].hi);
+    scnt[b] = __ldcg(&A.probe_acc[b].cnt);
+    A.probe_acc[b].lo = A.probe_acc[b].hi = A.probe_acc[b].cnt = 0ull;  // zero for the next pass
   }
-  int k = 0, cont = 1;
-  for (int depth = 0; depth < kProbeDepth && cont; ++depth) {
+  c.passes += 1;
+  c.total_passes += 1;
+  int pos = kProbeRay, ray = 0, cont = 1;
+  for (;;) {
+    // the first sorted threshold equal to c.t: the regions at or above it
+    // are the candidate actives
+    const unsigned long long tb = ebits(c.t);
     int j = 0;
-    while (j < kProbeNodes - 1 && T[j] != ebits(node[k])) ++j;
-    cont = threshold_step(c, n_at[j], e_at[j]);
-    if (cont && depth + 1 < kProbeDepth) {
-      // the step moved t to one of node k's children, bit for bit
-      if (c.t == node[2 * k + 1]) {
-        k = 2 * k + 1;
-      } else if (c.t == node[2 * k + 2]) {
-        k = 2 * k + 2;
-      } else {
-        c.watchdog = 3;
-        c.search_ok = 0;
-        cont = 0;
-      }
+    while (j < kProbeThr - 1 && thr[j] != tb) ++j;
+    long long n_act = 0;
+    for (int b = j + 1; b < kProbeBuckets; ++b) n_act += (long long)scnt[b];
+    unsigned long long lo = slo[kProbeBuckets], hi = shi[kProbeBuckets];
+    for (int b = 0; b <= j; ++b) {
+      lo += slo[b];
+      hi += shi[b] + (lo < slo[b] ? 1ull : 0ull);
+    }
+    const double e_abar = scalbn(fma(__ull2double_rn(hi), 0x1p64, __ull2double_rn(lo)), B - kProbeFrac);
+    cont = threshold_step(c, n_act, e_abar);
+    if (!cont) break;
+    const int d = c.last_dir;
+    if (ray == 0) ray = d;
+    if (d != ray) break;                                    // off the rays: the next pass starts at c.t
+    if (pos + d < 0 || pos + d > 2 * kProbeRay) break;      // past the end of the ray
+    pos += d;
+    if (ebits(c.t) != thr[pos]) {  // the step must land on the ray's next threshold, bit for bit
+      c.watchdog = 3;
+      c.search_ok = 0;
+      cont = 0;
+      break;
     }
   }
   c.search_cont = cont;
@@ -406,6 +427,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     tr->n_survivors = n_surv;
     if (c.trigger) {
       tr->probes = c.probes;
+      tr->probe_passes = c.passes;
       tr->search_ok = c.search_ok;
       tr->threshold = c.t;
       tr->direction_changes = (double)c.dir_changes;
@@ -621,7 +643,7 @@ struct Workspace {
   Ctrl* ctrl = nullptr;
   IntegrandParams* prm = nullptr;
   EvalPartial* eval_part = nullptr;
-  ProbePartial* probe_part = nullptr;
+  ProbeAcc* probe_acc = nullptr;  // kProbeBins bins, zero between probe passes
   CountPartial* count_part = nullptr;
   TraceRec* trace = nullptr;
   int trace_cap = 0;
@@ -753,7 +775,7 @@ static int ensure_workspace(int64_t want_cap, int n) {
   PG_ALLOC(w.ctrl, 1);
   PG_ALLOC(w.prm, 1);
   PG_ALLOC(w.eval_part, w.max_grid);
-  PG_ALLOC(w.probe_part, w.max_grid);
+  PG_ALLOC(w.probe_acc, kProbeBins);
   PG_ALLOC(w.count_part, w.max_grid);
   PG_ALLOC(w.trace, kTraceCap);
   {
@@ -904,6 +926,7 @@ struct Launch {
   int eval_grid, eval_block;
   size_t eval_smem;
   int mgmt_grid;
+  int probe_grid;
 };
 
 static int launch_config(const FamilyKernels& fk, int n, Launch* L) {
@@ -918,6 +941,8 @@ static int launch_config(const FamilyKernels& fk, int n, Launch* L) {
   if (L->eval_grid > w.max_grid) L->eval_grid = w.max_grid;
   L->mgmt_grid = w.sms * 2;
   if (L->mgmt_grid > w.max_grid) L->mgmt_grid = w.max_grid;
+  L->probe_grid = w.sms * 4;
+  if (L->probe_grid > w.max_grid) L->probe_grid = w.max_grid;
   return 0;
 }
 
@@ -932,7 +957,7 @@ static LoopArgs loop_args(int n, int use_graph, cudaGraphConditionalHandle hm, c
   a.ctrl = w.ctrl;
   a.prm = w.prm;
   a.eval_part = w.eval_part;
-  a.probe_part = w.probe_part;
+  a.probe_acc = w.probe_acc;
   a.count_part = w.count_part;
   a.trace = w.trace;
   a.trace_cap = w.trace_cap;
@@ -1006,8 +1031,8 @@ static int build_graph(int fam, int n, int degree, const EvalRule& rule, const L
   args = loop_args(n, 1, hm, hp);
   PG_CK(add_kernel(&nev, body, nullptr, 0, fk.loop_fn[n], L.eval_grid, L.eval_block, L.eval_smem, eargs));
   PG_CK(add_while(&wprobe, body, &nev, 1, hp, &pbody));
-  PG_CK(add_kernel(&nprobe, pbody, nullptr, 0, (const void*)&k_probe<kMgmtThreads>, L.mgmt_grid, kMgmtThreads, 0,
-                   margs));
+  PG_CK(add_kernel(&nprobe, pbody, nullptr, 0, (const void*)&k_probe<kProbeThreads>, L.probe_grid, kProbeThreads,
+                   0, margs));
   PG_CK(add_kernel(&ncount, body, &wprobe, 1, (const void*)&k_count<kMgmtThreads, kMgmtItems>, L.mgmt_grid,
                    kMgmtThreads, 0, margs));
   PG_CK(add_kernel(&nsplit, body, &ncount, 1, (const void*)&k_split<kMgmtThreads, kMgmtItems>, L.mgmt_grid,
@@ -1108,6 +1133,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
   // the pool must be indexed with the call's dimension
   w.pool.n = n;
   PG_CK(cudaMemcpyAsync(w.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  PG_CK(cudaMemsetAsync(w.probe_acc, 0, sizeof(ProbeAcc) * kProbeBins, st));  // probe bins start at zero
   PG_CK(cudaMemcpyAsync(w.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
   {
     Pool p = w.pool;
@@ -1163,7 +1189,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
       if (h.search) {
         for (int probe = 0; probe < 128; ++probe) {
           PG_CK(cudaEventRecord(ev[0], st));
-          k_probe<kMgmtThreads><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
+          k_probe<kProbeThreads><<<L.probe_grid, kProbeThreads, 0, st>>>(args);
           PG_CK(cudaGetLastError());
           PG_CK(cudaEventRecord(ev[1], st));
           ++launches;
@@ -1209,7 +1235,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
     // the graph ran the cache fill once, then one Evaluate, count and split
     // per iteration plus the probes
     eval_launches = h.it;
-    launches += 1 + 3 * h.it + h.total_probes;
+    launches += 1 + 3 * h.it + h.total_passes;
   }
   out->eval_launches = eval_launches;
   out->kernel_launches = launches;
@@ -1260,7 +1286,7 @@ static void* g_noalloc_base[64] = {nullptr};
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NoallocLayout {
-  size_t ctrl, prm, eval_part, probe_part, count_part, lower, level, V, E, K, act, Vp, tile_count, tile_offset, total;
+  size_t ctrl, prm, eval_part, probe_acc, count_part, lower, level, V, E, K, act, Vp, tile_count, tile_offset, total;
 };
 
 static NoallocLayout noalloc_layout(int64_t cap, int n, int max_grid) {
@@ -1275,7 +1301,7 @@ static NoallocLayout noalloc_layout(int64_t cap, int n, int max_grid) {
   L.ctrl = take(sizeof(Ctrl));
   L.prm = take(sizeof(IntegrandParams));
   L.eval_part = take(sizeof(EvalPartial) * (size_t)max_grid);
-  L.probe_part = take(sizeof(ProbePartial) * (size_t)max_grid);
+  L.probe_acc = take(sizeof(ProbeAcc) * (size_t)kProbeBins);
   L.count_part = take(sizeof(CountPartial) * (size_t)max_grid);
   L.lower = take(sizeof(double) * 2 * (size_t)n * cap);
   L.level = take((size_t)2 * n * cap);
@@ -1355,6 +1381,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   if (e != cudaSuccess || occ < 1) return out->status = fail(PAGANI_ERR_CUDA, "evaluate kernel does not fit");
   Lc.eval_grid = sms * occ < max_grid ? sms * occ : max_grid;
   Lc.mgmt_grid = sms * 2;
+  Lc.probe_grid = sms * 4;
   const int64_t cap = ((max_regions + 4095) / 4096) * 4096;
   const NoallocLayout L = noalloc_layout(cap, n, max_grid);
   LoopArgs a;
@@ -1373,7 +1400,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   a.ctrl = reinterpret_cast<Ctrl*>(base + L.ctrl);
   a.prm = reinterpret_cast<const IntegrandParams*>(base + L.prm);
   a.eval_part = reinterpret_cast<EvalPartial*>(base + L.eval_part);
-  a.probe_part = reinterpret_cast<ProbePartial*>(base + L.probe_part);
+  a.probe_acc = reinterpret_cast<ProbeAcc*>(base + L.probe_acc);
   a.count_part = reinterpret_cast<CountPartial*>(base + L.count_part);
   a.trace = nullptr;
   a.trace_cap = 0;
@@ -1408,6 +1435,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
     }                                                                                     \
   } while (0)
   PG_CK(cudaMemcpyAsync(a.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  PG_CK(cudaMemsetAsync(a.probe_acc, 0, sizeof(ProbeAcc) * kProbeBins, st));  // probe bins start at zero
   PG_CK(cudaMemcpyAsync(base + L.prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, st));
   k_uniform_split<<<(int)((s0 + 255) / 256), 256, 0, st>>>(a.pool, d0, log2d, s0);
   PG_CK(cudaGetLastError());
@@ -1421,7 +1449,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
     d2h += sizeof(Ctrl);
     if (h.search) {
       for (int probe = 0; probe < 128; ++probe) {
-        k_probe<kMgmtThreads><<<Lc.mgmt_grid, kMgmtThreads, 0, st>>>(a);
+        k_probe<kProbeThreads><<<Lc.probe_grid, kProbeThreads, 0, st>>>(a);
         PG_CK(cudaGetLastError());
         ++launches;
         PG_CK(cudaMemcpyAsync(&h, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));

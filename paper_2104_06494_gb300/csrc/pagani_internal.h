@@ -128,7 +128,9 @@ struct Ctrl {
   unsigned int ticket_eval, ticket_probe, ticket_count, ticket_split;
   int32_t watchdog;          // set if a kernel saw an impossible state
   int32_t loop_guard;        // iterations counted by the count kernel
-  int32_t total_probes;      // threshold probes over the whole call
+  int32_t total_probes;      // threshold probes (search steps) over the whole call
+  int32_t passes;            // probe passes (k_probe launches) this iteration
+  int32_t total_passes;      // probe passes over the whole call
   int32_t l0;                // level of the Uniform-Split boxes (log2 of the divisions)
   double active_volume;      // volume of the regions evaluated in the last iteration
   int32_t keep_leaves;       // append finished boxes to the leaf log
@@ -141,6 +143,7 @@ struct TraceRec {
   int32_t it, trigger, probes, search_ok;
   int64_t s, n_relerr_active, n_survivors;
   double v, e, vf, ef, threshold, direction_changes;
+  int32_t probe_passes, reserved;
 };
 
 // Per-block partial results written by the evaluate kernel.
@@ -156,16 +159,27 @@ struct CountPartial {
   NSum va, ea, finvol;  // V, E and volume summed over the finished regions
 };
 
-// Threshold-Classify probes take the search kProbeDepth steps per pass: the
-// tree of the coming thresholds has kProbeNodes nodes, and the sorted
-// thresholds cut the errors into kProbeBuckets buckets.
-constexpr int kProbeDepth = 3;
-constexpr int kProbeNodes = (1 << kProbeDepth) - 1;
-constexpr int kProbeBuckets = kProbeNodes + 1;
+// Threshold-Classify probes.  From the current threshold t, a run of steps
+// of the search that keep one direction visits the thresholds of a ray:
+// halfway to min E again and again (down) or to max E (up).  One probe pass
+// evaluates kProbeRay thresholds of each ray plus t itself, kProbeThr sorted
+// thresholds that cut the errors into kProbeBuckets buckets; the rel-err
+// finished regions form one more bin.  Each bin sums its errors exactly, as
+// integers: E / e_b in fixed point with kProbeFrac fraction bits (errors at
+// or above the budget e_b are counted as e_b, which fails the accuracy
+// requirement either way).
+constexpr int kProbeRay = 8;
+constexpr int kProbeThr = 2 * kProbeRay + 1;
+constexpr int kProbeBuckets = kProbeThr + 1;
+constexpr int kProbeBins = kProbeBuckets + 1;
+constexpr int kProbeFrac = 88;
+constexpr int kProbeThreads = 128;
 
-struct ProbePartial {
-  NSum sum[kProbeBuckets + 1];      // E of the rel-err actives per bucket; last: E of the rel-err finished
-  long long cnt[kProbeBuckets];     // rel-err actives per bucket
+// One bin of a probe pass, accumulated over all blocks by integer atomics
+// (order-independent, so exact and deterministic): the 128-bit fixed-point
+// error sum (lo, hi) and the region count.
+struct ProbeAcc {
+  unsigned long long lo, hi, cnt;
 };
 
 // Rule data passed by value to the evaluate kernels.
@@ -214,7 +228,7 @@ struct LoopArgs {
   Ctrl* ctrl;
   const IntegrandParams* prm;
   EvalPartial* eval_part;
-  ProbePartial* probe_part;
+  ProbeAcc* probe_acc;     // kProbeBins bins, zero between probe passes
   CountPartial* count_part;
   TraceRec* trace;
   int trace_cap;
