@@ -398,7 +398,7 @@ __device__ inline int threshold_step(Ctrl& c, long long n_active, double e_abar)
   c.total_probes += 1;
   long long s_abar = c.s - n_active;
   int dir;
-  if ((double)s_abar > 0.5 * (double)c.s) {       // memory requirement
+  if (2 * s_abar > c.s) {                          // memory requirement, s_abar > 0.5 s
     if (e_abar <= c.Pmax * c.e_b) {               // accuracy requirement
       c.search_ok = 1;
       return 0;

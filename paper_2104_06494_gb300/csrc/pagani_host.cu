@@ -118,42 +118,74 @@ __device__ __forceinline__ void probe_fixed(unsigned long long eb, unsigned long
   }
 }
 
+// The probe's thresholds: node k of the coming steps of the search from t.
+// Nodes 0..kProbeTree-1 form a binary tree in heap order (children 2k+1 one
+// step down, 2k+2 one step up); the kProbeExt nodes after them continue the
+// all-down path past the tree's depth, the last kProbeExt the all-up path.
+constexpr int kProbeExt = kProbeRay - kProbeDepth + 1;
+__device__ __forceinline__ double probe_node(int k, double t, double emin, double emax) {
+  if (k < kProbeTree) {
+    // directions from the root: the bits of k + 1 below its leading one
+    const int x = k + 1;
+    for (int b = 30 - __clz(x); b >= 0; --b) t = search_next(t, ((x >> b) & 1) ? 1 : -1, emin, emax);
+    return t;
+  }
+  const bool up = k >= kProbeTree + kProbeExt;
+  const int steps = kProbeDepth + (k - kProbeTree - (up ? kProbeExt : 0));
+  for (int i = 0; i < steps; ++i) t = search_next(t, up ? 1 : -1, emin, emax);
+  return t;
+}
+// The node after k when the search moves in direction d, or -1 when that
+// threshold is not among the pass's nodes.
+__device__ __forceinline__ int probe_next(int k, int d) {
+  constexpr int kLeft = kProbeTree / 2, kRight = kProbeTree - 1;  // the all-down and all-up leaves
+  if (k < kLeft) return d < 0 ? 2 * k + 1 : 2 * k + 2;
+  if (k < kProbeTree) return k == kLeft && d < 0 ? kProbeTree : (k == kRight && d > 0 ? kProbeTree + kProbeExt : -1);
+  if (k < kProbeTree + kProbeExt) return d < 0 && k + 1 < kProbeTree + kProbeExt ? k + 1 : -1;
+  return d > 0 && k + 1 < kProbeNodes ? k + 1 : -1;
+}
+
 // Threshold-Classify (Algorithm 3): one probe pass takes the search from the
-// current threshold t through up to kProbeRay + 1 of its steps.  A step that
-// keeps the direction of the one before moves t halfway towards min E (down)
-// or max E (up) again, so a run of steps in one direction visits the
-// thresholds of one of two rays from t, computed here with search_next, the
-// function threshold_step moves by.  Every block places each region's error
-// among the kProbeThr sorted thresholds (down ray reversed, t, up ray) and
-// adds it to its bucket (rel-err actives) or to the finished bin; the bins
-// hold exact integer sums (probe_fixed) and counts, combined over the grid by
-// integer atomics.  The last block then takes the steps of Algorithm 3 with
-// those totals: at a threshold, the candidate actives are the rel-err actives
-// of the buckets above it and e_abar is the error of the buckets below it
-// plus the rel-err finished.  The pass ends when the search ends, changes
-// direction after its first step, or reaches the end of a ray; a following
-// pass starts from the threshold it left in c.t.
+// current threshold t through as many of its steps as the pass's thresholds
+// cover: any kProbeDepth steps, and up to kProbeRay steps that keep one
+// direction.  The thresholds are computed here with search_next, the
+// function threshold_step moves by, so they are the bits the search arrives
+// at.  Every block places each region's error among the sorted thresholds
+// and adds it to its bucket (rel-err actives) or to the finished bin; the
+// bins hold exact integer sums (probe_fixed) and counts, combined over the
+// grid by integer atomics.  The last block then takes the steps of
+// Algorithm 3 with those totals: at a threshold, the candidate actives are
+// the rel-err actives of the buckets above it and e_abar is the error of the
+// buckets below it plus the rel-err finished.  The pass ends when the search
+// ends or moves to a threshold it does not cover; a following pass starts
+// from the threshold it left in c.t.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   Ctrl& c = *A.ctrl;
   constexpr int NW = THREADS / 32;
+  static_assert(kProbeNodes <= 31 && THREADS >= 32, "one warp computes the nodes; 32 sorted entries");
+  __shared__ unsigned long long nodeb[kProbeNodes];    // node k's threshold bits
+  __shared__ int node_at[kProbeNodes];                 // the first sorted threshold equal to node k's
   __shared__ unsigned long long thr[32];               // sorted thresholds, padded with all ones
   __shared__ ulonglong2 hist[kProbeBins * THREADS];    // per thread: (lo, hi | count << 44) per bin
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x < 2) {
-    const int dir = threadIdx.x ? 1 : -1;
-    double t = c.t;
-    for (int k = 1; k <= kProbeRay; ++k) {
-      t = search_next(t, dir, c.emin, c.emax);
-      thr[kProbeRay + dir * k] = ebits(t);
-    }
-  } else if (threadIdx.x == 2) {
-    thr[kProbeRay] = ebits(c.t);
-  } else if (threadIdx.x >= kProbeThr && threadIdx.x < 32) {
-    thr[threadIdx.x] = ~0ull;
-  }
+  if (threadIdx.x < kProbeNodes) nodeb[threadIdx.x] = ebits(probe_node(threadIdx.x, c.t, c.emin, c.emax));
 #pragma unroll
   for (int b = 0; b < kProbeBins; ++b) hist[b * THREADS + threadIdx.x] = make_ulonglong2(0ull, 0ull);
+  __syncthreads();
+  if (threadIdx.x < kProbeNodes) {
+    // rank among the nodes (equal values by node index)
+    const unsigned long long x = nodeb[threadIdx.x];
+    int below = 0, r = 0;
+    for (int j = 0; j < kProbeNodes; ++j) {
+      below += nodeb[j] < x;
+      r += nodeb[j] < x || (nodeb[j] == x && j < (int)threadIdx.x);
+    }
+    thr[r] = x;
+    node_at[threadIdx.x] = below;
+  } else if (threadIdx.x < 32) {
+    thr[threadIdx.x] = ~0ull;
+  }
   __syncthreads();
   const unsigned long long e_bits = ebits(c.e_b);
   int B;  // e_b = 2^B
@@ -163,33 +195,45 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   const uint8_t* __restrict__ act = A.pool.act;
   const double* __restrict__ E = A.pool.E;
   ulonglong2* mine = hist + threadIdx.x;
-  constexpr int U = 4;  // loads in flight per thread
+  auto add = [&](unsigned long long eb, int a) {
+    // number of thresholds at or below E (branch-free search of 32 entries)
+    int k = thr[15] <= eb ? 16 : 0;
+    k += thr[k + 7] <= eb ? 8 : 0;
+    k += thr[k + 3] <= eb ? 4 : 0;
+    k += thr[k + 1] <= eb ? 2 : 0;
+    k += thr[k] <= eb ? 1 : 0;
+    const int bin = a ? k : kProbeBuckets;
+    unsigned long long lo, hi;
+    probe_fixed(eb, e_bits, B, lo, hi);
+    ulonglong2 h = mine[bin * THREADS];
+    h.x += lo;
+    h.y += hi + (h.x < lo ? 1ull : 0ull) + (1ull << 44);
+    mine[bin * THREADS] = h;
+  };
+  // regions in pairs (one 16-byte load of two errors, one 2-byte load of two
+  // classification bytes), U pairs per thread in flight; E and act hold
+  // cap >= s + 1 entries for odd s (cap is a multiple of 4096), and the
+  // entry past s is masked
+  constexpr int U = 4;
+  const int64_t np = (s + 1) / 2;
   const int64_t stride = (int64_t)gridDim.x * THREADS;
-  for (int64_t i0 = (int64_t)blockIdx.x * THREADS + threadIdx.x; i0 < s; i0 += U * stride) {
-    unsigned long long eb[U];
-    int a[U];
+  const double2* __restrict__ E2 = reinterpret_cast<const double2*>(E);
+  const uint16_t* __restrict__ act2 = reinterpret_cast<const uint16_t*>(act);
+  for (int64_t p0 = (int64_t)blockIdx.x * THREADS + threadIdx.x; p0 < np; p0 += U * stride) {
+    double2 e2[U];
+    unsigned a2[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + u * stride;
-      eb[u] = i < s ? ebits(E[i]) : 0ull;
-      a[u] = i < s ? (int)act[i] : -1;
+      const int64_t p = p0 + u * stride;
+      e2[u] = p < np ? E2[p] : make_double2(0.0, 0.0);
+      a2[u] = p < np ? (unsigned)act2[p] : 0u;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (a[u] < 0) continue;
-      // number of thresholds at or below E (branch-free search of 32 entries)
-      int k = thr[15] <= eb[u] ? 16 : 0;
-      k += thr[k + 7] <= eb[u] ? 8 : 0;
-      k += thr[k + 3] <= eb[u] ? 4 : 0;
-      k += thr[k + 1] <= eb[u] ? 2 : 0;
-      k += thr[k] <= eb[u] ? 1 : 0;
-      const int bin = a[u] ? k : kProbeBuckets;
-      unsigned long long lo, hi;
-      probe_fixed(eb[u], e_bits, B, lo, hi);
-      ulonglong2 h = mine[bin * THREADS];
-      h.x += lo;
-      h.y += hi + (h.x < lo ? 1ull : 0ull) + (1ull << 44);
-      mine[bin * THREADS] = h;
+      const int64_t p = p0 + u * stride;
+      if (p >= np) break;
+      add(ebits(e2[u].x), (int)(a2[u] & 0xff));
+      if (2 * p + 1 < s) add(ebits(e2[u].y), (int)(a2[u] >> 8));
     }
   }
   __syncthreads();
@@ -213,46 +257,58 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
       cnt += c2;
     }
     if (lane == 0 && cnt != 0ull) {
+      constexpr unsigned long long M44 = (1ull << 44) - 1;
       ProbeAcc& g = A.probe_acc[b];
-      const unsigned long long old = atomicAdd(&g.lo, lo);
-      atomicAdd(&g.hi, hi + (old + lo < old ? 1ull : 0ull));
+      atomicAdd(&g.limb[0], lo & M44);
+      atomicAdd(&g.limb[1], (lo >> 44) | ((hi & ((1ull << 24) - 1)) << 20));
+      atomicAdd(&g.limb[2], hi >> 24);
       atomicAdd(&g.cnt, cnt);
     }
   }
   if (!last_block_arrived(&c.ticket_probe)) return;
-  if (threadIdx.x != 0) return;
-  unsigned long long slo[kProbeBins], shi[kProbeBins], scnt[kProbeBins];
-  for (int b = 0; b < kProbeBins; ++b) {
-    slo[b] = __ldcg(&A.probe_acc[b].lo);
-    shi[b] = __ldcg(&A.probe_acc[b].hi);
-    scnt[b] = __ldcg(&A.probe_acc[b].cnt);
-    A.probe_acc[b].lo = A.probe_acc[b].hi = A.probe_acc[b].cnt = 0ull;  // zero for the next pass
+  // the grid's bins, then at every threshold (in parallel) the candidate
+  // actives and e_abar; thread 0 then takes the steps
+  __shared__ unsigned long long blo[kProbeBins], bhi[kProbeBins], bcnt[kProbeBins];
+  __shared__ long long n_at[kProbeNodes];
+  __shared__ double e_at[kProbeNodes];
+  if (threadIdx.x < kProbeBins) {
+    ProbeAcc& g = A.probe_acc[threadIdx.x];
+    const unsigned long long l0 = __ldcg(&g.limb[0]), l1 = __ldcg(&g.limb[1]), l2 = __ldcg(&g.limb[2]);
+    bcnt[threadIdx.x] = __ldcg(&g.cnt);
+    g.limb[0] = g.limb[1] = g.limb[2] = g.cnt = 0ull;  // zero for the next pass
+    const unsigned long long a = l1 << 44;
+    const unsigned long long lo = l0 + a;
+    blo[threadIdx.x] = lo;
+    bhi[threadIdx.x] = (l1 >> 20) + (l2 << 24) + (lo < a ? 1ull : 0ull);
   }
+  __syncthreads();
+  if (threadIdx.x < kProbeNodes) {
+    // at the sorted threshold j: the candidate actives are the rel-err
+    // actives of buckets j+1.., e_abar the error of buckets 0..j plus the
+    // rel-err finished
+    const int j = threadIdx.x;
+    long long na = 0;
+    for (int b = j + 1; b < kProbeBuckets; ++b) na += (long long)bcnt[b];
+    unsigned long long lo = blo[kProbeBuckets], hi = bhi[kProbeBuckets];
+    for (int b = 0; b <= j; ++b) {
+      lo += blo[b];
+      hi += bhi[b] + (lo < blo[b] ? 1ull : 0ull);
+    }
+    n_at[j] = na;
+    e_at[j] = scalbn(fma(__ull2double_rn(hi), 0x1p64, __ull2double_rn(lo)), B - kProbeFrac);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   c.passes += 1;
   c.total_passes += 1;
-  int pos = kProbeRay, ray = 0, cont = 1;
+  int k = 0, cont = 1;
   for (;;) {
-    // the first sorted threshold equal to c.t: the regions at or above it
-    // are the candidate actives
-    const unsigned long long tb = ebits(c.t);
-    int j = 0;
-    while (j < kProbeThr - 1 && thr[j] != tb) ++j;
-    long long n_act = 0;
-    for (int b = j + 1; b < kProbeBuckets; ++b) n_act += (long long)scnt[b];
-    unsigned long long lo = slo[kProbeBuckets], hi = shi[kProbeBuckets];
-    for (int b = 0; b <= j; ++b) {
-      lo += slo[b];
-      hi += shi[b] + (lo < slo[b] ? 1ull : 0ull);
-    }
-    const double e_abar = scalbn(fma(__ull2double_rn(hi), 0x1p64, __ull2double_rn(lo)), B - kProbeFrac);
-    cont = threshold_step(c, n_act, e_abar);
+    const int j = node_at[k];
+    cont = threshold_step(c, n_at[j], e_at[j]);
     if (!cont) break;
-    const int d = c.last_dir;
-    if (ray == 0) ray = d;
-    if (d != ray) break;                                    // off the rays: the next pass starts at c.t
-    if (pos + d < 0 || pos + d > 2 * kProbeRay) break;      // past the end of the ray
-    pos += d;
-    if (ebits(c.t) != thr[pos]) {  // the step must land on the ray's next threshold, bit for bit
+    k = probe_next(k, c.last_dir);
+    if (k < 0) break;  // not among this pass's thresholds: the next pass starts at c.t
+    if (ebits(c.t) != nodeb[k]) {  // the step must land on the node's threshold, bit for bit
       c.watchdog = 3;
       c.search_ok = 0;
       cont = 0;
@@ -267,18 +323,87 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
 // ------------------------------------------- finished sums + survivor count
 // The final classification of every region (Evaluate's Rel-Err-Classify
 // byte and, after a successful threshold search, E >= t), the survivors of
-// every 256-region warp slice of a tile, and per block the sums of V, E and
-// the volume of the finished regions.  The last block scans the tile counts
-// and takes the decisions that follow Threshold-Classify in Algorithm 2
-// (v_f, e_f, the memory check).
+// every 256-region warp slice of a tile, and the sums of V, E and the volume
+// of the finished regions.  The last block takes the decisions that follow
+// Threshold-Classify in Algorithm 2 (v_f, e_f, the memory check).
 //
-// Built for bandwidth: a thread takes ITEMS contiguous regions of a tile
-// (one 8-byte load of their classification bytes), the bytes of kCountAhead
-// tiles are requested before the first is used, every warp stores its own
-// slice count (no block-wide barrier per tile), and V, E and the levels are
-// read only where they are needed: E of the rel-err actives after a search,
-// V, E and levels of the finished.
+// Built for bandwidth: each block owns a contiguous range of tiles; a thread
+// takes ITEMS contiguous regions of a tile (one 8-byte load of their
+// classification bytes), the bytes of kCountAhead tiles are requested before
+// the first is used, every warp stores its own slice count, and V, E and the
+// levels are read only where they are needed (E of the rel-err actives after
+// a search; V, E and levels of the finished).  Each block scans its own
+// tiles' counts (offsets within the block) and publishes its survivor total;
+// the last block scans only the block totals.  E and the volume of the
+// finished regions are summed exactly as integers (E as a fixed-point
+// multiple of max E rounded up to a power of two, 2^-kCountEFrac of it; a
+// volume 2^-L as 2^(127 - L), exact for L <= 127), so only V takes an FP64
+// add per finished region.
 constexpr int kCountAhead = 8;
+constexpr int kCountEFrac = 96;
+
+// add x = m 2^sh (m < 2^53) to the 128-bit (lo, hi); sh < 128
+__device__ __forceinline__ void add128_shifted(unsigned long long& lo, unsigned long long& hi, unsigned long long m,
+                                               int sh) {
+  unsigned long long xl, xh;
+  if (sh >= 64) {
+    xl = 0ull;
+    xh = m << (sh - 64);
+  } else if (sh > 0) {
+    xl = m << sh;
+    xh = m >> (64 - sh);
+  } else if (sh > -64) {
+    xl = m >> (-sh);
+    xh = 0ull;
+  } else {
+    return;
+  }
+  lo += xl;
+  hi += xh + (lo < xl ? 1ull : 0ull);
+}
+
+// E (0 <= E <= 2^X) as a multiple of 2^(X - kCountEFrac), truncated, added to (lo, hi)
+__device__ __forceinline__ void add_e_fixed(unsigned long long& lo, unsigned long long& hi, double e, int X) {
+  const unsigned long long b = ebits(e);
+  int ex = (int)(b >> 52);
+  unsigned long long m = b & ((1ull << 52) - 1);
+  if (ex) m |= 1ull << 52;
+  else ex = 1;
+  add128_shifted(lo, hi, m, ex - 1075 + kCountEFrac - X);
+}
+
+// 128-bit sums over a warp (valid on lane 0)
+__device__ __forceinline__ void warp_sum128(unsigned long long& lo, unsigned long long& hi) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, off);
+    const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, off);
+    lo += l2;
+    hi += h2 + (lo < l2 ? 1ull : 0ull);
+  }
+}
+
+// (lo, hi) added to three 44-bit-limb accumulators by independent atomics
+__device__ __forceinline__ void atomic_add_limbs(unsigned long long* limb, unsigned long long lo, unsigned long long hi) {
+  constexpr unsigned long long M44 = (1ull << 44) - 1;
+  atomicAdd(&limb[0], lo & M44);
+  atomicAdd(&limb[1], (lo >> 44) | ((hi & ((1ull << 24) - 1)) << 20));
+  atomicAdd(&limb[2], hi >> 24);
+}
+// the 128-bit value of three limb accumulators (read, then zeroed)
+__device__ __forceinline__ void take_limbs(unsigned long long* limb, unsigned long long& lo, unsigned long long& hi) {
+  const unsigned long long l0 = __ldcg(&limb[0]), l1 = __ldcg(&limb[1]), l2 = __ldcg(&limb[2]);
+  limb[0] = limb[1] = limb[2] = 0ull;
+  const unsigned long long a = l1 << 44;
+  lo = l0 + a;
+  hi = (l1 >> 20) + (l2 << 24) + (lo < a ? 1ull : 0ull);
+}
+
+// a 128-bit integer times 2^e as a double (nearly exact: two roundings)
+__device__ __forceinline__ double fixed_to_double(unsigned long long lo, unsigned long long hi, int e) {
+  return scalbn(fma(__ull2double_rn(hi), 0x1p64, __ull2double_rn(lo)), e);
+}
+
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   static_assert(ITEMS == 8 && THREADS / 32 == kTileWarps, "one 8-byte load per thread, one slice per warp");
@@ -288,6 +413,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     return;
   }
   constexpr int TILE = THREADS * ITEMS;
+  constexpr int NW = THREADS / 32;
   const int64_t s = c.s;
   const int n = A.pool.n;
   const int64_t cap = A.pool.cap;
@@ -296,28 +422,36 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   const double* __restrict__ E = A.pool.E;
   uint8_t* __restrict__ act = A.pool.act;
   const int64_t ntiles = (s + TILE - 1) / TILE;
+  const int64_t tpb = (ntiles + gridDim.x - 1) / gridDim.x;  // tiles per block
+  const int64_t t_beg = (int64_t)blockIdx.x * tpb;
+  const int64_t t_end = t_beg + tpb < ntiles ? t_beg + tpb : ntiles;
   const bool searched = c.search_ok != 0;
   const unsigned long long tb = ebits(c.t);
+  // E's fixed-point scale: max E rounded up to a power of two, 2^X
+  const unsigned long long mb = ebits(c.emax);
+  const int X = (mb >> 52) ? (int)(mb >> 52) - 1023 + ((mb & ((1ull << 52) - 1)) ? 1 : 0) : -1022;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ long long shl[2 * (THREADS / 32)];
-  __shared__ NSum shn[3 * THREADS + 3];
-  // a thread adds its finished regions of a tile plainly (relative error at
-  // most (ITEMS - 1) u) and that partial into Neumaier accumulators
-  NSum acc3[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};  // finished V, E and volume
-  for (int64_t t0 = blockIdx.x; t0 < ntiles; t0 += (int64_t)gridDim.x * kCountAhead) {
+  __shared__ long long shl[2 * NW];
+  __shared__ NSum shn[THREADS + 1];
+  __shared__ unsigned long long shu[4 * NW];
+  // a thread adds its finished V of a tile plainly (relative error at most
+  // (ITEMS - 1) u) and that partial into a Neumaier accumulator
+  NSum accv = {0.0, 0.0};
+  unsigned long long elo = 0ull, ehi = 0ull, vlo = 0ull, vhi = 0ull;  // finished E and volume
+  for (int64_t t0 = t_beg; t0 < t_end; t0 += kCountAhead) {
     unsigned long long bytes[kCountAhead];
 #pragma unroll
     for (int u = 0; u < kCountAhead; ++u) {
-      const int64_t tile = t0 + (int64_t)u * gridDim.x;
+      const int64_t tile = t0 + u;
       const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * ITEMS;
       // the act array holds cap >= s entries, cap a multiple of 4096: the
       // 8-byte load stays inside it; bytes past s are masked below
-      bytes[u] = tile < ntiles && i0 < s ? *reinterpret_cast<const unsigned long long*>(act + i0) : 0ull;
+      bytes[u] = tile < t_end && i0 < s ? *reinterpret_cast<const unsigned long long*>(act + i0) : 0ull;
     }
 #pragma unroll 1
     for (int u = 0; u < kCountAhead; ++u) {
-      const int64_t tile = t0 + (int64_t)u * gridDim.x;
-      if (tile >= ntiles) break;
+      const int64_t tile = t0 + u;
+      if (tile >= t_end) break;
       const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * ITEMS;
       const int valid = i0 < s ? (s - i0 < ITEMS ? (int)(s - i0) : ITEMS) : 0;
       int a0[ITEMS];
@@ -356,17 +490,15 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
 #pragma unroll
           for (int r = 0; r < ITEMS; ++r) Lr[r] += (int)((lv >> (8 * r)) & 0xff);
         }
-        double tv = 0.0, te = 0.0, tf = 0.0;
+        double tv = 0.0;
 #pragma unroll
         for (int r = 0; r < ITEMS; ++r)
           if (r < valid && !actv[r]) {
             tv += vv[r];
-            te += ee[r];
-            tf += pow2_neg(Lr[r]);
+            add_e_fixed(elo, ehi, ee[r], X);
+            add128_shifted(vlo, vhi, 1ull, 127 - Lr[r]);
           }
-        nadd(acc3[0], tv);
-        nadd(acc3[1], te);
-        nadd(acc3[2], tf);
+        nadd(accv, tv);
         if (searched)  // regions finished by the threshold: the split reads the byte back
 #pragma unroll
           for (int r = 0; r < ITEMS; ++r)
@@ -376,49 +508,84 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
       if (lane == 0) A.pool.tile_count[tile * kTileWarps + warp] = wc;
     }
   }
-  // a block without tiles holds exact zeros: it skips the FP64 shuffles (a
-  // warp-wide FP64 instruction costs the SM's FP64 pipe 16 cycles) and the
-  // last block reads only the partials of blocks that had tiles, which
-  // leaves every sum bit for bit unchanged
-  const int64_t nparts = ntiles < (int64_t)gridDim.x ? ntiles : (int64_t)gridDim.x;
-  if ((int64_t)blockIdx.x < nparts) {
-    nsum_block_reduce_staged<THREADS, 3>(acc3, shn);
-    if (threadIdx.x == 0) {
-      A.count_part[blockIdx.x].va = acc3[0];
-      A.count_part[blockIdx.x].ea = acc3[1];
-      A.count_part[blockIdx.x].finvol = acc3[2];
-    }
-  }
-  if (!last_block_arrived(&c.ticket_count)) return;
-
-  // exclusive scan of the tile counts (each the sum of its warp slices):
-  // each thread a contiguous chunk of tiles, the chunk sums scanned by warp
-  // shuffles
-  const int64_t per = (ntiles + THREADS - 1) / THREADS;
-  const int64_t q0 = threadIdx.x * per, q1 = q0 + per < ntiles ? q0 + per : ntiles;
+  __syncthreads();  // the block's slice counts are written
+  // survivors before each of the block's tiles, within the block: each
+  // thread a contiguous chunk of tiles, the chunk sums scanned by shuffles
   auto tile_total = [&](int64_t t) {
     const int4* w = reinterpret_cast<const int4*>(A.pool.tile_count + t * kTileWarps);
     const int4 a = w[0], b = w[1];
     return (long long)a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w;
   };
+  const int64_t nt = t_end > t_beg ? t_end - t_beg : 0;
+  const int64_t per = (nt + THREADS - 1) / THREADS;
+  const int64_t q0 = t_beg + (int64_t)threadIdx.x * per, q1 = q0 + per < t_end ? q0 + per : t_end;
   long long acc = 0;
   for (int64_t t = q0; t < q1; ++t) acc += tile_total(t);
-  long long n_surv = 0;
-  long long run = block_exclusive_scan<THREADS>(acc, shl, &n_surv);
+  long long blk_surv = 0;
+  long long run = block_exclusive_scan<THREADS>(acc, shl, &blk_surv);
   for (int64_t t = q0; t < q1; ++t) {
     const long long x = tile_total(t);
     A.pool.tile_offset[t] = run;
     run += x;
   }
-  NSum p3[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
-  for (int64_t b = threadIdx.x; b < nparts; b += THREADS) {
-    p3[0] = ncomb(p3[0], A.count_part[b].va);
-    p3[1] = ncomb(p3[1], A.count_part[b].ea);
-    p3[2] = ncomb(p3[2], A.count_part[b].finvol);
+  // the block's finished V (compensated), and E and volume (integers, added
+  // to the grid totals in the control block by atomics)
+  if (nt > 0) {
+    NSum v1[1] = {accv};
+    nsum_block_reduce_staged<THREADS, 1>(v1, shn);
+    warp_sum128(elo, ehi);
+    warp_sum128(vlo, vhi);
+    if (lane == 0) {
+      shu[warp] = elo;
+      shu[NW + warp] = ehi;
+      shu[2 * NW + warp] = vlo;
+      shu[3 * NW + warp] = vhi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < NW; ++w) {
+        elo += shu[w];
+        ehi += shu[NW + w] + (elo < shu[w] ? 1ull : 0ull);
+        vlo += shu[2 * NW + w];
+        vhi += shu[3 * NW + w] + (vlo < shu[2 * NW + w] ? 1ull : 0ull);
+      }
+      if (elo | ehi) atomic_add_limbs(c.fin_e_fixed, elo, ehi);
+      if (vlo | vhi) atomic_add_limbs(c.fin_vol_fixed, vlo, vhi);
+      A.count_part[blockIdx.x].va = v1[0];
+      A.count_part[blockIdx.x].n_surv = blk_surv;
+    }
+  } else if (threadIdx.x == 0) {
+    A.count_part[blockIdx.x].va = {0.0, 0.0};
+    A.count_part[blockIdx.x].n_surv = 0;
   }
-  nsum_block_reduce_staged<THREADS, 3>(p3, shn);
+  if (!last_block_arrived(&c.ticket_count)) return;
+
+  // survivors before each block (the split adds them to the block's tile
+  // offsets), and the grid's finished sums
+  const int G = (int)gridDim.x;
+  const int64_t nparts = (ntiles + tpb - 1) / tpb;  // blocks that had tiles
+  const int per_b = (G + THREADS - 1) / THREADS;
+  const int b0 = threadIdx.x * per_b, b1 = b0 + per_b < G ? b0 + per_b : G;
+  long long bacc = 0;
+  for (int b = b0; b < b1; ++b) bacc += __ldcg(&A.count_part[b].n_surv);
+  long long n_surv = 0;
+  long long brun = block_exclusive_scan<THREADS>(bacc, shl, &n_surv);
+  for (int b = b0; b < b1; ++b) {
+    const long long x = __ldcg(&A.count_part[b].n_surv);
+    A.count_part[b].surv_before = brun;
+    brun += x;
+  }
+  NSum p1[1] = {{0.0, 0.0}};
+  for (int64_t b = threadIdx.x; b < nparts; b += THREADS) p1[0] = ncomb(p1[0], A.count_part[b].va);
+  nsum_block_reduce_staged<THREADS, 1>(p1, shn);
   if (threadIdx.x != 0) return;
-  const NSum tva = p3[0], tea = p3[1], tfv = p3[2];
+  const NSum tva = p1[0];
+  unsigned long long el, eh, vl, vh;
+  take_limbs(c.fin_e_fixed, el, eh);  // (and zero them for the next iteration)
+  take_limbs(c.fin_vol_fixed, vl, vh);
+  const double tea = fixed_to_double(el, eh, X - kCountEFrac);
+  const NSum tfv = {fixed_to_double(0ull, vh, -127), fixed_to_double(vl, 0ull, -127)};
+  c.count_tpb = tpb;
   c.n_surv = n_surv;
   const bool tr_ok = c.trace_on && c.it - 1 < A.trace_cap;
   TraceRec* tr = tr_ok ? &A.trace[c.it - 1] : nullptr;
@@ -442,7 +609,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     // v - sum V.A and e - sum E.A of Algorithm 2, summed over the finished
     // regions directly
     const double vf_new = c.vf + nval(tva);
-    const double ef_new = c.ef + nval(tea);
+    const double ef_new = c.ef + tea;
     if (tr) {
       tr->vf = vf_new;
       tr->ef = ef_new;
@@ -508,7 +675,9 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
   __shared__ int shr[THREADS / 32];
   int bad = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long tile_base = A.pool.tile_offset[tile];
+    // survivors before the tile: within its block of the count kernel, plus
+    // before that block
+    const long long tile_base = A.pool.tile_offset[tile] + A.count_part[tile / c.count_tpb].surv_before;
     // phase 1: every item's classification (stored by the count kernel) and
     // rank; phase 2: the copies, whose loads then overlap across items
     // instead of following one barrier each
@@ -927,6 +1096,7 @@ struct Launch {
   size_t eval_smem;
   int mgmt_grid;
   int probe_grid;
+  int count_grid;
 };
 
 static int launch_config(const FamilyKernels& fk, int n, Launch* L) {
@@ -941,8 +1111,10 @@ static int launch_config(const FamilyKernels& fk, int n, Launch* L) {
   if (L->eval_grid > w.max_grid) L->eval_grid = w.max_grid;
   L->mgmt_grid = w.sms * 2;
   if (L->mgmt_grid > w.max_grid) L->mgmt_grid = w.max_grid;
-  L->probe_grid = w.sms * 4;
+  L->probe_grid = w.sms * 5;
   if (L->probe_grid > w.max_grid) L->probe_grid = w.max_grid;
+  L->count_grid = w.sms * 2;
+  if (L->count_grid > w.max_grid) L->count_grid = w.max_grid;
   return 0;
 }
 
@@ -1033,7 +1205,7 @@ static int build_graph(int fam, int n, int degree, const EvalRule& rule, const L
   PG_CK(add_while(&wprobe, body, &nev, 1, hp, &pbody));
   PG_CK(add_kernel(&nprobe, pbody, nullptr, 0, (const void*)&k_probe<kProbeThreads>, L.probe_grid, kProbeThreads,
                    0, margs));
-  PG_CK(add_kernel(&ncount, body, &wprobe, 1, (const void*)&k_count<kMgmtThreads, kMgmtItems>, L.mgmt_grid,
+  PG_CK(add_kernel(&ncount, body, &wprobe, 1, (const void*)&k_count<kMgmtThreads, kMgmtItems>, L.count_grid,
                    kMgmtThreads, 0, margs));
   PG_CK(add_kernel(&nsplit, body, &ncount, 1, (const void*)&k_split<kMgmtThreads, kMgmtItems>, L.mgmt_grid,
                    kMgmtThreads, 0, margs));
@@ -1201,7 +1373,7 @@ static int integrate_locked(int n, int fam, const double* params, const double* 
         }
       }
       PG_CK(cudaEventRecord(ev[3], st));
-      k_count<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
+      k_count<kMgmtThreads, kMgmtItems><<<L.count_grid, kMgmtThreads, 0, st>>>(args);
       PG_CK(cudaGetLastError());
       PG_CK(cudaEventRecord(ev[4], st));
       k_split<kMgmtThreads, kMgmtItems><<<L.mgmt_grid, kMgmtThreads, 0, st>>>(args);
@@ -1381,7 +1553,8 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   if (e != cudaSuccess || occ < 1) return out->status = fail(PAGANI_ERR_CUDA, "evaluate kernel does not fit");
   Lc.eval_grid = sms * occ < max_grid ? sms * occ : max_grid;
   Lc.mgmt_grid = sms * 2;
-  Lc.probe_grid = sms * 4;
+  Lc.probe_grid = sms * 5;
+  Lc.count_grid = sms * 2;
   const int64_t cap = ((max_regions + 4095) / 4096) * 4096;
   const NoallocLayout L = noalloc_layout(cap, n, max_grid);
   LoopArgs a;
@@ -1458,7 +1631,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
         if (!h.search_cont) break;
       }
     }
-    k_count<kMgmtThreads, kMgmtItems><<<Lc.mgmt_grid, kMgmtThreads, 0, st>>>(a);
+    k_count<kMgmtThreads, kMgmtItems><<<Lc.count_grid, kMgmtThreads, 0, st>>>(a);
     PG_CK(cudaGetLastError());
     k_split<kMgmtThreads, kMgmtItems><<<Lc.mgmt_grid, kMgmtThreads, 0, st>>>(a);
     PG_CK(cudaGetLastError());

@@ -131,6 +131,11 @@ struct Ctrl {
   int32_t total_probes;      // threshold probes (search steps) over the whole call
   int32_t passes;            // probe passes (k_probe launches) this iteration
   int32_t total_passes;      // probe passes over the whole call
+  int64_t count_tpb;         // tiles per block of the count kernel (the split locates a tile's block)
+  // count kernel: finished E and volume of this iteration as 128-bit fixed
+  // point in limbs of 44 bits (value = limb[0] + limb[1] 2^44 + limb[2] 2^88)
+  unsigned long long fin_e_fixed[3];
+  unsigned long long fin_vol_fixed[3];
   int32_t l0;                // level of the Uniform-Split boxes (log2 of the divisions)
   double active_volume;      // volume of the regions evaluated in the last iteration
   int32_t keep_leaves;       // append finished boxes to the leaf log
@@ -156,30 +161,37 @@ struct EvalPartial {
 };
 
 struct CountPartial {
-  NSum va, ea, finvol;  // V, E and volume summed over the finished regions
+  NSum va;                 // V summed over the block's finished regions
+  long long n_surv;        // the block's survivors
+  long long surv_before;   // survivors of the blocks before it (set by the last block)
 };
 
-// Threshold-Classify probes.  From the current threshold t, a run of steps
-// of the search that keep one direction visits the thresholds of a ray:
-// halfway to min E again and again (down) or to max E (up).  One probe pass
-// evaluates kProbeRay thresholds of each ray plus t itself, kProbeThr sorted
-// thresholds that cut the errors into kProbeBuckets buckets; the rel-err
-// finished regions form one more bin.  Each bin sums its errors exactly, as
-// integers: E / e_b in fixed point with kProbeFrac fraction bits (errors at
-// or above the budget e_b are counted as e_b, which fails the accuracy
+// Threshold-Classify probes.  One probe pass evaluates the thresholds the
+// search can reach from the current threshold t in its next steps: every
+// path of kProbeDepth steps (a binary tree: each step moves t halfway to min
+// E or to max E), and beyond that the two paths that keep one direction, up
+// to kProbeRay steps (runs of same-direction steps are common).  The
+// kProbeNodes thresholds, sorted, cut the errors into kProbeBuckets buckets;
+// the rel-err finished regions form one more bin.  Each bin sums its errors
+// exactly, as integers: E / e_b in fixed point with kProbeFrac fraction bits
+// (errors at or above the budget e_b count as e_b, which fails the accuracy
 // requirement either way).
+constexpr int kProbeDepth = 4;
 constexpr int kProbeRay = 8;
-constexpr int kProbeThr = 2 * kProbeRay + 1;
-constexpr int kProbeBuckets = kProbeThr + 1;
+constexpr int kProbeTree = (1 << kProbeDepth) - 1;
+constexpr int kProbeNodes = kProbeTree + 2 * (kProbeRay - kProbeDepth + 1);
+constexpr int kProbeBuckets = kProbeNodes + 1;
 constexpr int kProbeBins = kProbeBuckets + 1;
 constexpr int kProbeFrac = 88;
-constexpr int kProbeThreads = 128;
+constexpr int kProbeThreads = 96;
 
 // One bin of a probe pass, accumulated over all blocks by integer atomics
 // (order-independent, so exact and deterministic): the 128-bit fixed-point
-// error sum (lo, hi) and the region count.
+// error sum as three limbs, sum = limb[0] + limb[1] 2^44 + limb[2] 2^88
+// (each block adds limbs below 2^44, so no carry crosses them and no atomic
+// waits for another's result), and the region count.
 struct ProbeAcc {
-  unsigned long long lo, hi, cnt;
+  unsigned long long limb[3], cnt;
 };
 
 // Rule data passed by value to the evaluate kernels.
