@@ -80,15 +80,25 @@ def _load(parallel: bool = False):
 _rule_cache: dict = {}
 
 
-def _rule_struct(n: int, degree: int = 9):
+# families whose split-axis fourth difference takes the two inner radii
+# (kinks and jumps); every other family takes the inner and outer radius
+_INNER_SPLIT_FAMILIES = (4, 5)   # C0, discontinuous
+
+
+def split_outer(family: int) -> bool:
+    return family not in _INNER_SPLIT_FAMILIES
+
+
+def _rule_struct(n: int, degree: int = 9, outer: bool = True):
     """The rule as the C oracle reads it: degree 9 (the PAGANI rule, four
-    null rules) or 7 (the Genz-Malik rule, error |R7 - R5|)."""
-    key = (n, degree)
+    null rules; outer selects the fourth difference's radii) or 7 (the
+    Genz-Malik rule, error |R7 - R5|, its own radii)."""
+    key = (n, degree, bool(outer) if degree == 9 else True)
     if key not in _rule_cache:
         if degree == 9:
             gen, wts = _rule.rule_tables(n)
-            a, b = _rule.fourth_difference_offsets()
-            q = float(_rule.LP / _rule.L2)
+            a, b = _rule.fourth_difference_offsets(outer)
+            q = float(_rule.fourth_difference_weight(outer))
             _, counts, _, _, _ = _rule.exact_rule(n)
             kind = 0
         elif degree == 7:
@@ -130,7 +140,7 @@ def evaluate(family: int, n: int, params, lower, width, diag: bool = False, degr
     E = np.zeros(m)
     K = np.zeros(m, dtype=np.int32)
     D = np.zeros((m, 13 + 2 * n)) if diag else None
-    lib.oracle_evaluate(ctypes.byref(_rule_struct(n, degree)), ctypes.c_int(family), _dp(p), ctypes.c_int64(m),
+    lib.oracle_evaluate(ctypes.byref(_rule_struct(n, degree, split_outer(family))), ctypes.c_int(family), _dp(p), ctypes.c_int64(m),
                         _dp(lo), _dp(wd), _dp(V), _dp(E), K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                         _dp(D) if diag else None)
     return (V, E, K, D) if diag else (V, E, K)
@@ -182,7 +192,7 @@ def integrate(family: int, n: int, params, epsrel: float, epsabs: float = 1e-20,
         lcap = 8 * max_regions
         ll = np.zeros((lcap, n))
         lw = np.zeros((lcap, n))
-    lib.oracle_pagani(ctypes.byref(_rule_struct(n, degree)), ctypes.c_int(family), _dp(p), ctypes.c_double(epsrel),
+    lib.oracle_pagani(ctypes.byref(_rule_struct(n, degree, split_outer(family))), ctypes.c_int(family), _dp(p), ctypes.c_double(epsrel),
                       ctypes.c_double(epsabs), ctypes.c_int64(max_regions), ctypes.byref(opt), ctypes.byref(res),
                       trace.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(it_max),
                       _dp(fl) if want_regions else None, _dp(fw) if want_regions else None,

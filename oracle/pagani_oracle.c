@@ -39,6 +39,15 @@
  *  - Split axis (Sec. 2.2, Sec. 3.2): fourth divided difference per axis,
  *    D_j = |(f(c+a h_j e_j) + f(c-a h_j e_j) - 2 f(c))
  *           - q (f(c+b h_j e_j) + f(c-b h_j e_j) - 2 f(c))|, q = a^2/b^2,
+ *    with radii a < b of the rule's one-axis orbits (they come in with the
+ *    rule, per family, from oracle/capi.py): the inner and the outer
+ *    radius a = sqrt(l2), b = sqrt(l1) for smooth integrands, as Genz and
+ *    Malik's rule does with sqrt(9/70), sqrt(9/10) (the degree-7 variant's
+ *    radii); the two inner radii a = sqrt(lp), b = sqrt(l2) for the C0 and
+ *    discontinuous families, whose kinks and jumps, once a difference
+ *    reaching out to sqrt(l1) has bisected a box across them, can sit in
+ *    the outer margin of a child beyond every rule point, where no error
+ *    estimate sees them;
  *    a D_j no larger than 2^12 u M_j (M_j the same sum over |f|) is rounding
  *    noise and counts as zero; K = smallest j with D_j >= (1 - 1e-10) max D;
  *    if every D_j counts as zero, the widest axis (smallest j among equals).
@@ -117,7 +126,7 @@ typedef struct {
   int G;              /* number of generators */
   const double *gen;  /* G x n generator magnitudes on [-1,1]^n, row-major */
   const double *wts;  /* G x 5: basic rule, then null rules u_1..u_4 */
-  double a, b, q;     /* fourth-difference radii sqrt(lp), sqrt(l2); q = a^2/b^2 */
+  double a, b, q;     /* fourth-difference radii: inner a, outer b; q = a^2/b^2 */
   const int64_t *count; /* G orbit sizes */
   int error_kind;     /* 0: the four-null-rule error formula (degree-9 rule);
                          1: |R7 - R5|, the Genz-Malik degree-7 rule's difference

@@ -265,10 +265,24 @@ def rule_tables(n: int):
     return gen, wts
 
 
-def fourth_difference_offsets():
-    """(a, b) = (sqrt(lp), sqrt(l2)): the two one-axis radii whose second
-    differences are combined into a fourth difference."""
+def fourth_difference_offsets(outer: bool = True):
+    """(a, b): the two one-axis radii whose second differences are combined
+    into a fourth difference, with weight q = a^2 / b^2
+    (fourth_difference_weight).  outer: the inner and the outer radius of the
+    rule, (sqrt(l2), sqrt(l1)), as Genz and Malik's rule takes its difference
+    at its inner and outer radii sqrt(9/70) and sqrt(9/10); used for the
+    smooth families.  Otherwise the two inner radii (sqrt(lp), sqrt(l2)),
+    used for the families with kinks or jumps, where a difference reaching
+    out to sqrt(l1) bisects boxes across features that then sit in the
+    children's outer margin, beyond every rule point."""
+    if outer:
+        return float(_dsqrt(L2)), float(_dsqrt(L1))
     return float(_dsqrt(LP)), float(_dsqrt(L2))
+
+
+def fourth_difference_weight(outer: bool = True) -> Fraction:
+    """q = a^2 / b^2: l2 / l1 (outer), lp / l2 (inner)."""
+    return L2 / L1 if outer else LP / L2
 
 
 def lambdas():

@@ -38,6 +38,9 @@ struct RealProduct {
   __device__ static __forceinline__ double acc(double S, T a, T b) { return fma(a, b, S); }
   static constexpr bool kUnitBounded = false;  // positive values: |S_g| = sum |f|
   static constexpr bool kHasGrad = true;        // f = prod_j phi_j(x_j; p0_j, p1_j), phi > 0
+  // split-axis fourth difference at the rule's inner and outer radius (smooth
+  // integrands); false: at its two inner radii (kinks, jumps)
+  static constexpr bool kOuterSplit = true;
   __device__ static __forceinline__ T mul(T a, T b) { return a * b; }
   __device__ static __forceinline__ double last(T a, T b) { return a * b; }
   __device__ static __forceinline__ double val(T a) { return a; }
@@ -90,6 +93,7 @@ struct Gaussian : RealProduct {  // exp(-sum_j a_j^2 (x_j - w_j)^2)
 };
 
 struct C0Fam : RealProduct {  // exp(-sum_j a_j |x_j - w_j|)
+  static constexpr bool kOuterSplit = false;  // kinks
   static constexpr int kFamily = kFamC0;
   struct Ax { double a, w; };
   __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
@@ -113,6 +117,7 @@ struct Oscillatory {  // cos(2 pi u + sum_j a_j x_j) = Re[e^{2 pi i u} prod_j e^
   static constexpr int kFamily = kFamOscillatory;
   static constexpr bool kUnitBounded = true;  // signed values with |f| <= 1
   static constexpr bool kHasGrad = false;
+  static constexpr bool kOuterSplit = true;
   typedef double2 T;
   struct Ax { double a; };
   __device__ static __forceinline__ T mul(T a, T b) {
@@ -146,6 +151,7 @@ struct CornerPeak {  // (1 + sum_j a_j x_j)^-(N+1): per-axis terms add up
   static constexpr int kFamily = kFamCornerPeak;
   static constexpr bool kUnitBounded = false;
   static constexpr bool kHasGrad = false;
+  static constexpr bool kOuterSplit = true;
   typedef double T;
   struct Ax { double a; };
   __device__ static __forceinline__ T mul(T a, T b) { return a + b; }
@@ -176,6 +182,7 @@ struct CornerPeak {  // (1 + sum_j a_j x_j)^-(N+1): per-axis terms add up
 struct Discontinuous : RealProduct {  // prod_j exp(a_j x_j) [x_j < w_j] (Genz discontinuous)
   static constexpr int kFamily = kFamDiscontinuous;
   static constexpr bool kHasGrad = false;  // not differentiable in w
+  static constexpr bool kOuterSplit = false;  // jumps
   struct Ax { double a, w; };
   __device__ static __forceinline__ Ax axis(const IntegrandParams& p, int j) {
     Ax a;
@@ -196,6 +203,7 @@ struct BoxPower {
   static constexpr int kFamily = kFamBoxPower;
   static constexpr bool kUnitBounded = false;
   static constexpr bool kHasGrad = false;
+  static constexpr bool kOuterSplit = true;
   typedef double2 T;  // (partial sum, exponent)
   struct Ax { double p; };
   // out of line: inlined into every unrolled rule point its loop, square root
@@ -286,6 +294,13 @@ __device__ __forceinline__ void axis_entries(typename F::T* tab, const EvalRule&
   }
 }
 
+// The fourth difference's weight q = (a / b)^2 for the radii the family's
+// axis choice uses (see rule_sums).
+template <class F, int DEG>
+__device__ __forceinline__ double split_q(const EvalRule& R) {
+  return (DEG == 9 && F::kOuterSplit) ? R.q_outer : R.q;
+}
+
 // The nine generator sums S[g] = sum over the orbit of g of f, and the
 // fourth differences D[j], for one region whose factor table is `tab`.
 // DEG 9: every orbit of the degree-9 rule.  DEG 7: the Genz-Malik rule's
@@ -311,39 +326,49 @@ __device__ __forceinline__ void rule_sums(const typename F::T* __restrict__ tab,
 #pragma unroll
   for (int g = 1; g < kNumGen; ++g) S[g] = 0.0;
 
-  // one-axis generators and the fourth differences
+  // one-axis generators and the fourth differences.  The difference takes
+  // its points at two radii a < b (split_slots): for the degree-9 rule the
+  // l2 and l1 slots on smooth families, the lp and l2 slots on families
+  // with kinks or jumps; for the degree-7 one the lp and l2 slots
+  // (sqrt(9/70), sqrt(9/10)).  Those two orbits enter it through their pair
+  // sums (and, for signed families, its noise floor through their
+  // magnitudes); the other one-axis orbits go straight into their sums.
+  constexpr bool kOut = DEG == 9 && F::kOuterSplit;
+  constexpr int kInP = kOut ? kR2P : kRpP, kInM = kOut ? kR2M : kRpM;
+  constexpr int kOutP = kOut ? kR1P : kR2P, kOutM = kOut ? kR1M : kR2M;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     T Q = (j == N - 1) ? pre[N - 1] : F::mul(pre[j], suf[j + 1]);
-    // the l2 and lp points also enter the fourth difference through their
-    // pair sums (and, for signed families, its noise floor through their
-    // magnitudes); the l1 and l3 points go straight into their sums
-    double p2 = 0.0, m2 = 0.0, pp = 0.0, mp = 0.0, s2, sp;
+    double pin = 0.0, min_ = 0.0, pout = 0.0, mout = 0.0, si, so;
     if constexpr (F::kUnitBounded) {
-      p2 = F::last(Q, PG_TB(kR2P, j));
-      m2 = F::last(Q, PG_TB(kR2M, j));
-      pp = F::last(Q, PG_TB(kRpP, j));
-      mp = F::last(Q, PG_TB(kRpM, j));
-      s2 = p2 + m2;
-      sp = pp + mp;
+      pin = F::last(Q, PG_TB(kInP, j));
+      min_ = F::last(Q, PG_TB(kInM, j));
+      pout = F::last(Q, PG_TB(kOutP, j));
+      mout = F::last(Q, PG_TB(kOutM, j));
+      si = pin + min_;
+      so = pout + mout;
     } else {
-      s2 = F::acc(F::last(Q, PG_TB(kR2M, j)), Q, PG_TB(kR2P, j));
-      sp = F::acc(F::last(Q, PG_TB(kRpM, j)), Q, PG_TB(kRpP, j));
+      si = F::acc(F::last(Q, PG_TB(kInM, j)), Q, PG_TB(kInP, j));
+      so = F::acc(F::last(Q, PG_TB(kOutM, j)), Q, PG_TB(kOutP, j));
     }
-    if constexpr (DEG == 9) {
-      S[kGenL1] = F::acc(F::acc(S[kGenL1], Q, PG_TB(kR1P, j)), Q, PG_TB(kR1M, j));
-      S[kGenL3] = F::acc(F::acc(S[kGenL3], Q, PG_TB(kR3P, j)), Q, PG_TB(kR3M, j));
+    if constexpr (kOut) {
+      S[kGenL1] += so;
+      S[kGenL2] += si;
+      S[kGenLp] = F::acc(F::acc(S[kGenLp], Q, PG_TB(kRpP, j)), Q, PG_TB(kRpM, j));
+    } else {
+      if constexpr (DEG == 9) S[kGenL1] = F::acc(F::acc(S[kGenL1], Q, PG_TB(kR1P, j)), Q, PG_TB(kR1M, j));
+      S[kGenLp] += si;
+      S[kGenL2] += so;
     }
-    S[kGenL2] += s2;
-    S[kGenLp] += sp;
+    if constexpr (DEG == 9) S[kGenL3] = F::acc(F::acc(S[kGenL3], Q, PG_TB(kR3P, j)), Q, PG_TB(kR3M, j));
     // a difference within rounding noise of zero (2^12 u of the magnitude
     // of its five values) says nothing about the axis: its sign bit marks it
     // for region_epilogue, which then skips it
-    const double dj = fabs((sp - 2.0 * f0) - q * (s2 - 2.0 * f0));
+    const double dj = fabs((si - 2.0 * f0) - q * (so - 2.0 * f0));
     // (for the positive families the values are their own magnitudes)
     const double mj = F::kUnitBounded
-                          ? (fabs(pp) + fabs(mp)) + q * (fabs(p2) + fabs(m2)) + (2.0 + 2.0 * q) * fabs(f0)
-                          : fma(2.0 + 2.0 * q, fabs(f0), fma(q, fabs(s2), fabs(sp)));
+                          ? (fabs(pin) + fabs(min_)) + q * (fabs(pout) + fabs(mout)) + (2.0 + 2.0 * q) * fabs(f0)
+                          : fma(2.0 + 2.0 * q, fabs(f0), fma(q, fabs(so), fabs(si)));
     D[j] = fma(-kDiffNoise, mj, dj) > 0.0 ? dj : -dj;
   }
 
@@ -626,23 +651,26 @@ __device__ __forceinline__ void coop_pairs(const EvalRule& R, const LoopArgs& A,
     double Dj;
     {
       const int jd = hl < N ? hl : 0;
-      T c0 = base, p2 = base, m2 = base, pp = base, mp = base;
+      constexpr bool kOut = DEG == 9 && F::kOuterSplit;
+      constexpr int kInP = kOut ? kR2P : kRpP, kInM = kOut ? kR2M : kRpM;
+      constexpr int kOutP = kOut ? kR1P : kR2P, kOutM = kOut ? kR1M : kR2M;
+      T c0 = base, ip = base, im = base, op = base, om = base;
 #pragma unroll
       for (int m = 0; m < N; ++m) {
         const T t0 = tab[kC0 * N + m];
         c0 = F::mul(c0, t0);
-        p2 = F::mul(p2, m == jd ? tab[kR2P * N + m] : t0);
-        m2 = F::mul(m2, m == jd ? tab[kR2M * N + m] : t0);
-        pp = F::mul(pp, m == jd ? tab[kRpP * N + m] : t0);
-        mp = F::mul(mp, m == jd ? tab[kRpM * N + m] : t0);
+        ip = F::mul(ip, m == jd ? tab[kInP * N + m] : t0);
+        im = F::mul(im, m == jd ? tab[kInM * N + m] : t0);
+        op = F::mul(op, m == jd ? tab[kOutP * N + m] : t0);
+        om = F::mul(om, m == jd ? tab[kOutM * N + m] : t0);
       }
-      const double q = R.q;
-      const double f0 = F::val(c0), vp2 = F::val(p2), vm2 = F::val(m2), vpp = F::val(pp), vmp = F::val(mp);
-      const double s2 = vp2 + vm2, sp = vpp + vmp;
-      const double dj = fabs((sp - 2.0 * f0) - q * (s2 - 2.0 * f0));
+      const double q = split_q<F, DEG>(R);
+      const double f0 = F::val(c0), vip = F::val(ip), vim = F::val(im), vop = F::val(op), vom = F::val(om);
+      const double si = vip + vim, so = vop + vom;
+      const double dj = fabs((si - 2.0 * f0) - q * (so - 2.0 * f0));
       const double mj = F::kUnitBounded
-                            ? (fabs(vpp) + fabs(vmp)) + q * (fabs(vp2) + fabs(vm2)) + (2.0 + 2.0 * q) * fabs(f0)
-                            : fma(2.0 + 2.0 * q, fabs(f0), fma(q, fabs(s2), fabs(sp)));
+                            ? (fabs(vip) + fabs(vim)) + q * (fabs(vop) + fabs(vom)) + (2.0 + 2.0 * q) * fabs(f0)
+                            : fma(2.0 + 2.0 * q, fabs(f0), fma(q, fabs(so), fabs(si)));
       Dj = fma(-kDiffNoise, mj, dj) > 0.0 ? dj : -dj;
     }
     double D[N], width[N];
@@ -741,7 +769,7 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
           axis_entries<F, N, THREADS>(tab, R, prm, fcache, A.fcache_levels, lo, lv, j);
         }
         double S[kNumGen], D[N];
-        rule_sums<F, N, THREADS, DEG>(tab, base, R.q, S, D);
+        rule_sums<F, N, THREADS, DEG>(tab, base, split_q<F, DEG>(R), S, D);
         region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, pow2_neg(lvsum) * prm.vol, wd, V, E, K, nullptr);
       }
       const double Vo = __shfl_xor_sync(0xffffffffu, V, 1);
@@ -799,12 +827,12 @@ __global__ void __launch_bounds__(THREADS, PAGANI_EVAL_MINB) k_evaluate_loop(con
     double S[kNumGen], D[N];
     double VL, EL, VR, ER;
     int KL, KR;
-    rule_sums<F, N, THREADS, DEG>(tab, base, R.q, S, D);
+    rule_sums<F, N, THREADS, DEG>(tab, base, split_q<F, DEG>(R), S, D);
     region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, pow2_neg(lvL) * prm.vol, wL, VL, EL, KL, nullptr);
     // patch the one axis where the right sibling differs
     if (diff_axis >= 0)
       axis_entries<F, N, THREADS>(tab, R, prm, fcache, A.fcache_levels, diff_lo, diff_lv, diff_axis);
-    rule_sums<F, N, THREADS, DEG>(tab, base, R.q, S, D);
+    rule_sums<F, N, THREADS, DEG>(tab, base, split_q<F, DEG>(R), S, D);
     region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, pow2_neg(lvR) * prm.vol, wR, VR, ER, KR, nullptr);
 
     if (it > 1) two_level(VL, VR, A.pool.Vp[p], EL, ER);
@@ -931,7 +959,7 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_standalone(const EvalRule 
       }
       double S[kNumGen], D[N], V, E, nk[8];
       int K;
-      rule_sums<F, N, THREADS, DEG>(tab, base, R.q, S, D);
+      rule_sums<F, N, THREADS, DEG>(tab, base, split_q<F, DEG>(R), S, D);
       region_epilogue<N, F::kUnitBounded, DEG>(R, S, D, vol, w, V, E, K, nk);
       A.V[i] = V;
       A.E[i] = E;
@@ -1039,12 +1067,12 @@ __global__ void __launch_bounds__(THREADS) k_evaluate_batch(const EvalRule R, co
     double S[kNumGen], D[N];
     double VL, EL, VR, ER;
     int KL, KR;
-    rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
+    rule_sums<F, N, THREADS>(tab, base, split_q<F, 9>(R), S, D);
     region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvL) * prm.vol, wL, VL, EL, KL, nullptr);
     if (diff_axis >= 0)
       axis_entries<F, N, THREADS, kBatchCacheSlots>(tab, R, prm, icache, kBatchCacheLevels, diff_lo, diff_lv,
                                                     diff_axis);
-    rule_sums<F, N, THREADS>(tab, base, R.q, S, D);
+    rule_sums<F, N, THREADS>(tab, base, split_q<F, 9>(R), S, D);
     region_epilogue<N, F::kUnitBounded>(R, S, D, pow2_neg(lvR) * prm.vol, wR, VR, ER, KR, nullptr);
     if (it > 1) two_level(VL, VR, G.Vp[p], EL, ER);
     *reinterpret_cast<double2*>(G.V + iL) = make_double2(VL, VR);

@@ -1011,6 +1011,7 @@ static EvalRule to_eval_rule(const RuleTable& t) {
   EvalRule r;
   for (int i = 0; i < 5; ++i) r.radius[i] = t.radius[i];
   r.q = t.q;
+  r.q_outer = t.q_outer;
   r.noise = 64.0 * (double)t.num_points * 0x1p-53;
   for (int g = 0; g < kNumGen; ++g) r.cnt[g] = (double)t.count[g];
   for (int k = 0; k < 4; ++k) {

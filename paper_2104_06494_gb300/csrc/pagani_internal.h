@@ -55,7 +55,9 @@ struct RuleTable {
   int degree;              // 9: the PAGANI rule; 7: the Genz-Malik variant (error |R7 - R5| = null rule 1)
   int num_points;
   double radius[5];        // sqrt of l1, l2, l3, lp, l0 (on [-1, 1])
-  double q;                // lp / l2 (fourth-difference weight)
+  double q;                // fourth-difference weight of the lp and l2 slots, (lp slot / l2 slot)^2 radii:
+                           // lp / l2 (degree 9, families with kinks or jumps), 1/7 (degree 7)
+  double q_outer;          // weight of the l2 and l1 slots, l2 / l1 (degree 9, smooth families); 0 for degree 7
   double w[kNumGen][5];    // basic rule, null rules 1..4 (unit-volume cube)
   int64_t count[kNumGen];  // orbit sizes
 };
@@ -197,7 +199,8 @@ struct ProbeAcc {
 // Rule data passed by value to the evaluate kernels.
 struct EvalRule {
   double radius[5];
-  double q;
+  double q;        // fourth-difference weight, lp and l2 slots
+  double q_outer;  // fourth-difference weight, l2 and l1 slots (degree 9)
   double noise;  // 64 N(n) u: null values below noise * vol * sum_g |u_kg| M_g count as zero
   double w[kNumGen][5];
   double cnt[kNumGen];  // orbit sizes

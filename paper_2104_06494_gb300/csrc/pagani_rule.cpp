@@ -324,7 +324,10 @@ bool build_rule(int n, int degree, RuleTable* out, double* max_residual) {
   out->radius[2] = (double)sqrtl(L.l3);
   out->radius[3] = (double)sqrtl(L.lp);
   out->radius[4] = (double)sqrtl(L.l0);
+  // fourth-difference weights: the two inner radii (sqrt(lp), sqrt(l2)) and
+  // the inner and outer radius (sqrt(l2), sqrt(l1))
   out->q = (double)(L.lp / L.l2);
+  out->q_outer = (double)(L.l2 / L.l1);
   for (int c = 0; c < G; ++c) {
     int g = gens[c];
     out->count[g] = orbit_count(n, g);

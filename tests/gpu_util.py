@@ -18,10 +18,11 @@ def value_condition(family, n, params, lo, wd):
     at most k_rel eps |f| + k_abs eps, whichever way it is formed (products
     of per-axis factors or the formula written out):
       product peak  k_rel = 2n + 4 (n divisions and products)
-      Gaussian      k_rel = max sum a^2 (x - w)^2 (the exponent: exp
-                    turns an absolute error of its argument into a relative
-                    error of its value)
-      C0            k_rel = max sum a |x - w|
+      Gaussian      k_rel = max sum (3 u^2 + 2 |u| |a| |x|) + n + 4, u = a (x - w)
+                    (exp turns an absolute error of its argument into a
+                    relative error of its value; the point coordinate x
+                    carries eps |x|, which u^2 turns into 2 |u| |a| eps |x|)
+      C0            k_rel = max sum (2 |u| + |a| |x|) + n + 4, u = a |x - w|
       corner peak   k_rel = 4 (n + 1) (a power of a sum of n terms)
       oscillatory   k_abs = 2 pi |u| + sum |a| max |x| (the cosine argument)
       discontinuous k_rel = 2n + 4 + max sum |a x| (the exponent)
@@ -37,12 +38,15 @@ def value_condition(family, n, params, lo, wd):
     p = np.asarray(params, dtype=np.float64)
     k_rel = np.full(m, 2.0 * n + 4)
     k_abs = np.zeros(m)
+    xmax = np.maximum(np.abs(lo), np.abs(hi))
     if family == 1:
         a, w = p[:n], p[n:]
-        k_rel = np.sum(a ** 2 * np.maximum((lo - w) ** 2, (hi - w) ** 2), axis=1)
+        u = np.abs(a) * np.maximum(np.abs(lo - w), np.abs(hi - w))
+        k_rel = np.sum(3 * u ** 2 + 2 * u * np.abs(a) * xmax, axis=1) + n + 4
     elif family == 4:
         a, w = p[:n], p[n:]
-        k_rel = np.sum(a * np.maximum(np.abs(lo - w), np.abs(hi - w)), axis=1)
+        u = np.abs(a) * np.maximum(np.abs(lo - w), np.abs(hi - w))
+        k_rel = np.sum(2 * u + np.abs(a) * xmax, axis=1) + n + 4
     elif family == 3:
         k_rel = np.full(m, 4.0 * (n + 1))
     elif family == 2:

@@ -48,7 +48,11 @@ def test_rule_tables_match_oracle(lib, n):
     _, counts, _, _, _ = orule.exact_rule(n)
     names = orule.generator_names(n)
     full = ["centre", "l1", "l2", "l3", "lp", "l1l1", "l1l2", "l1l1l1", "l0^n"]
-    a, b = orule.fourth_difference_offsets()
+    # the fourth difference's radii: the l2 and l1 slots (smooth families),
+    # the lp and l2 slots (families with kinks or jumps)
+    a, b = orule.fourth_difference_offsets(outer=True)
+    assert abs(rad[1] - a) <= 2e-16 and abs(rad[0] - b) <= 2e-16
+    a, b = orule.fourth_difference_offsets(outer=False)
     assert abs(rad[3] - a) <= 1e-16 and abs(rad[1] - b) <= 2e-16
     for gi, name in enumerate(names):
         g = full.index(name)

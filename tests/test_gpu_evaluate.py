@@ -40,7 +40,9 @@ def oracle_side(family, n, params, lo, wd, degree=9):
     vround = V_ROUND * (vol * W[0] if family == 2 else Do[:, 8])
     return dict(V=Vo, E=Eo, K=Ko, N=Do[:, 0:4], Nabs=Do[:, 4:8], Vabs=Do[:, 8], Dj=Do[:, 9:9 + n],
                 Dabs=Do[:, 9 + n:9 + 2 * n], floor=Do[:, 9 + 2 * n:13 + 2 * n], k_rel=k_rel, k_abs=k_abs,
-                W=W, vol=vol, width=np.atleast_2d(wd), degree=degree, vround=vround)
+                W=W, vol=vol, width=np.atleast_2d(wd), degree=degree, vround=vround,
+                # the fourth difference's weight for this family's radii
+                q=float(orule.fourth_difference_weight(oracle.split_outer(family))) if degree == 9 else 1 / 7)
 
 
 def run_both(torch, family, n, params, lo, wd, degree=9):
@@ -103,7 +105,7 @@ def check_parity(g, o, n):
         checked += 1
         assert abs(g["E"][i] - o["E"][i]) <= (8 * delta + 1e-12) * o["E"][i], (i, g["E"][i], o["E"][i], delta)
     Dg = g["D"][8:8 + n].T
-    q = 0.0625 / 0.16488242915640136 if o["degree"] == 9 else 1 / 7
+    q = o["q"]
     tolD = 1e-12 * o["Dj"] + (2 * n + 16 + kr[:, None]) * EPS * o["Dabs"] + (4 + 4 * q) * ka[:, None] * EPS
     assert np.all(np.abs(Dg - o["Dj"]) <= tolD), np.max(np.abs(Dg - o["Dj"]) / tolD)
     # split axis: equal, or a valid choice under the rounding of D and of

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 # name, epsrel, max_regions, expected status
 SUITE = [
     ("f1_d8", 1e-3, 1_000_000, 2),  # oscillatory, relative-error filter off: the pool runs out
-    ("f2_d6", 1e-2, 1_000_000, 0),  # product peak c = 50: 25 iterations, 1.3e6 regions
+    ("f2_d6", 1e-2, 1_000_000, 0),  # product peak c = 50: 25 iterations, 9.6e5 regions
     ("f3_d3", 1e-6, 1_000_000, 0),  # corner peak: converged in one pass
     ("f3_d8", 1e-3, 1_000_000, 2),
     ("f4_d5", 1e-3, 1_000_000, 0),  # Gaussian a = 25: 1.05e6 regions over 16 iterations

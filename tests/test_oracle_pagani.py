@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import capi, closed_forms as cf, rule
-from paper_2104_06494_gb300.workloads import (draw_params, random_dyadic_regions, PRODUCT_PEAK, GAUSSIAN,
+from paper_2104_06494_gb300.workloads import (config_workloads, draw_params, random_dyadic_regions, PRODUCT_PEAK, GAUSSIAN,
                                               OSCILLATORY, CORNER_PEAK, C0, SplitMix64)
 
 FAMS = [PRODUCT_PEAK, GAUSSIAN, OSCILLATORY, CORNER_PEAK, C0]
@@ -50,9 +50,9 @@ def test_tiny_cases_vs_tensor_gauss_legendre(family):
 def test_hand_computed_fourth_difference_x1_pow4():
     """f = x_1^4 on [0,1]^2: along axis 0 the second differences at radii a,
     b are 12 c^2 r^2 h^2 + 2 r^4 h^4, so D_0 = 2 a^2 h^4 |a^2 - b^2| with
-    a^2 = 1/16, b^2 = l2, h = 1/2; along axis 1 f is constant, D_1 = 0."""
+    a^2 = l2, b^2 = l1, h = 1/2; along axis 1 f is constant, D_1 = 0."""
     V, E, K, D = capi.evaluate(100, 2, [4, 0], [[0.0, 0.0]], [[1.0, 1.0]], diag=True)
-    a2, b2, h = 1 / 16, float(rule.L2), 0.5
+    a2, b2, h = float(rule.L2), float(rule.L1), 0.5
     assert abs(D[0, 9] - 2 * a2 * h ** 4 * abs(a2 - b2)) < 1e-16
     assert D[0, 10] == 0.0
     assert K[0] == 0
@@ -78,7 +78,7 @@ def test_split_axis_ignores_differences_at_rounding_noise():
     assert D[0, 9] <= 2.0 ** -41 * D[0, 12]
     assert K[0] == 1
     V, E, K, D = capi.evaluate(100, 3, [4, 0, 0], [[0.0, 0.0, 0.0]], [[0.5, 1.0, 1.0]], diag=True)
-    a2, b2, h = 1 / 16, float(rule.L2), 0.25
+    a2, b2, h = float(rule.L2), float(rule.L1), 0.25
     assert abs(D[0, 9] - 2 * a2 * h ** 4 * abs(a2 - b2)) < 1e-16
     assert K[0] == 0
 
@@ -336,3 +336,81 @@ def test_openmp_build_reproduces_the_serial_oracle():
         assert (a.status, a.iterations, a.n_regions) == (b.status, b.iterations, b.n_regions)
         assert a.estimate == b.estimate and a.errorest == b.errorest
         assert a.trace.tobytes() == b.trace.tobytes()
+
+
+def test_outer_radius_sees_a_jump_the_inner_radii_miss():
+    """A box of the discontinuous family cut by its jump on axis 0 at 0.7 of
+    the half-width from the centre (between the inner radius sqrt(l2) = 0.41
+    and the outer sqrt(l1) = 0.96), smooth exp(3 x) along axes 1 and 2.  A
+    fourth difference taken at sqrt(l2) and sqrt(l1) sees the jump and picks
+    axis 0; one taken at the two inner radii sqrt(lp), sqrt(l2) (the
+    family's own reading) does not, and picks a smooth axis."""
+    from paper_2104_06494_gb300.workloads import DISCONTINUOUS
+    n = 3
+    p = [1.0, 3.0, 3.0, 0.5 + 0.7 * 0.5, 2.0, 2.0]
+    lo, wd = [[0.0, 0.0, 0.0]], [[1.0, 1.0, 1.0]]
+    _, _, K_inner = capi.evaluate(DISCONTINUOUS, n, p, lo, wd)
+    assert K_inner[0] != 0
+    st = capi._rule_struct(n, 9, False)
+    saved = (st.a, st.b, st.q)
+    try:
+        st.a, st.b, st.q = float(rule.L2) ** 0.5, float(rule.L1) ** 0.5, float(rule.L2 / rule.L1)
+        _, _, K_outer = capi.evaluate(DISCONTINUOUS, n, p, lo, wd)
+    finally:
+        st.a, st.b, st.q = saved
+    assert K_outer[0] == 0
+
+
+def _integrate_with_radii(w, outer, max_regions):
+    """The oracle on workload w with the split-axis radii of the other
+    reading planted into its rule (restored afterwards)."""
+    st = capi._rule_struct(w.dim, 9, capi.split_outer(w.family))
+    saved = (st.a, st.b, st.q)
+    try:
+        st.a, st.b = rule.fourth_difference_offsets(outer)
+        st.q = float(rule.fourth_difference_weight(outer))
+        return capi.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, max_regions,
+                              relerr_filter=w.relerr_filter)
+    finally:
+        st.a, st.b, st.q = saved
+
+
+@pytest.mark.parametrize("case", ["c0", "discontinuous"])
+def test_kinks_and_jumps_take_the_inner_radii(case):
+    """Why the C0 and discontinuous families take the two inner radii.  With
+    the outer radius their boxes are bisected across a kink or jump, and a
+    feature that ends up within 2.2 % of a cut lies in the child's outer
+    margin, beyond every rule point (sqrt(l1) = 0.956): no null rule and no
+    parent-child comparison sees it.  On these seeded instances the outer
+    reading then converges with the true error far above its estimate and
+    above tau; the family's own reading (inner radii) ends in status 2, its
+    estimate covering the true error."""
+    from paper_2104_06494_gb300.workloads import Workload, C0, DISCONTINUOUS, batch_workloads
+    if case == "c0":
+        w = [x for x in batch_workloads() if x.name == "batch_519"][0]   # C0, n = 4, tau 1e-6
+        pool = 16384
+    else:
+        w = Workload("disc_d4", DISCONTINUOUS, 4, 1e-3, draw_params(DISCONTINUOUS, 4, 7055), 0)
+        pool = 100000
+    assert not capi.split_outer(w.family)
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    bad = _integrate_with_radii(w, True, pool)
+    assert bad.status == 0 and abs(bad.estimate - ex) > 10 * bad.errorest
+    assert abs(bad.estimate - ex) > w.epsrel * abs(ex)
+    own = capi.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, pool, relerr_filter=w.relerr_filter)
+    assert own.status == 2 and abs(own.estimate - ex) <= own.errorest
+
+
+def test_smooth_families_take_the_outer_radius():
+    """The 5-D Gaussian of the bench (tau 1e-7): with the inner and outer
+    radius the loop reaches the same accuracy with far fewer region
+    evaluations than with the two inner radii (the fourth difference then
+    spans the box's rule points out to sqrt(l1), where its error lives)."""
+    w = config_workloads()["gaussian_d5"]
+    assert capi.split_outer(w.family)
+    ex = cf.closed_form(w.family, w.dim, w.params)
+    own = capi.integrate(w.family, w.dim, w.params, w.epsrel, w.epsabs, 4_000_000)
+    inner = _integrate_with_radii(w, False, 4_000_000)
+    for r in (own, inner):
+        assert r.status == 0 and abs(r.estimate - ex) <= r.errorest
+    assert own.n_regions < 0.7 * inner.n_regions
