@@ -253,13 +253,13 @@ def management_bandwidth(part, hbm_peak):
     threshold search succeeded) over the phase's CUDA-event time.
       probe: per pass, every region's classification byte and error, 9 s
              (the passes of each iteration are in the trace)
-      count: the classification bytes, s; V and the n level bytes of every
-             finished region, (8 + n)(s - n_surv); E of the finished, or
-             after a search E of every region and the byte of each region
-             the threshold finished, 8 (s - n_surv) or 8 s + (r - n_surv)
+      count: the classification bytes, s; after a search also E of each
+             rel-err active region and the byte of each region the
+             threshold finished, 8 r + (r - n_surv)
       split: the classification byte read; per survivor K and V read, its
              bounds and levels (9n) read, V_p and both halves (2 * 9n)
-             written: s + n_surv (17 + 27 n)"""
+             written; per finished region V, E and its n levels read (the
+             finished sums): s + n_surv (17 + 27 n) + (s - n_surv)(16 + n)"""
     import numpy as np
     tr, n = part["trace"], part["dim"]
     s = tr["s"].astype(float)
@@ -269,9 +269,9 @@ def management_bandwidth(part, hbm_peak):
     passes = tr["probe_passes"].astype(float)
     probe_b = float(np.sum(passes * 9 * s))
     fin = s - surv
-    count_b = float(np.sum(s + (8 + n) * fin + np.where(ok, 8 * s + (rel - surv), 8 * fin)))
+    count_b = float(np.sum(s + np.where(ok, 8 * rel + (rel - surv), 0.0)))
     # the last iteration is split only when the loop goes on (not here: it ended)
-    split_b = float(np.sum((s + surv * (17 + 27 * n))[:-1]))
+    split_b = float(np.sum((s + surv * (17 + 27 * n) + fin * (16 + n))[:-1]))
     out = {}
     for key, b, ms in (("threshold_probe", probe_b, part["phase_ms"][1]), ("sums_count", count_b, part["phase_ms"][2]),
                        ("filter_split", split_b, part["phase_ms"][3])):

@@ -320,25 +320,23 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   __threadfence();
 }
 
-// ------------------------------------------- finished sums + survivor count
+// ------------------------------------------------------------ survivor count
 // The final classification of every region (Evaluate's Rel-Err-Classify
-// byte and, after a successful threshold search, E >= t), the survivors of
-// every 256-region warp slice of a tile, and the sums of V, E and the volume
-// of the finished regions.  The last block takes the decisions that follow
-// Threshold-Classify in Algorithm 2 (v_f, e_f, the memory check).
+// byte and, after a successful threshold search, E >= t) and the survivors
+// of every 256-region warp slice of a tile.  The last block takes the
+// decisions that follow Threshold-Classify in Algorithm 2 that need only the
+// survivor count (the memory check, Sec. 3.5.2).  The finished regions' sums
+// (v_f, e_f of Algorithm 2) are formed by the split kernel, which reads
+// every region's classification byte anyway.
 //
-// Built for bandwidth: each block owns a contiguous range of tiles; a thread
-// takes ITEMS contiguous regions of a tile (one 8-byte load of their
-// classification bytes), the bytes of kCountAhead tiles are requested before
-// the first is used, every warp stores its own slice count, and V, E and the
-// levels are read only where they are needed (E of the rel-err actives after
-// a search; V, E and levels of the finished).  Each block scans its own
-// tiles' counts (offsets within the block) and publishes its survivor total;
-// the last block scans only the block totals.  E and the volume of the
-// finished regions are summed exactly as integers (E as a fixed-point
-// multiple of max E rounded up to a power of two, 2^-kCountEFrac of it; a
-// volume 2^-L as 2^(127 - L), exact for L <= 127), so only V takes an FP64
-// add per finished region.
+// Built for bandwidth: the kernel does no floating-point arithmetic.  Each
+// block owns a contiguous range of tiles; a thread takes ITEMS contiguous
+// regions of a tile (one 8-byte load of their classification bytes), the
+// bytes of kCountAhead tiles are requested before the first is used, and
+// every warp stores its own slice count.  Without a search it reads one
+// byte per region; after one, also E of each rel-err active region.  Each
+// block scans its own tiles' counts (offsets within the block) and publishes
+// its survivor total; the last block scans only the block totals.
 constexpr int kCountAhead = 8;
 constexpr int kCountEFrac = 96;
 
@@ -404,6 +402,12 @@ __device__ __forceinline__ double fixed_to_double(unsigned long long lo, unsigne
   return scalbn(fma(__ull2double_rn(hi), 0x1p64, __ull2double_rn(lo)), e);
 }
 
+// the exponent X of max E rounded up to a power of two, 2^X (E's fixed-point scale)
+__device__ __forceinline__ int emax_scale(double emax) {
+  const unsigned long long mb = ebits(emax);
+  return (mb >> 52) ? (int)(mb >> 52) - 1023 + ((mb & ((1ull << 52) - 1)) ? 1 : 0) : -1022;
+}
+
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   static_assert(ITEMS == 8 && THREADS / 32 == kTileWarps, "one 8-byte load per thread, one slice per warp");
@@ -413,12 +417,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     return;
   }
   constexpr int TILE = THREADS * ITEMS;
-  constexpr int NW = THREADS / 32;
   const int64_t s = c.s;
-  const int n = A.pool.n;
-  const int64_t cap = A.pool.cap;
-  const uint8_t* __restrict__ level = A.pool.level + (size_t)((c.it - 1) & 1) * n * cap;
-  const double* __restrict__ V = A.pool.V;
   const double* __restrict__ E = A.pool.E;
   uint8_t* __restrict__ act = A.pool.act;
   const int64_t ntiles = (s + TILE - 1) / TILE;
@@ -427,17 +426,8 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   const int64_t t_end = t_beg + tpb < ntiles ? t_beg + tpb : ntiles;
   const bool searched = c.search_ok != 0;
   const unsigned long long tb = ebits(c.t);
-  // E's fixed-point scale: max E rounded up to a power of two, 2^X
-  const unsigned long long mb = ebits(c.emax);
-  const int X = (mb >> 52) ? (int)(mb >> 52) - 1023 + ((mb & ((1ull << 52) - 1)) ? 1 : 0) : -1022;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ long long shl[2 * NW];
-  __shared__ NSum shn[THREADS + 1];
-  __shared__ unsigned long long shu[4 * NW];
-  // a thread adds its finished V of a tile plainly (relative error at most
-  // (ITEMS - 1) u) and that partial into a Neumaier accumulator
-  NSum accv = {0.0, 0.0};
-  unsigned long long elo = 0ull, ehi = 0ull, vlo = 0ull, vhi = 0ull;  // finished E and volume
+  __shared__ long long shl[2 * (THREADS / 32)];
   for (int64_t t0 = t_beg; t0 < t_end; t0 += kCountAhead) {
     unsigned long long bytes[kCountAhead];
 #pragma unroll
@@ -448,61 +438,32 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
       // 8-byte load stays inside it; bytes past s are masked below
       bytes[u] = tile < t_end && i0 < s ? *reinterpret_cast<const unsigned long long*>(act + i0) : 0ull;
     }
-#pragma unroll 1
+#pragma unroll
     for (int u = 0; u < kCountAhead; ++u) {
       const int64_t tile = t0 + u;
       if (tile >= t_end) break;
       const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * ITEMS;
       const int valid = i0 < s ? (s - i0 < ITEMS ? (int)(s - i0) : ITEMS) : 0;
-      int a0[ITEMS];
-#pragma unroll
-      for (int r = 0; r < ITEMS; ++r) a0[r] = r < valid && ((bytes[u] >> (8 * r)) & 0xff) != 0;
-      double ee[ITEMS];
-      bool actv[ITEMS];
+      int cnt = 0;
       if (searched) {
-#pragma unroll
-        for (int r = 0; r < ITEMS; ++r) ee[r] = a0[r] ? E[i0 + r] : 0.0;
-#pragma unroll
-        for (int r = 0; r < ITEMS; ++r) actv[r] = a0[r] && ebits(ee[r]) >= tb;
-      } else {
-#pragma unroll
-        for (int r = 0; r < ITEMS; ++r) actv[r] = a0[r];
-      }
-      int cnt = 0, nfin = 0;
-#pragma unroll
-      for (int r = 0; r < ITEMS; ++r) {
-        cnt += actv[r];
-        nfin += r < valid && !actv[r];
-      }
-      if (nfin) {
-        double vv[ITEMS];
+        // rel-err actives the threshold finishes: E < t; their byte is
+        // cleared for the split
+        double ee[ITEMS];
+        bool a0[ITEMS];
 #pragma unroll
         for (int r = 0; r < ITEMS; ++r) {
-          const bool fin = r < valid && !actv[r];
-          vv[r] = fin ? V[i0 + r] : 0.0;
-          if (fin && !(searched && a0[r])) ee[r] = E[i0 + r];
+          a0[r] = r < valid && ((bytes[u] >> (8 * r)) & 0xff) != 0;
+          ee[r] = a0[r] ? E[i0 + r] : 0.0;
         }
-        int Lr[ITEMS];
 #pragma unroll
-        for (int r = 0; r < ITEMS; ++r) Lr[r] = 0;
-        for (int j = 0; j < n; ++j) {
-          const unsigned long long lv = *reinterpret_cast<const unsigned long long*>(level + (size_t)j * cap + i0);
-#pragma unroll
-          for (int r = 0; r < ITEMS; ++r) Lr[r] += (int)((lv >> (8 * r)) & 0xff);
+        for (int r = 0; r < ITEMS; ++r) {
+          const bool keep = a0[r] && ebits(ee[r]) >= tb;
+          cnt += keep;
+          if (a0[r] && !keep) act[i0 + r] = 0;
         }
-        double tv = 0.0;
+      } else {
 #pragma unroll
-        for (int r = 0; r < ITEMS; ++r)
-          if (r < valid && !actv[r]) {
-            tv += vv[r];
-            add_e_fixed(elo, ehi, ee[r], X);
-            add128_shifted(vlo, vhi, 1ull, 127 - Lr[r]);
-          }
-        nadd(accv, tv);
-        if (searched)  // regions finished by the threshold: the split reads the byte back
-#pragma unroll
-          for (int r = 0; r < ITEMS; ++r)
-            if (a0[r] && !actv[r]) act[i0 + r] = 0;
+        for (int r = 0; r < ITEMS; ++r) cnt += r < valid && ((bytes[u] >> (8 * r)) & 0xff) != 0;
       }
       const int wc = __reduce_add_sync(0xffffffffu, cnt);
       if (lane == 0) A.pool.tile_count[tile * kTileWarps + warp] = wc;
@@ -528,42 +489,12 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     A.pool.tile_offset[t] = run;
     run += x;
   }
-  // the block's finished V (compensated), and E and volume (integers, added
-  // to the grid totals in the control block by atomics)
-  if (nt > 0) {
-    NSum v1[1] = {accv};
-    nsum_block_reduce_staged<THREADS, 1>(v1, shn);
-    warp_sum128(elo, ehi);
-    warp_sum128(vlo, vhi);
-    if (lane == 0) {
-      shu[warp] = elo;
-      shu[NW + warp] = ehi;
-      shu[2 * NW + warp] = vlo;
-      shu[3 * NW + warp] = vhi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < NW; ++w) {
-        elo += shu[w];
-        ehi += shu[NW + w] + (elo < shu[w] ? 1ull : 0ull);
-        vlo += shu[2 * NW + w];
-        vhi += shu[3 * NW + w] + (vlo < shu[2 * NW + w] ? 1ull : 0ull);
-      }
-      if (elo | ehi) atomic_add_limbs(c.fin_e_fixed, elo, ehi);
-      if (vlo | vhi) atomic_add_limbs(c.fin_vol_fixed, vlo, vhi);
-      A.count_part[blockIdx.x].va = v1[0];
-      A.count_part[blockIdx.x].n_surv = blk_surv;
-    }
-  } else if (threadIdx.x == 0) {
-    A.count_part[blockIdx.x].va = {0.0, 0.0};
-    A.count_part[blockIdx.x].n_surv = 0;
-  }
+  if (threadIdx.x == 0) A.count_part[blockIdx.x].n_surv = nt > 0 ? blk_surv : 0;
   if (!last_block_arrived(&c.ticket_count)) return;
 
   // survivors before each block (the split adds them to the block's tile
-  // offsets), and the grid's finished sums
+  // offsets)
   const int G = (int)gridDim.x;
-  const int64_t nparts = (ntiles + tpb - 1) / tpb;  // blocks that had tiles
   const int per_b = (G + THREADS - 1) / THREADS;
   const int b0 = threadIdx.x * per_b, b1 = b0 + per_b < G ? b0 + per_b : G;
   long long bacc = 0;
@@ -575,16 +506,7 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     A.count_part[b].surv_before = brun;
     brun += x;
   }
-  NSum p1[1] = {{0.0, 0.0}};
-  for (int64_t b = threadIdx.x; b < nparts; b += THREADS) p1[0] = ncomb(p1[0], A.count_part[b].va);
-  nsum_block_reduce_staged<THREADS, 1>(p1, shn);
   if (threadIdx.x != 0) return;
-  const NSum tva = p1[0];
-  unsigned long long el, eh, vl, vh;
-  take_limbs(c.fin_e_fixed, el, eh);  // (and zero them for the next iteration)
-  take_limbs(c.fin_vol_fixed, vl, vh);
-  const double tea = fixed_to_double(el, eh, X - kCountEFrac);
-  const NSum tfv = {fixed_to_double(0ull, vh, -127), fixed_to_double(vl, 0ull, -127)};
   c.count_tpb = tpb;
   c.n_surv = n_surv;
   const bool tr_ok = c.trace_on && c.it - 1 < A.trace_cap;
@@ -605,28 +527,6 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     c.done = 1;
     c.estimate = c.v + c.vf;
     c.errorest = c.e + c.ef;
-  } else {
-    // v - sum V.A and e - sum E.A of Algorithm 2, summed over the finished
-    // regions directly
-    const double vf_new = c.vf + nval(tva);
-    const double ef_new = c.ef + tea;
-    if (tr) {
-      tr->vf = vf_new;
-      tr->ef = ef_new;
-    }
-    if (n_surv == 0) {
-      // nothing left to refine: v + v_f and e + e_f cannot change any more,
-      // so the loop ends as it would at it_max
-      c.status = 1;
-      c.done = 1;
-      c.estimate = c.v + c.vf;
-      c.errorest = c.e + c.ef;
-    } else {
-      c.tau_cls = survivor_tolerance(c.tau_rel, c.v + c.vf, ef_new, c.v - nval(tva));
-      c.vf = vf_new;
-      c.ef = ef_new;
-      c.fin_volume_acc = ncomb(c.fin_volume_acc, tfv);
-    }
   }
   // independent bound on the device loop: never more than it_max + 1 passes
   c.loop_guard += 1;
@@ -638,12 +538,20 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   __threadfence();
 }
 
-// ----------------------------------------- Filter + parent update + Split
+// ------------------------- Filter + parent update + Split + finished sums
 // Survivor i with rank r (in region order) writes V_p[r] = V_i and its two
 // halves along K_i to slots 2r (lower half) and 2r+1 (upper half) of the
-// other pool buffer.
+// other pool buffer.  Every finished region adds its V, its E and its volume
+// to the iteration's finished sums (v - sum V.A and e - sum E.A of Algorithm
+// 2, formed directly over the finished regions): V as a plain per-thread sum
+// of its items entering a Neumaier block sum, E and the volume exactly as
+// integers (E as a fixed-point multiple of max E rounded up to a power of
+// two, 2^-kCountEFrac of it; a volume 2^-L as 2^(127 - L), exact for
+// L <= 127).  The last block then updates v_f, e_f and the survivors'
+// classification share tau_cls, or, when no region survived, ends the loop
+// (the it_max status: v + v_f and e + e_f cannot change any more).
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
+__global__ void __launch_bounds__(THREADS, 2) k_split(const LoopArgs A) {
   Ctrl& c = *A.ctrl;
   const bool logl = c.keep_leaves && A.leaves.lower != nullptr;
   if (c.done) {
@@ -672,21 +580,29 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
   double* __restrict__ lo_d = A.pool.lower + (size_t)dst * n * cap;
   uint8_t* __restrict__ lv_d = A.pool.level + (size_t)dst * n * cap;
   const int64_t ntiles = (s + TILE - 1) / TILE;
-  __shared__ int shr[THREADS / 32];
+  const int X = emax_scale(c.emax);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = THREADS / 32;
+  __shared__ int shr[NW];
+  __shared__ NSum shn[THREADS + 1];
+  __shared__ unsigned long long shu[4 * NW];
   int bad = 0;
+  NSum accv = {0.0, 0.0};
+  unsigned long long elo = 0ull, ehi = 0ull, vlo = 0ull, vhi = 0ull;  // finished E and volume
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     // survivors before the tile: within its block of the count kernel, plus
     // before that block
     const long long tile_base = A.pool.tile_offset[tile] + A.count_part[tile / c.count_tpb].surv_before;
     // phase 1: every item's classification (stored by the count kernel) and
-    // rank; phase 2: the copies, whose loads then overlap across items
-    // instead of following one barrier each
-    bool actv[ITEMS];
+    // rank; phase 2: the loads and copies, whose loads then overlap across
+    // items instead of following one barrier each
+    bool actv[ITEMS], valid[ITEMS];
     long long qv[ITEMS];
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-      actv[r] = i < s && A.pool.act[i] != 0;  // classified by the count kernel
+      valid[r] = i < s;
+      actv[r] = valid[r] && A.pool.act[i] != 0;  // classified by the count kernel
     }
     long long base = tile_base;
 #pragma unroll
@@ -700,7 +616,7 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
 #pragma unroll
       for (int r = 0; r < ITEMS; ++r) {
         const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
-        if (!actv[r] && i < s) {
+        if (!actv[r] && valid[r]) {
           // finished box: its rank among the finished ones is i - (survivors before i)
           const int64_t pos = c.leaf_count + i - qv[r];
           if (pos < A.leaves.cap) {
@@ -714,20 +630,31 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
         }
       }
     }
-    // the survivors' copies: every item's loads are issued before any store
-    // (per axis), so a thread waits on one L2 round trip per axis instead of
-    // one per item and axis
-    int kv[ITEMS];
-    double vv[ITEMS];
+    // every item's loads are issued before any store (per axis), so a
+    // thread waits on one L2 round trip per axis instead of one per item
+    // and axis: V of every region, K of the survivors, E of the finished
+    int kv[ITEMS], lsum[ITEMS];
+    double vv[ITEMS], ev[ITEMS];
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
       kv[r] = actv[r] ? A.pool.K[i] : -1;
-      vv[r] = actv[r] ? A.pool.V[i] : 0.0;
+      vv[r] = valid[r] ? A.pool.V[i] : 0.0;
+      ev[r] = valid[r] && !actv[r] ? A.pool.E[i] : 0.0;
+      lsum[r] = 0;
     }
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r)
       if (actv[r]) A.pool.Vp[qv[r]] = vv[r];
+    // the finished items' V and E (their volume follows from the levels)
+    double tv = 0.0;
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r)
+      if (valid[r] && !actv[r]) {
+        tv += vv[r];
+        add_e_fixed(elo, ehi, ev[r], X);
+      }
+    nadd(accv, tv);
     for (int j = 0; j < n; ++j) {
       double lo[ITEMS];
       int lv[ITEMS];
@@ -735,10 +662,11 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
       for (int r = 0; r < ITEMS; ++r) {
         const int64_t i = tile * TILE + (int64_t)r * THREADS + threadIdx.x;
         lo[r] = actv[r] ? lo_s[(size_t)j * cap + i] : 0.0;
-        lv[r] = actv[r] ? lv_s[(size_t)j * cap + i] : 0;
+        lv[r] = valid[r] ? lv_s[(size_t)j * cap + i] : 0;  // the finished need it for their volume
       }
 #pragma unroll
       for (int r = 0; r < ITEMS; ++r) {
+        lsum[r] += lv[r];
         if (!actv[r]) continue;
         const int64_t q = qv[r];
         double2 out = make_double2(lo[r], lo[r]);
@@ -752,16 +680,74 @@ __global__ void __launch_bounds__(THREADS) k_split(const LoopArgs A) {
         *reinterpret_cast<uchar2*>(lv_d + (size_t)j * cap + 2 * q) = ol;
       }
     }
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r)
+      if (valid[r] && !actv[r]) add128_shifted(vlo, vhi, 1ull, 127 - lsum[r]);
   }
   if (bad & 1) atomicExch(&c.watchdog, 1);
   if (bad & 2) atomicExch(&c.leaf_overflow, 1);
-  if (!last_block_arrived(&c.ticket_split)) return;
+  // the block's finished V (compensated), and E and volume (integers, added
+  // to the grid totals in the control block by atomics)
+  NSum v1[1] = {accv};
+  nsum_block_reduce_staged<THREADS, 1>(v1, shn);
+  warp_sum128(elo, ehi);
+  warp_sum128(vlo, vhi);
+  if (lane == 0) {
+    shu[warp] = elo;
+    shu[NW + warp] = ehi;
+    shu[2 * NW + warp] = vlo;
+    shu[3 * NW + warp] = vhi;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    for (int w = 1; w < NW; ++w) {
+      elo += shu[w];
+      ehi += shu[NW + w] + (elo < shu[w] ? 1ull : 0ull);
+      vlo += shu[2 * NW + w];
+      vhi += shu[3 * NW + w] + (vlo < shu[2 * NW + w] ? 1ull : 0ull);
+    }
+    if (elo | ehi) atomic_add_limbs(c.fin_e_fixed, elo, ehi);
+    if (vlo | vhi) atomic_add_limbs(c.fin_vol_fixed, vlo, vhi);
+    A.count_part[blockIdx.x].va = v1[0];
+  }
+  if (!last_block_arrived(&c.ticket_split)) return;
+  NSum p1[1] = {{0.0, 0.0}};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += THREADS)
+    p1[0] = ncomb(p1[0], NSum{__ldcg(&A.count_part[b].va.s), __ldcg(&A.count_part[b].va.c)});
+  nsum_block_reduce_staged<THREADS, 1>(p1, shn);
+  if (threadIdx.x != 0) return;
+  const NSum tva = p1[0];
+  unsigned long long el, eh, vl, vh;
+  take_limbs(c.fin_e_fixed, el, eh);  // (and zero them for the next iteration)
+  take_limbs(c.fin_vol_fixed, vl, vh);
+  const double tea = fixed_to_double(el, eh, X - kCountEFrac);
+  const NSum tfv = {fixed_to_double(0ull, vh, -127), fixed_to_double(vl, 0ull, -127)};
+  const double vf_new = c.vf + nval(tva);
+  const double ef_new = c.ef + tea;
+  const bool tr_ok = c.trace_on && c.it - 1 < A.trace_cap;
+  if (tr_ok) {
+    A.trace[c.it - 1].vf = vf_new;
+    A.trace[c.it - 1].ef = ef_new;
+  }
+  if (c.n_surv == 0) {
+    // nothing left to refine: v + v_f and e + e_f cannot change any more,
+    // so the loop ends as it would at it_max (every box of the iteration was
+    // finished, and logged as a leaf above)
+    c.status = 1;
+    c.done = 1;
+    c.estimate = c.v + c.vf;
+    c.errorest = c.e + c.ef;
+    set_cond(A.use_graph, A.h_main, 0u);
+  } else {
+    c.tau_cls = survivor_tolerance(c.tau_rel, c.v + c.vf, ef_new, c.v - nval(tva));
+    c.vf = vf_new;
+    c.ef = ef_new;
+    c.fin_volume_acc = ncomb(c.fin_volume_acc, tfv);
     if (logl) c.leaf_count += c.s - c.n_surv;
     c.s = 2 * c.n_surv;
     c.it += 1;
-    __threadfence();
   }
+  __threadfence();
 }
 
 // ------------------------------------------------------- FP64 peak probe
@@ -1114,7 +1100,7 @@ static int launch_config(const FamilyKernels& fk, int n, Launch* L) {
   if (L->mgmt_grid > w.max_grid) L->mgmt_grid = w.max_grid;
   L->probe_grid = w.sms * 5;
   if (L->probe_grid > w.max_grid) L->probe_grid = w.max_grid;
-  L->count_grid = w.sms * 2;
+  L->count_grid = w.sms * 4;
   if (L->count_grid > w.max_grid) L->count_grid = w.max_grid;
   return 0;
 }
@@ -1555,7 +1541,7 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
   Lc.eval_grid = sms * occ < max_grid ? sms * occ : max_grid;
   Lc.mgmt_grid = sms * 2;
   Lc.probe_grid = sms * 5;
-  Lc.count_grid = sms * 2;
+  Lc.count_grid = sms * 4;
   const int64_t cap = ((max_regions + 4095) / 4096) * 4096;
   const NoallocLayout L = noalloc_layout(cap, n, max_grid);
   LoopArgs a;

@@ -134,7 +134,7 @@ struct Ctrl {
   int32_t passes;            // probe passes (k_probe launches) this iteration
   int32_t total_passes;      // probe passes over the whole call
   int64_t count_tpb;         // tiles per block of the count kernel (the split locates a tile's block)
-  // count kernel: finished E and volume of this iteration as 128-bit fixed
+  // split kernel: finished E and volume of this iteration as 128-bit fixed
   // point in limbs of 44 bits (value = limb[0] + limb[1] 2^44 + limb[2] 2^88)
   unsigned long long fin_e_fixed[3];
   unsigned long long fin_vol_fixed[3];
@@ -163,7 +163,7 @@ struct EvalPartial {
 };
 
 struct CountPartial {
-  NSum va;                 // V summed over the block's finished regions
+  NSum va;                 // V summed over the finished regions of the split kernel's block
   long long n_surv;        // the block's survivors
   long long surv_before;   // survivors of the blocks before it (set by the last block)
 };
