@@ -102,20 +102,21 @@ __device__ __forceinline__ void probe_fixed(unsigned long long eb, unsigned long
   unsigned long long m = eb & ((1ull << 52) - 1);
   if (ex) m |= 1ull << 52;
   else ex = 1;
-  // E = m 2^(ex - 1075); E 2^(kProbeFrac - B) = m 2^sh, below 2^kProbeFrac
+  // E = m 2^(ex - 1075); E 2^(kProbeFrac - B) = m 2^sh, below 2^kProbeFrac.
+  // PTX shifts clamp the shift amount to the register width (a shift by 64
+  // or more gives 0), so every case (sh >= 64, 0 < sh < 64, sh = 0, sh < 0,
+  // down to sh <= -64) is the same straight-line code: the warp does not
+  // diverge on the errors' exponents.
   const int sh = ex - 1075 + kProbeFrac - B;
-  if (sh >= 64) {
-    lo = 0ull;
-    hi = m << (sh - 64);
-  } else if (sh > 0) {
-    lo = m << sh;
-    hi = m >> (64 - sh);
-  } else if (sh > -64) {
-    lo = m >> (-sh);
-    hi = 0ull;
-  } else {
-    lo = hi = 0ull;
-  }
+  const unsigned left = sh > 0 ? (unsigned)sh : 0u, right = sh < 0 ? (unsigned)(-sh) : 0u;
+  const unsigned up = left < 64u ? 64u - left : 64u, down = left >= 64u ? left - 64u : 64u;
+  unsigned long long l, r, h1, h2;
+  asm("shl.b64 %0, %1, %2;" : "=l"(l) : "l"(m), "r"(left));
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(l), "r"(right));
+  asm("shr.b64 %0, %1, %2;" : "=l"(h1) : "l"(m), "r"(up));
+  asm("shl.b64 %0, %1, %2;" : "=l"(h2) : "l"(m), "r"(down));
+  lo = r;
+  hi = h1 | h2;
 }
 
 // The probe's thresholds: node k of the coming steps of the search from t.
@@ -169,9 +170,15 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   __shared__ unsigned long long thr[32];               // sorted thresholds, padded with all ones
   __shared__ ulonglong2 hist[kProbeBins * THREADS];    // per thread: (lo, hi | count << 44) per bin
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t s = c.s;
+  const int64_t np = (s + 1) / 2;
+  // a block whose threads have no region pair only computes the thresholds
+  // (in case it is the last to arrive) and takes its ticket
+  const bool idle = (int64_t)blockIdx.x * THREADS >= np;
   if (threadIdx.x < kProbeNodes) nodeb[threadIdx.x] = ebits(probe_node(threadIdx.x, c.t, c.emin, c.emax));
+  if (!idle)
 #pragma unroll
-  for (int b = 0; b < kProbeBins; ++b) hist[b * THREADS + threadIdx.x] = make_ulonglong2(0ull, 0ull);
+    for (int b = 0; b < kProbeBins; ++b) hist[b * THREADS + threadIdx.x] = make_ulonglong2(0ull, 0ull);
   __syncthreads();
   if (threadIdx.x < kProbeNodes) {
     // rank among the nodes (equal values by node index)
@@ -191,7 +198,6 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   int B;  // e_b = 2^B
   if (e_bits >> 52) B = (int)(e_bits >> 52) - 1023;
   else B = -1074 + 63 - __clzll((long long)e_bits);
-  const int64_t s = c.s;
   const uint8_t* __restrict__ act = A.pool.act;
   const double* __restrict__ E = A.pool.E;
   ulonglong2* mine = hist + threadIdx.x;
@@ -215,54 +221,55 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   // cap >= s + 1 entries for odd s (cap is a multiple of 4096), and the
   // entry past s is masked
   constexpr int U = 4;
-  const int64_t np = (s + 1) / 2;
   const int64_t stride = (int64_t)gridDim.x * THREADS;
   const double2* __restrict__ E2 = reinterpret_cast<const double2*>(E);
   const uint16_t* __restrict__ act2 = reinterpret_cast<const uint16_t*>(act);
-  for (int64_t p0 = (int64_t)blockIdx.x * THREADS + threadIdx.x; p0 < np; p0 += U * stride) {
-    double2 e2[U];
-    unsigned a2[U];
+  if (!idle) {
+    for (int64_t p0 = (int64_t)blockIdx.x * THREADS + threadIdx.x; p0 < np; p0 += U * stride) {
+      double2 e2[U];
+      unsigned a2[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t p = p0 + u * stride;
-      e2[u] = p < np ? E2[p] : make_double2(0.0, 0.0);
-      a2[u] = p < np ? (unsigned)act2[p] : 0u;
-    }
+      for (int u = 0; u < U; ++u) {
+        const int64_t p = p0 + u * stride;
+        e2[u] = p < np ? E2[p] : make_double2(0.0, 0.0);
+        a2[u] = p < np ? (unsigned)act2[p] : 0u;
+      }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t p = p0 + u * stride;
-      if (p >= np) break;
-      add(ebits(e2[u].x), (int)(a2[u] & 0xff));
-      if (2 * p + 1 < s) add(ebits(e2[u].y), (int)(a2[u] >> 8));
+      for (int u = 0; u < U; ++u) {
+        const int64_t p = p0 + u * stride;
+        if (p >= np) break;
+        add(ebits(e2[u].x), (int)(a2[u] & 0xff));
+        if (2 * p + 1 < s) add(ebits(e2[u].y), (int)(a2[u] >> 8));
+      }
     }
-  }
-  __syncthreads();
-  // per bin: the block's sum and count, then one set of atomics
-  for (int b = warp; b < kProbeBins; b += NW) {
-    unsigned long long lo = 0ull, hi = 0ull, cnt = 0ull;
+    __syncthreads();
+    // per bin: the block's sum and count, then one set of atomics
+    for (int b = warp; b < kProbeBins; b += NW) {
+      unsigned long long lo = 0ull, hi = 0ull, cnt = 0ull;
 #pragma unroll
-    for (int t = lane; t < THREADS; t += 32) {
-      const ulonglong2 h = hist[b * THREADS + t];
-      lo += h.x;
-      hi += (h.y & ((1ull << 44) - 1)) + (lo < h.x ? 1ull : 0ull);
-      cnt += h.y >> 44;
-    }
+      for (int t = lane; t < THREADS; t += 32) {
+        const ulonglong2 h = hist[b * THREADS + t];
+        lo += h.x;
+        hi += (h.y & ((1ull << 44) - 1)) + (lo < h.x ? 1ull : 0ull);
+        cnt += h.y >> 44;
+      }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long lo2 = __shfl_down_sync(0xffffffffu, lo, off);
-      const unsigned long long hi2 = __shfl_down_sync(0xffffffffu, hi, off);
-      const unsigned long long c2 = __shfl_down_sync(0xffffffffu, cnt, off);
-      lo += lo2;
-      hi += hi2 + (lo < lo2 ? 1ull : 0ull);
-      cnt += c2;
-    }
-    if (lane == 0 && cnt != 0ull) {
-      constexpr unsigned long long M44 = (1ull << 44) - 1;
-      ProbeAcc& g = A.probe_acc[b];
-      atomicAdd(&g.limb[0], lo & M44);
-      atomicAdd(&g.limb[1], (lo >> 44) | ((hi & ((1ull << 24) - 1)) << 20));
-      atomicAdd(&g.limb[2], hi >> 24);
-      atomicAdd(&g.cnt, cnt);
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long lo2 = __shfl_down_sync(0xffffffffu, lo, off);
+        const unsigned long long hi2 = __shfl_down_sync(0xffffffffu, hi, off);
+        const unsigned long long c2 = __shfl_down_sync(0xffffffffu, cnt, off);
+        lo += lo2;
+        hi += hi2 + (lo < lo2 ? 1ull : 0ull);
+        cnt += c2;
+      }
+      if (lane == 0 && cnt != 0ull) {
+        constexpr unsigned long long M44 = (1ull << 44) - 1;
+        ProbeAcc& g = A.probe_acc[b];
+        atomicAdd(&g.limb[0], lo & M44);
+        atomicAdd(&g.limb[1], (lo >> 44) | ((hi & ((1ull << 24) - 1)) << 20));
+        atomicAdd(&g.limb[2], hi >> 24);
+        atomicAdd(&g.cnt, cnt);
+      }
     }
   }
   if (!last_block_arrived(&c.ticket_probe)) return;
@@ -428,16 +435,22 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   const unsigned long long tb = ebits(c.t);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ long long shl[2 * (THREADS / 32)];
-  for (int64_t t0 = t_beg; t0 < t_end; t0 += kCountAhead) {
-    unsigned long long bytes[kCountAhead];
+  // the classification bytes of kCountAhead tiles; the act array holds
+  // cap >= s entries, cap a multiple of 4096: the 8-byte loads stay inside
+  // it, and bytes past s are masked below
+  auto load_bytes = [&](int64_t t0, unsigned long long (&b)[kCountAhead]) {
 #pragma unroll
     for (int u = 0; u < kCountAhead; ++u) {
       const int64_t tile = t0 + u;
       const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * ITEMS;
-      // the act array holds cap >= s entries, cap a multiple of 4096: the
-      // 8-byte load stays inside it; bytes past s are masked below
-      bytes[u] = tile < t_end && i0 < s ? *reinterpret_cast<const unsigned long long*>(act + i0) : 0ull;
+      b[u] = tile < t_end && i0 < s ? *reinterpret_cast<const unsigned long long*>(act + i0) : 0ull;
     }
+  };
+  unsigned long long bytes[kCountAhead], ahead[kCountAhead];
+  if (t_beg < t_end) load_bytes(t_beg, bytes);
+  for (int64_t t0 = t_beg; t0 < t_end; t0 += kCountAhead) {
+    // the next group's bytes are in flight while this group is counted
+    if (t0 + kCountAhead < t_end) load_bytes(t0 + kCountAhead, ahead);
 #pragma unroll
     for (int u = 0; u < kCountAhead; ++u) {
       const int64_t tile = t0 + u;
@@ -468,6 +481,8 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
       const int wc = __reduce_add_sync(0xffffffffu, cnt);
       if (lane == 0) A.pool.tile_count[tile * kTileWarps + warp] = wc;
     }
+#pragma unroll
+    for (int u = 0; u < kCountAhead; ++u) bytes[u] = ahead[u];
   }
   __syncthreads();  // the block's slice counts are written
   // survivors before each of the block's tiles, within the block: each
