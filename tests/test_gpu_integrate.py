@@ -289,7 +289,7 @@ def test_configs_within_errorest_of_closed_form(pg, name):
 
 
 def test_bench_workload_gaussian_d5_full_size(pg):
-    """The bench's 5-D Gaussian at its full size (epsrel 1e-7, ~2.3e6
+    """The bench's 5-D Gaussian at its full size (epsrel 1e-7, 1.35e6
     regions over 18 iterations), in the launch configuration bench.py times
     (graph loop, library workspace): the same region-set evolution as the
     oracle, the estimate within 1e-12, converged with the closed form
@@ -299,6 +299,24 @@ def test_bench_workload_gaussian_d5_full_size(pg):
     g = pg.pagani_integrate_ex(w.dim, w.family, w.params, w.epsrel, w.epsabs, w.max_regions, trace=True)
     compare_runs(g, o)
     ex = cf.closed_form(w.family, w.dim, w.params)
+    assert abs(g.estimate - ex) <= g.errorest
+
+
+def test_tens_of_millions_of_regions_per_iteration(pg):
+    """A 3-D C0 integral (kinks at 0.31, 0.47, 0.73) at epsrel 1e-10 with
+    the heuristic filter off and a pool of 2^25 regions: the active set
+    grows to 2.5e7 regions and the pool runs out at iteration 23 (status 2),
+    with 7.0e7 region evaluations in all.  At that size the count kernel
+    gives each block more than one group of 8 tiles (its prefetched bytes
+    cross groups), and the split forms the finished sums of millions of
+    regions a launch.  Region-set evolution, trace and estimates as the
+    oracle's."""
+    params = [3.0, 4.0, 5.0, 0.31, 0.47, 0.73]
+    o = oracle.integrate(4, 3, params, 1e-10, 1e-30, 1 << 25, heuristic_filter=0, it_max=40, parallel=True)
+    g = pg.pagani_integrate_ex(3, 4, params, 1e-10, 1e-30, 1 << 25, heuristic_filter=0, it_max=40, trace=True)
+    assert o.status == 2 and int(o.trace["s"].max()) > 2 * 10 ** 7
+    compare_runs(g, o)
+    ex = cf.closed_form(4, 3, params)
     assert abs(g.estimate - ex) <= g.errorest
 
 
