@@ -123,13 +123,13 @@ __device__ __forceinline__ bool final_active(double V, double E, const Ctrl& c) 
 
 // Last-block election: every block calls this after publishing its partial;
 // exactly one (the last to arrive) gets true and may read all partials.
-__device__ __forceinline__ bool last_block_arrived(unsigned int* ticket) {
+__device__ __forceinline__ bool last_block_arrived(unsigned int* ticket, unsigned int nblocks) {
   __shared__ bool is_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int prev = atomicAdd(ticket, 1u);
-    is_last = (prev == gridDim.x - 1);
+    is_last = (prev == nblocks - 1);
   }
   __syncthreads();
   if (is_last) {
@@ -137,6 +137,9 @@ __device__ __forceinline__ bool last_block_arrived(unsigned int* ticket) {
     if (threadIdx.x == 0) *ticket = 0u;  // reset for the next launch
   }
   return is_last;
+}
+__device__ __forceinline__ bool last_block_arrived(unsigned int* ticket) {
+  return last_block_arrived(ticket, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,6 +384,27 @@ __device__ inline int finalize_iteration_head(Ctrl& c, double v, double e, long 
   return 1;
 }
 
+// The fields of the control block that the steps of the search read and
+// write, held in registers while one thread takes several steps in a row.
+struct SearchState {
+  int64_t s;
+  int32_t probes, total_probes, search_ok, last_dir, dir_changes;
+  double t, Pmax, e_b, emin, emax;
+  __device__ explicit SearchState(const Ctrl& c)
+      : s(c.s), probes(c.probes), total_probes(c.total_probes), search_ok(c.search_ok), last_dir(c.last_dir),
+        dir_changes(c.dir_changes), t(c.t), Pmax(c.Pmax), e_b(c.e_b), emin(c.emin), emax(c.emax) {}
+  // the fields a step changes, back into the control block
+  __device__ void store(Ctrl& c) const {
+    c.probes = probes;
+    c.total_probes = total_probes;
+    c.search_ok = search_ok;
+    c.last_dir = last_dir;
+    c.dir_changes = dir_changes;
+    c.t = t;
+    c.Pmax = Pmax;
+  }
+};
+
 // The threshold after t in the search of Algorithm 3: too few regions
 // finished (dir > 0) moves it halfway to max E, too much error (dir < 0)
 // halfway to min E.  The probe kernel builds its tree of coming thresholds
@@ -392,8 +416,10 @@ __host__ __device__ __forceinline__ double search_next(double t, int dir, double
 // One step of Algorithm 3 after a probe with threshold c.t counted
 // n_active candidate actives; e_abar is the error of the candidate finished
 // regions (summed directly, not as e_it - sum A.E).  Returns 1 if another
-// probe is needed.
-__device__ inline int threshold_step(Ctrl& c, long long n_active, double e_abar) {
+// probe is needed.  S is the control block or a register copy of its search
+// fields (SearchState) with the same names.
+template <class S>
+__device__ inline int threshold_step(S& c, long long n_active, double e_abar) {
   c.probes += 1;
   c.total_probes += 1;
   long long s_abar = c.s - n_active;

@@ -172,13 +172,14 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t s = c.s;
   const int64_t np = (s + 1) / 2;
-  // a block whose threads have no region pair only computes the thresholds
-  // (in case it is the last to arrive) and takes its ticket
-  const bool idle = (int64_t)blockIdx.x * THREADS >= np;
+  // only the first nact blocks have region pairs: the others leave at once,
+  // and the last of the nact to arrive takes the search's steps
+  const int64_t need = (np + THREADS - 1) / THREADS;
+  const unsigned nact = need < 1 ? 1u : (need < (int64_t)gridDim.x ? (unsigned)need : gridDim.x);
+  if (blockIdx.x >= nact) return;
   if (threadIdx.x < kProbeNodes) nodeb[threadIdx.x] = ebits(probe_node(threadIdx.x, c.t, c.emin, c.emax));
-  if (!idle)
 #pragma unroll
-    for (int b = 0; b < kProbeBins; ++b) hist[b * THREADS + threadIdx.x] = make_ulonglong2(0ull, 0ull);
+  for (int b = 0; b < kProbeBins; ++b) hist[b * THREADS + threadIdx.x] = make_ulonglong2(0ull, 0ull);
   __syncthreads();
   if (threadIdx.x < kProbeNodes) {
     // rank among the nodes (equal values by node index)
@@ -224,55 +225,53 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   const int64_t stride = (int64_t)gridDim.x * THREADS;
   const double2* __restrict__ E2 = reinterpret_cast<const double2*>(E);
   const uint16_t* __restrict__ act2 = reinterpret_cast<const uint16_t*>(act);
-  if (!idle) {
-    for (int64_t p0 = (int64_t)blockIdx.x * THREADS + threadIdx.x; p0 < np; p0 += U * stride) {
-      double2 e2[U];
-      unsigned a2[U];
+  for (int64_t p0 = (int64_t)blockIdx.x * THREADS + threadIdx.x; p0 < np; p0 += U * stride) {
+    double2 e2[U];
+    unsigned a2[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t p = p0 + u * stride;
-        e2[u] = p < np ? E2[p] : make_double2(0.0, 0.0);
-        a2[u] = p < np ? (unsigned)act2[p] : 0u;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t p = p0 + u * stride;
-        if (p >= np) break;
-        add(ebits(e2[u].x), (int)(a2[u] & 0xff));
-        if (2 * p + 1 < s) add(ebits(e2[u].y), (int)(a2[u] >> 8));
-      }
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = p0 + u * stride;
+      e2[u] = p < np ? E2[p] : make_double2(0.0, 0.0);
+      a2[u] = p < np ? (unsigned)act2[p] : 0u;
     }
-    __syncthreads();
-    // per bin: the block's sum and count, then one set of atomics
-    for (int b = warp; b < kProbeBins; b += NW) {
-      unsigned long long lo = 0ull, hi = 0ull, cnt = 0ull;
 #pragma unroll
-      for (int t = lane; t < THREADS; t += 32) {
-        const ulonglong2 h = hist[b * THREADS + t];
-        lo += h.x;
-        hi += (h.y & ((1ull << 44) - 1)) + (lo < h.x ? 1ull : 0ull);
-        cnt += h.y >> 44;
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long lo2 = __shfl_down_sync(0xffffffffu, lo, off);
-        const unsigned long long hi2 = __shfl_down_sync(0xffffffffu, hi, off);
-        const unsigned long long c2 = __shfl_down_sync(0xffffffffu, cnt, off);
-        lo += lo2;
-        hi += hi2 + (lo < lo2 ? 1ull : 0ull);
-        cnt += c2;
-      }
-      if (lane == 0 && cnt != 0ull) {
-        constexpr unsigned long long M44 = (1ull << 44) - 1;
-        ProbeAcc& g = A.probe_acc[b];
-        atomicAdd(&g.limb[0], lo & M44);
-        atomicAdd(&g.limb[1], (lo >> 44) | ((hi & ((1ull << 24) - 1)) << 20));
-        atomicAdd(&g.limb[2], hi >> 24);
-        atomicAdd(&g.cnt, cnt);
-      }
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = p0 + u * stride;
+      if (p >= np) break;
+      add(ebits(e2[u].x), (int)(a2[u] & 0xff));
+      if (2 * p + 1 < s) add(ebits(e2[u].y), (int)(a2[u] >> 8));
     }
   }
-  if (!last_block_arrived(&c.ticket_probe)) return;
+  __syncthreads();
+  // per bin: the block's sum and count, then one set of atomics
+  for (int b = warp; b < kProbeBins; b += NW) {
+    unsigned long long lo = 0ull, hi = 0ull, cnt = 0ull;
+#pragma unroll
+    for (int t = lane; t < THREADS; t += 32) {
+      const ulonglong2 h = hist[b * THREADS + t];
+      lo += h.x;
+      hi += (h.y & ((1ull << 44) - 1)) + (lo < h.x ? 1ull : 0ull);
+      cnt += h.y >> 44;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long lo2 = __shfl_down_sync(0xffffffffu, lo, off);
+      const unsigned long long hi2 = __shfl_down_sync(0xffffffffu, hi, off);
+      const unsigned long long c2 = __shfl_down_sync(0xffffffffu, cnt, off);
+      lo += lo2;
+      hi += hi2 + (lo < lo2 ? 1ull : 0ull);
+      cnt += c2;
+    }
+    if (lane == 0 && cnt != 0ull) {
+      constexpr unsigned long long M44 = (1ull << 44) - 1;
+      ProbeAcc& g = A.probe_acc[b];
+      atomicAdd(&g.limb[0], lo & M44);
+      atomicAdd(&g.limb[1], (lo >> 44) | ((hi & ((1ull << 24) - 1)) << 20));
+      atomicAdd(&g.limb[2], hi >> 24);
+      atomicAdd(&g.cnt, cnt);
+    }
+  }
+  if (!last_block_arrived(&c.ticket_probe, nact)) return;
   // the grid's bins, then at every threshold (in parallel) the candidate
   // actives and e_abar; thread 0 then takes the steps
   __shared__ unsigned long long blo[kProbeBins], bhi[kProbeBins], bcnt[kProbeBins];
@@ -308,20 +307,25 @@ __global__ void __launch_bounds__(THREADS) k_probe(const LoopArgs A) {
   if (threadIdx.x != 0) return;
   c.passes += 1;
   c.total_passes += 1;
+  // the steps run on a register copy of the search fields: one read of the
+  // control block before them and one write after, not a round trip to
+  // memory per field and step
+  SearchState st(c);
   int k = 0, cont = 1;
   for (;;) {
     const int j = node_at[k];
-    cont = threshold_step(c, n_at[j], e_at[j]);
+    cont = threshold_step(st, n_at[j], e_at[j]);
     if (!cont) break;
-    k = probe_next(k, c.last_dir);
+    k = probe_next(k, st.last_dir);
     if (k < 0) break;  // not among this pass's thresholds: the next pass starts at c.t
-    if (ebits(c.t) != nodeb[k]) {  // the step must land on the node's threshold, bit for bit
+    if (ebits(st.t) != nodeb[k]) {  // the step must land on the node's threshold, bit for bit
       c.watchdog = 3;
-      c.search_ok = 0;
+      st.search_ok = 0;
       cont = 0;
       break;
     }
   }
+  st.store(c);
   c.search_cont = cont;
   set_cond(A.use_graph, A.h_probe, (unsigned)cont);
   __threadfence();
