@@ -433,6 +433,10 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
   uint8_t* __restrict__ act = A.pool.act;
   const int64_t ntiles = (s + TILE - 1) / TILE;
   const int64_t tpb = (ntiles + gridDim.x - 1) / gridDim.x;  // tiles per block
+  // blocks past the last tile leave at once; the nact others take tickets
+  const int64_t need = tpb > 0 ? (ntiles + tpb - 1) / tpb : 0;
+  const unsigned nact = need < 1 ? 1u : (unsigned)need;
+  if (blockIdx.x >= nact) return;
   const int64_t t_beg = (int64_t)blockIdx.x * tpb;
   const int64_t t_end = t_beg + tpb < ntiles ? t_beg + tpb : ntiles;
   const bool searched = c.search_ok != 0;
@@ -509,11 +513,11 @@ __global__ void __launch_bounds__(THREADS) k_count(const LoopArgs A) {
     run += x;
   }
   if (threadIdx.x == 0) A.count_part[blockIdx.x].n_surv = nt > 0 ? blk_surv : 0;
-  if (!last_block_arrived(&c.ticket_count)) return;
+  if (!last_block_arrived(&c.ticket_count, nact)) return;
 
   // survivors before each block (the split adds them to the block's tile
   // offsets)
-  const int G = (int)gridDim.x;
+  const int G = (int)nact;
   const int per_b = (G + THREADS - 1) / THREADS;
   const int b0 = threadIdx.x * per_b, b1 = b0 + per_b < G ? b0 + per_b : G;
   long long bacc = 0;
@@ -599,6 +603,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_split(const LoopArgs A) {
   double* __restrict__ lo_d = A.pool.lower + (size_t)dst * n * cap;
   uint8_t* __restrict__ lv_d = A.pool.level + (size_t)dst * n * cap;
   const int64_t ntiles = (s + TILE - 1) / TILE;
+  // blocks without a tile leave at once; the nact others take tickets
+  const unsigned nact = ntiles < 1 ? 1u : (ntiles < (int64_t)gridDim.x ? (unsigned)ntiles : gridDim.x);
+  if (blockIdx.x >= nact) return;
   const int X = emax_scale(c.emax);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = THREADS / 32;
@@ -729,9 +736,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_split(const LoopArgs A) {
     if (vlo | vhi) atomic_add_limbs(c.fin_vol_fixed, vlo, vhi);
     A.count_part[blockIdx.x].va = v1[0];
   }
-  if (!last_block_arrived(&c.ticket_split)) return;
+  if (!last_block_arrived(&c.ticket_split, nact)) return;
   NSum p1[1] = {{0.0, 0.0}};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += THREADS)
+  for (int b = threadIdx.x; b < (int)nact; b += THREADS)
     p1[0] = ncomb(p1[0], NSum{__ldcg(&A.count_part[b].va.s), __ldcg(&A.count_part[b].va.c)});
   nsum_block_reduce_staged<THREADS, 1>(p1, shn);
   if (threadIdx.x != 0) return;
