@@ -1683,6 +1683,9 @@ static int integrate_noalloc_locked(int n, int fam, const double* params, double
 // block per instance reduces, classifies, searches a threshold, compacts and
 // splits within its slot.
 constexpr int kBatchThreads = 256;
+// steps of Algorithm 3 one batch probe launch may take per instance (the
+// search itself gives up after 64 probes, so one launch finishes it)
+constexpr int kBatchProbeSteps = 64;
 
 __device__ __forceinline__ void batch_slot(const BatchArgs& A, const BatchInst& I, int64_t& base, int64_t& slots,
                                            const BatchGroup*& G) {
@@ -1759,6 +1762,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_reduce(const BatchArgs 
 __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A) {
   __shared__ NSum shn[kBatchThreads + 1];
   __shared__ long long shl[kBatchThreads / 32];
+  __shared__ double sh_t;
+  __shared__ int sh_cont;
   for (int b = blockIdx.x; b < A.n_inst; b += gridDim.x) {
     BatchInst& I = A.inst[b];
     Ctrl& c = I.c;
@@ -1767,23 +1772,36 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A
     int64_t base, slots;
     batch_slot(A, I, base, slots, G);
     const int64_t s_cur = c.s;
-    const double t_cur = c.t;
-    NSum sa = {0.0, 0.0};
-    long long na = 0;
-    for (int64_t i = threadIdx.x; i < s_cur; i += kBatchThreads) {
-      const double e = G->E[base + i];
-      if (relerr_active(G->V[base + i], e, c.tau_cls, c.relerr_filter) && !(e < t_cur)) ++na;
-      else nadd(sa, e);
+    const double tau_cls = c.tau_cls;
+    const int relerr = c.relerr_filter;
+    if (threadIdx.x == 0) sh_t = c.t;
+    __syncthreads();
+    // the instance's whole search in this launch: one probe and one step of
+    // Algorithm 3 per round (its regions, at most one slot, stay in L2),
+    // until the search ends or kBatchProbeSteps steps were taken
+    for (int step = 0; step < kBatchProbeSteps; ++step) {
+      const double t_cur = sh_t;
+      NSum sa = {0.0, 0.0};
+      long long na = 0;
+      for (int64_t i = threadIdx.x; i < s_cur; i += kBatchThreads) {
+        const double e = G->E[base + i];
+        if (relerr_active(G->V[base + i], e, tau_cls, relerr) && !(e < t_cur)) ++na;
+        else nadd(sa, e);
+      }
+      NSum tot1[1] = {sa};
+      nsum_block_reduce_staged<kBatchThreads, 1>(tot1, shn);
+      const NSum tot = tot1[0];
+      const long long n = block_sum_ll<kBatchThreads>(na, shl);
+      if (threadIdx.x == 0) {
+        const int cont = threshold_step(c, n, nval(tot));
+        c.search_cont = cont;
+        sh_cont = cont;
+        sh_t = c.t;
+      }
+      __syncthreads();
+      if (!sh_cont) break;
     }
-    NSum tot1[1] = {sa};
-    nsum_block_reduce_staged<kBatchThreads, 1>(tot1, shn);
-    const NSum tot = tot1[0];
-    const long long n = block_sum_ll<kBatchThreads>(na, shl);
-    if (threadIdx.x == 0) {
-      const int cont = threshold_step(c, n, nval(tot));
-      c.search_cont = cont;
-      if (cont) atomicOr(&A.flags[0], 1);
-    }
+    if (threadIdx.x == 0 && sh_cont) atomicOr(&A.flags[0], 1);
     __syncthreads();
   }
   if (!last_block_arrived(&A.tickets[1])) return;
