@@ -1760,7 +1760,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_reduce(const BatchArgs 
 
 // One threshold-search probe for every instance still searching (Algorithm 3).
 __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A) {
-  __shared__ NSum shn[kBatchThreads + 1];
+  __shared__ unsigned long long sh_lo[kBatchThreads / 32], sh_hi[kBatchThreads / 32];
   __shared__ long long shl[kBatchThreads / 32];
   __shared__ double sh_t;
   __shared__ int sh_cont;
@@ -1774,6 +1774,11 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A
     const int64_t s_cur = c.s;
     const double tau_cls = c.tau_cls;
     const int relerr = c.relerr_filter;
+    // the finished candidates' error summed exactly, as the single
+    // integral's probe sums it: E / e_b in 128-bit fixed point (e_b = 2^B),
+    // so e_abar and every decision of the search are the same bits
+    const unsigned long long e_bits = ebits(c.e_b);
+    const int B = (e_bits >> 52) ? (int)(e_bits >> 52) - 1023 : -1074 + 63 - __clzll((long long)e_bits);
     if (threadIdx.x == 0) sh_t = c.t;
     __syncthreads();
     // the instance's whole search in this launch: one probe and one step of
@@ -1781,19 +1786,32 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_probe(const BatchArgs A
     // until the search ends or kBatchProbeSteps steps were taken
     for (int step = 0; step < kBatchProbeSteps; ++step) {
       const double t_cur = sh_t;
-      NSum sa = {0.0, 0.0};
+      unsigned long long lo = 0ull, hi = 0ull;
       long long na = 0;
       for (int64_t i = threadIdx.x; i < s_cur; i += kBatchThreads) {
         const double e = G->E[base + i];
-        if (relerr_active(G->V[base + i], e, tau_cls, relerr) && !(e < t_cur)) ++na;
-        else nadd(sa, e);
+        if (relerr_active(G->V[base + i], e, tau_cls, relerr) && !(e < t_cur)) {
+          ++na;
+        } else {
+          unsigned long long l, h;
+          probe_fixed(ebits(e), e_bits, B, l, h);
+          lo += l;
+          hi += h + (lo < l ? 1ull : 0ull);
+        }
       }
-      NSum tot1[1] = {sa};
-      nsum_block_reduce_staged<kBatchThreads, 1>(tot1, shn);
-      const NSum tot = tot1[0];
-      const long long n = block_sum_ll<kBatchThreads>(na, shl);
+      warp_sum128(lo, hi);
+      if ((threadIdx.x & 31) == 0) {
+        sh_lo[threadIdx.x >> 5] = lo;
+        sh_hi[threadIdx.x >> 5] = hi;
+      }
+      const long long n = block_sum_ll<kBatchThreads>(na, shl);  // (its barriers publish sh_lo, sh_hi)
       if (threadIdx.x == 0) {
-        const int cont = threshold_step(c, n, nval(tot));
+        unsigned long long L = sh_lo[0], H = sh_hi[0];
+        for (int w = 1; w < kBatchThreads / 32; ++w) {
+          L += sh_lo[w];
+          H += sh_hi[w] + (L < sh_lo[w] ? 1ull : 0ull);
+        }
+        const int cont = threshold_step(c, n, fixed_to_double(L, H, B - kProbeFrac));
         c.search_cont = cont;
         sh_cont = cont;
         sh_t = c.t;
